@@ -1,0 +1,25 @@
+"""Float64 CPU oracle for the randomized range finder / randomized SVD.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import anything under ``oracle/``; the
+library (``paper_1607_01649_gb300``) never does, and the two share no code.
+
+Parity status per function:
+* philox4x32_10 / gaussian: pinned (independent Philox implementation,
+  distribution tests, prefix property).
+* orth, rsvd_basic, rsvd_power, rsvd_power_plain, stage_b: pinned (exact
+  recovery of rank-k matrices, full SVD when l = min(m, n), Stage-B identity,
+  singular-value interlacing, Eckart-Young, expectation/tail/power bounds,
+  the A^(q) closed form, round-off ablation).
+* adaptive_blocked, single_vector_range_finder, adaptive_range_finder:
+  pinned (Frobenius identity of Sec. 12.4, residual <= eps, rank vs the
+  eps-rank from a full SVD, span equivalence with the block method).
+* certificate, spectral_residual: pinned (eq. (infomm), Lemma
+  thm:aposteriori statistically, direct 2-norm on small cases).
+"""
+from .philox import (philox4x32_10, gaussian, omega_words, box_muller, seed_key,
+                     STREAM_SKETCH, STREAM_ADAPTIVE, STREAM_CERTIFY, STREAM_ADAPTIVE2, STREAM_NORM)
+from .rsvd import orth, sign_normalize, stage_b, rsvd_basic, rsvd_power, rsvd_power_plain
+from .norms import fro_residual, spectral_residual, certificate, theorem_bounds
+from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_finder,
+                       adaptive_range_finder)

@@ -1,0 +1,388 @@
+"""Benchmark: randomized SVD solves/s on one GB300 (or N replicas).
+
+Workload: the polynomial-decay matrix A = U diag(j^-1.5) V^T, 32768 x 32768
+float32 with Haar U, V (4.29 GB, far larger than the 129 MB L2), rank k = 200
+with p = 56 (l = 256) and q = 2 power steps.  One step = one full
+rsvd_fixed_rank call (every row of the path: Omega, the six tensor-core passes
+over A, CholeskyQR2 after each product, B^T = A^T Q in split bf16, the small
+SVD, the lift to U and V).
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+matrix (replicas; there is no exchange step), and `value` is the total over
+ranks.  ``--impl reference`` times the float64 CPU oracle instead, on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RSVD solves/s and % roofline at stated FP64-oracle error; mixed vs plain FP32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--m", type=int, default=32768)
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--k", type=int, default=200)
+    ap.add_argument("--p", type=int, default=56)
+    ap.add_argument("--q", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=2001)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-f32", action="store_true")
+    ap.add_argument("--sample", type=int, default=8192, help="CPU oracle sample size (square)")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return "poly-decay %dx%d fp32, sigma_j=j^-1.5, Haar U,V; k=%d p=%d (l=%d) q=%d" % (
+        a.m, a.n, a.k, a.p, a.k + a.p, a.q)
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in a child process."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------- distributed ---
+def dist_setup(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------- oracle leg --
+def oracle_sample(a, seconds=12.0, device=None):
+    """Time the float64 oracle on a sample x sample matrix of the same family
+    (same k, p, q), scaled to the full workload by the m*n ratio (the sketch
+    passes are linear in m*n).  Returns (solves_per_s_full_size, detail)."""
+    import numpy as np
+    import oracle
+    s = min(a.sample, a.m, a.n)
+    A = _make_matrix(s, s, a.seed, device).astype(np.float64) if device is not None else None
+    if A is None:
+        from workloads import poly_decay_matrix_np
+        A = poly_decay_matrix_np(s, s, a.seed).astype(np.float64)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.rsvd_power(A, a.k, a.p, a.q, a.seed)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > seconds or len(times) >= 20:
+            break
+    t = statistics.median(times)
+    scale = (a.m * a.n) / float(s * s)
+    detail = ("float64 oracle rsvd_power on a %dx%d matrix of the same family (k=%d p=%d q=%d), %d solve(s), "
+              "median %.3f s, scaled by m*n ratio %.1f" % (s, s, a.k, a.p, a.q, len(times), t, scale))
+    return 1.0 / (t * scale), detail, t, len(times)
+
+
+def _make_matrix(m, n, seed, device):
+    import torch
+    from workloads import poly_decay_matrix
+    A = poly_decay_matrix(m, n, seed=seed, device=device)
+    out = A.cpu().numpy()
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_reference(a):
+    world, rank, local = dist_setup(a)
+    if rank != 0:
+        return
+    dev = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = "cuda:%d" % local
+    except Exception:
+        dev = None
+    import numpy as np
+    import oracle
+    s = min(a.sample, a.m, a.n)
+    if dev is not None:
+        A = _make_matrix(s, s, a.seed, dev).astype(np.float64)
+    else:
+        from workloads import poly_decay_matrix_np
+        A = poly_decay_matrix_np(s, s, a.seed).astype(np.float64)
+    for _ in range(a.warmup):
+        oracle.rsvd_power(A, a.k, a.p, a.q, a.seed)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        oracle.rsvd_power(A, a.k, a.p, a.q, a.seed + i)
+    dt = time.perf_counter() - t0
+    scale = (a.m * a.n) / float(s * s)
+    value = a.steps / dt / scale
+    sample = ("float64 oracle rsvd_power on a %dx%d matrix of the same family (k=%d p=%d q=%d) per step, "
+              "time scaled by the m*n ratio %.1f" % (s, s, a.k, a.p, a.q, scale))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * dt / a.steps * scale,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------- ours --
+def run_ours(a):
+    import numpy as np
+    import torch
+    import paper_1607_01649_gb300 as rs
+
+    world, rank, local = dist_setup(a)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from workloads import poly_decay_matrix
+    m, n, k, p, q = a.m, a.n, a.k, a.p, a.q
+    l = k + p
+    prec = rs.RSVD_MIXED_BF16 if a.prec == "bf16" else rs.RSVD_F32
+    A = poly_decay_matrix(m, n, seed=a.seed + rank, device=dev)
+    h = rs.handle(local)
+    prm = rs.make_params(k, p, q, seed=a.seed, prec=prec, flags=0)
+    ws = torch.empty(rs.rsvd_workspace_size(h, m, n, prm), dtype=torch.uint8, device=dev)
+    U = torch.empty(m, k, dtype=torch.float32, device=dev)
+    D = torch.empty(k, dtype=torch.float64, device=dev)
+    V = torch.empty(n, k, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve(seed):
+        prm.seed = seed
+        code = rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm, U, U.stride(0), D, V, V.stride(0), ws)
+        if code != rs.RSVD_OK:
+            raise rs.RsvdError(code, rs.last_error(h))
+
+    for i in range(a.warmup):
+        solve(a.seed + i)
+    torch.cuda.synchronize()
+    st = rs.rsvd_query_status(h, ws)
+    if st != rs.RSVD_OK:
+        raise rs.RsvdError(st, "device status after warm-up")
+
+    # ---- timed region
+    clocks = ClockSampler(torch.cuda.current_device())
+    rs.rsvd_profile_read(h, 0)
+    rs.rsvd_profile_read(h, 1)
+    rs.rsvd_profile(h, 1)
+    launches0 = rs.rsvd_kernel_launches(h)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(a.steps):
+        solve(a.seed + 100 + i)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    rs.rsvd_profile(h, 0)
+    launches = rs.rsvd_kernel_launches(h) - launches0
+    ms = e0.elapsed_time(e1)
+    sk_ms, sk_n = rs.rsvd_profile_read(h, 0)
+    pj_ms, pj_n = rs.rsvd_profile_read(h, 1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = rs.rsvd_query_status(h, ws)
+    if st != rs.RSVD_OK:
+        raise rs.RsvdError(st, "device status after timing")
+    ms_per_step = ms / a.steps
+    value = world * a.steps / (ms / 1000.0)
+
+    # ---- accuracy of the last solve (not timed): singular values against the
+    # construction sigma_j = j^-1.5, Frobenius residual in float64 blockwise
+    torch.cuda.synchronize()
+    sig_true = torch.arange(1, k + 1, dtype=torch.float64, device=dev).pow(-1.5)
+    d_rel = float(((D - sig_true).abs() / sig_true).max())
+    fro2 = 0.0
+    Ud = (U.double() * D[None, :])
+    for r0 in range(0, m, 4096):
+        R = A[r0:r0 + 4096].double() - Ud[r0:r0 + 4096] @ V.double().T
+        fro2 += float((R * R).sum())
+    fro_a = float(torch.linalg.norm(A.double()))
+    fro_opt = float(torch.arange(k + 1, min(m, n) + 1, dtype=torch.float64).pow(-3.0).sum().sqrt())
+    err = {"max_rel_err_sigma_1..k_vs_construction": d_rel,
+           "fro_residual_rel": (fro2 ** 0.5) / fro_a,
+           "fro_residual_optimal_rel(Eckart-Young)": fro_opt / fro_a}
+
+    # ---- roofline of the dominant kernel: the tcgen05 sketch product
+    roof = None
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+        peak_src = "measured"
+    except Exception:
+        hbm, peak_src = 6800.0, "fallback"
+    if prec == rs.RSVD_MIXED_BF16 and sk_n > 0:
+        per_launch_ms = sk_ms / sk_n
+        # algorithmic bytes of one sketch product: A in bf16 once, X in bf16, Y in fp32
+        alg_bytes = 2.0 * m * n + 2.0 * n * l + 4.0 * m * l
+        achieved = alg_bytes / (per_launch_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "tc_gemm_kernel (bf16 sketch A*X / A^T*X, stream-K)",
+                "launches": sk_n, "avg_ms": per_launch_ms, "peak_source": peak_src,
+                "projection_split3_avg_ms": (pj_ms / pj_n) if pj_n else None}
+    elif prec == rs.RSVD_F32:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
+
+    # ---- e2e: host buffers in pinned memory, copies inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        Ah = torch.empty(m, n, dtype=torch.float32, pin_memory=True)
+        Ah.copy_(A)
+        Uh = torch.empty(m, k, dtype=torch.float32, pin_memory=True)
+        Dh = torch.empty(k, dtype=torch.float64, pin_memory=True)
+        Vh = torch.empty(n, k, dtype=torch.float32, pin_memory=True)
+        steps_e2e = max(1, min(a.steps, 5))
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(steps_e2e):
+            A.copy_(Ah, non_blocking=True)
+            solve(a.seed + 200 + i)
+            Uh.copy_(U, non_blocking=True)
+            Dh.copy_(D, non_blocking=True)
+            Vh.copy_(V, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ems = f0.elapsed_time(f1)
+        if dist is not None:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * steps_e2e / (ems / 1000.0), "unit": "solves/s",
+               "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": (m * k + n * k) * 4 + k * 8,
+               "steps": steps_e2e}
+        del Ah
+
+    # ---- plain fp32 comparator (same workload, SIMT binary32 path), 1 solve
+    f32 = None
+    if prec == rs.RSVD_MIXED_BF16 and not a.no_f32:
+        prm32 = rs.make_params(k, p, q, seed=a.seed, prec=rs.RSVD_F32, flags=0)
+        ws32 = torch.empty(rs.rsvd_workspace_size(h, m, n, prm32), dtype=torch.uint8, device=dev)
+        U32 = torch.empty_like(U)
+        D32 = torch.empty_like(D)
+        V32 = torch.empty_like(V)
+        rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm32, U32, k, D32, V32, k, ws32)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm32, U32, k, D32, V32, k, ws32)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        d32 = float(((D32 - sig_true).abs() / sig_true).max())
+        f32 = {"value": 1000.0 / g0.elapsed_time(g1), "unit": "solves/s",
+               "max_rel_err_sigma_1..k_vs_construction": d32}
+        del ws32
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not a.no_cpu:
+        v, detail, t, nsol = oracle_sample(a, device=dev)
+        cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": detail}
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if prec == rs.RSVD_MIXED_BF16 else "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "precision": a.prec,
+                       "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB)" % (m * n * 4 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "error": err, "plain_f32": f32}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * rsvd.h -- C ABI of the GB300 (sm_103a) randomized-SVD library.
+ *
+ * The library computes a rank-k approximate SVD  A ~= U diag(D) V^T  of a dense
+ * m x n matrix by the randomized range finder with power iteration and
+ * re-orthonormalization between products (Martinsson, "Randomized methods for
+ * matrix computations", Sec. 8.1, Fig. "Accuracy enhanced randomized SVD (with
+ * orthonormalization)"), followed by the Stage-B factorization of Sec. 3:
+ *
+ *   G = randn(n, l);  Q = orth(A G);
+ *   repeat q times:  W = orth(A^T Q);  Q = orth(A W);
+ *   B = Q^T A;  [Uhat, D, V] = svd(B);  U = Q Uhat;   keep the k leading triplets
+ *
+ * with l = k + p (Sec. 4, Remark "How many basis vectors").  The tolerance form
+ * of the problem (Sec. 1.1: find k with ||A - U D V^T||_Fro <= eps) is solved by
+ * the blocked greedy range finder of Sec. 12.3 (Fig. "greedy_blocked").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All matrices are ROW-MAJOR with a leading dimension (row stride, in
+ *    elements) >= the number of columns.  A column-major caller passes A^T and
+ *    swaps the roles of U and V.
+ *  - Every pointer to matrix data is a DEVICE pointer on the handle's device,
+ *    unless the parameter says "host".  All device buffers (inputs, outputs,
+ *    workspace) are owned by the caller; A is never written.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL means
+ *    the legacy default stream).  Calls return as soon as the work is enqueued
+ *    unless RSVD_FLAG_SYNC is set.  Nothing allocates device memory on the
+ *    solve path: all scratch comes from the caller's workspace, sized by
+ *    rsvd_workspace_size().
+ *  - Errors: invalid arguments are reported synchronously (RSVD_E_INVALID) and
+ *    nothing is enqueued.  Numerical failures found on the device (Cholesky
+ *    breakdown, non-finite values, non-convergence) are written to a status
+ *    word inside the workspace; the first failure wins.  They are returned by
+ *    the call itself when RSVD_FLAG_SYNC is set, or later by
+ *    rsvd_query_status().  No call aborts or throws.
+ *  - Not thread-safe per handle: one handle per host thread, or serialize.
+ */
+#ifndef RSVD_H
+#define RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsvd_handle_s* rsvd_handle_t;
+typedef void* rsvd_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  RSVD_OK = 0,
+  RSVD_E_INVALID = 1,       /* bad argument; nothing was enqueued */
+  RSVD_E_NOMEM = 2,         /* workspace too small, or host allocation failed */
+  RSVD_E_CUDA = 3,          /* a CUDA runtime call failed (see rsvd_last_error_detail) */
+  RSVD_E_BREAKDOWN = 4,     /* Cholesky pivot non-positive even after the shifted retries */
+  RSVD_E_NOT_CONVERGED = 5, /* adaptive rank reached max_rank / min(m, n) above tolerance */
+  RSVD_E_NONFINITE = 6,     /* NaN or Inf met in a Gram diagonal or a pivot */
+  RSVD_E_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  RSVD_E_UNSUPPORTED = 8    /* valid request this build does not implement */
+} rsvd_status;
+
+/* Arithmetic of the solve (what A, U and V hold, and how the sketch products
+ * are taken).  D is always double. */
+typedef enum {
+  RSVD_F64 = 0,        /* A, U, V double; every product in binary64 */
+  RSVD_F32 = 1,        /* A, U, V float; plain binary32 SIMT products */
+  RSVD_MIXED_BF16 = 2, /* A, U, V float; A*Omega, A^T Q, A W on tcgen05 tensor
+                          cores with bf16 operands and fp32 accumulation; the
+                          final B = Q^T A as a three-term split-bf16 product;
+                          Gram matrices accumulated in binary64 */
+  RSVD_MIXED_FP8 = 3   /* reserved: e4m3 sketch with per-128-row scales */
+} rsvd_precision;
+
+/* Element types for the stage entry points. */
+typedef enum { RSVD_DT_F64 = 0, RSVD_DT_F32 = 1, RSVD_DT_BF16 = 2 } rsvd_dtype;
+
+enum {
+  RSVD_FLAG_RETURN_FULL_L = 1, /* return all l = k + p triplets instead of k */
+  RSVD_FLAG_SYNC = 2,          /* block until the work ends; return the device status */
+  RSVD_FLAG_CERTIFY = 4,       /* reserved: a-posteriori certificate (Sec. 14) */
+  RSVD_FLAG_USE_CONTROLLER = 8 /* reserved: learned (l, q) controller */
+};
+
+typedef struct {
+  int k;          /* target rank (fixed-rank solve), >= 1 */
+  int p;          /* oversampling, >= 0; l = k + p <= min(m, n) and l <= 256 */
+  int q;          /* power steps, >= 0 */
+  int block;      /* adaptive block size b (0 -> 16) */
+  int max_rank;   /* adaptive cap on the rank (0 -> min(m, n)) */
+  int probe_cols; /* reserved (controller probe width) */
+  double tol;     /* adaptive: relative Frobenius tolerance, eps = tol ||A||_Fro */
+  uint64_t seed;  /* key of the Philox4x32-10 Gaussian stream */
+  int prec;       /* rsvd_precision */
+  int flags;      /* RSVD_FLAG_* */
+} rsvd_params;
+
+/* Handle: the device ordinal, its SM count and the library's small persistent
+ * host state.  rsvd_create makes `device` current on the calling thread. */
+rsvd_status rsvd_create(rsvd_handle_t* handle, int device);
+rsvd_status rsvd_destroy(rsvd_handle_t handle);
+
+/* Number of workspace bytes a solve of this shape and these parameters needs
+ * (rsvd_fixed_rank when params->tol == 0, else rsvd_adaptive_tol).  The
+ * workspace must be 256-byte aligned device memory. */
+rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_params* params,
+                                size_t* bytes);
+
+/* Fixed-rank randomized SVD (Sec. 8.1, Fig. RSVDP_stabilized, + Sec. 3 Stage B).
+ *   A  : m x n, lda >= n, double (RSVD_F64) or float (others).
+ *   U  : m x kk output, ldu >= kk, same type as A;  kk = k, or l with
+ *        RSVD_FLAG_RETURN_FULL_L.
+ *   D  : kk doubles, descending.
+ *   V  : n x kk output, ldv >= kk, same type as A.
+ *   Each pair (u_i, v_i) is signed so that the largest-magnitude entry of v_i
+ *   is positive (lowest index on ties).
+ * The random test matrix is the Philox4x32-10 stream keyed by params->seed:
+ * G(i, j) comes from counter (i / 4, j, 0, 0) through a 24-bit Box-Muller map
+ * (see rsvd_gaussian). */
+rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, int lda,
+                            const rsvd_params* params, void* U, int ldu, double* D, void* V,
+                            int ldv, void* workspace, size_t ws_bytes, rsvd_stream_t stream);
+
+/* Tolerance-driven randomized SVD (Sec. 12.3, Fig. greedy_blocked; stopping on
+ * the Frobenius norm of the explicitly updated remainder, Sec. 12.4):
+ * blocks of b Gaussian columns (Philox stream 1, block t = columns t*b ..)
+ * are drawn until ||A - Q B||_Fro <= tol ||A||_Fro, then Stage B runs on B.
+ *   U, V : capacity max_rank columns (ldu, ldv >= max_rank).
+ *   rank_out : DEVICE int, receives the rank r (a multiple of b, or max_rank).
+ *   err_out  : DEVICE double, receives ||A - Q B||_Fro / ||A||_Fro.
+ * Entries of D, U, V beyond r are set to zero.  If the cap is hit first the
+ * status is RSVD_E_NOT_CONVERGED and the outputs hold the rank-max_rank
+ * factorization. */
+rsvd_status rsvd_adaptive_tol(rsvd_handle_t handle, int m, int n, const void* A, int lda,
+                              const rsvd_params* params, void* U, int ldu, double* D, void* V,
+                              int ldv, int* rank_out, double* err_out, void* workspace,
+                              size_t ws_bytes, rsvd_stream_t stream);
+
+/* Reads the device status word of the last solve that used `workspace`
+ * (synchronizes `stream` first).  *status receives an rsvd_status value. */
+rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status,
+                              rsvd_stream_t stream);
+
+/* Copies a human-readable description of the last synchronous error on this
+ * handle into buf (always NUL-terminated when len > 0). */
+rsvd_status rsvd_last_error_detail(rsvd_handle_t handle, char* buf, size_t len);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points: single steps of the path, for composition and testing.
+ * ------------------------------------------------------------------------- */
+
+/* Raw Philox4x32-10 words (Salmon et al., SC'11) behind the Gaussian stream:
+ * out[(j * n_groups + g) * 4 + w] = word w of counter (g, col0 + j, stream_id, 0)
+ * under key (seed mod 2^32, seed div 2^32), for g < n_groups, j < l. */
+rsvd_status rsvd_philox_words(rsvd_handle_t handle, int n_groups, int l, uint64_t seed,
+                              uint32_t stream_id, int col0, uint32_t* out, rsvd_stream_t stream);
+
+/* Gaussian test matrix (the paper's randn; Fig. RSVD step 1): out is n x l,
+ * row-major with leading dimension ldo >= l, element type `dtype`.
+ * Entry (i, j) uses counter (i / 4, col0 + j, stream_id, 0); its words
+ * (w0, w1) serve rows 4g, 4g+1 and (w2, w3) rows 4g+2, 4g+3 through
+ * v = w >> 8, u1 = (v_a + 1) 2^-24, u2 = v_b 2^-24,
+ * z = sqrt(-2 ln u1) * (cos | sin)(2 pi u2).  binary32/bf16 outputs are
+ * computed in binary32, binary64 outputs in binary64. */
+rsvd_status rsvd_gaussian(rsvd_handle_t handle, int n, int l, uint64_t seed, uint32_t stream_id,
+                          int col0, int dtype, void* out, int ldo, rsvd_stream_t stream);
+
+/* One sketch product (Fig. RSVDP_stabilized steps 2, 4, 5, 7):
+ *   trans = 0:  Y (m x l) = A (m x n) X (n x l)
+ *   trans = 1:  Y (n x l) = A^T (n x m) X (m x l)
+ * A row-major m x n (lda).  prec RSVD_F64: A, X, Y double; RSVD_F32: float
+ * (SIMT fp32); RSVD_MIXED_BF16: A and X bf16 (raw 16-bit storage), Y float,
+ * tcgen05 tensor-core product with fp32 accumulation.  Needs workspace
+ * (rsvd_sketch_workspace_size) for split-K partial sums. */
+rsvd_status rsvd_sketch_workspace_size(rsvd_handle_t handle, int prec, int trans, int m, int n,
+                                       int l, size_t* bytes);
+rsvd_status rsvd_sketch(rsvd_handle_t handle, int prec, int trans, int m, int n, int l,
+                        const void* A, int lda, const void* X, int ldx, void* Y, int ldy,
+                        void* workspace, size_t ws_bytes, rsvd_stream_t stream);
+
+/* Projection B = Q^T A of Stage B (Sec. 3 step 1; Fig. RSVDP_stabilized step 7),
+ * returned transposed:  Bt (n x l, row-major, ldb) = A^T Q  for A m x n (lda)
+ * and Q m x l (ldq).  RSVD_F64: double; RSVD_F32: float, SIMT; RSVD_MIXED_BF16:
+ * A and Q float, each split into a bf16 pair (x = hi + lo) and
+ * Bt = Ah^T Qh + Ah^T Ql + Al^T Qh on tcgen05 tensor cores (relative error
+ * about 2^-16 instead of bf16's 2^-8). */
+rsvd_status rsvd_project_workspace_size(rsvd_handle_t handle, int prec, int m, int n, int l, size_t* bytes);
+rsvd_status rsvd_project(rsvd_handle_t handle, int prec, int m, int n, int l, const void* A, int lda,
+                         const void* Q, int ldq, void* Bt, int ldb, void* workspace, size_t ws_bytes,
+                         rsvd_stream_t stream);
+
+/* Diagnostics.  rsvd_kernel_launches: number of kernels this library has
+ * enqueued (through any handle) since it was loaded.  rsvd_profile: while
+ * enabled (on != 0) every tensor-core sketch product (kind 0) and
+ * split-bf16 projection (kind 1) enqueued through `handle` is bracketed by a
+ * pair of CUDA events on its stream; rsvd_profile_read waits for the recorded
+ * events, returns the summed device time in milliseconds and the number of
+ * launches of that kind, and clears them. */
+rsvd_status rsvd_kernel_launches(rsvd_handle_t handle, long long* count);
+rsvd_status rsvd_profile(rsvd_handle_t handle, int on);
+rsvd_status rsvd_profile_read(rsvd_handle_t handle, int kind, double* total_ms, long long* launches);
+
+/* Orthonormalization (Sec. 2.3, "orth", unpivoted): Q = Y R^-1 with R upper
+ * triangular, diag(R) > 0, by CholeskyQR2 (a shifted first pass is added when
+ * the Gram matrix is too ill-conditioned, Fukaya et al., SISC 2020).  Y is
+ * rows x l row-major (ldy), double for RSVD_F64 else float, overwritten by Q.
+ * R (optional, may be NULL): l x l row-major doubles, receives R.
+ * Gram matrices are accumulated in binary64. */
+rsvd_status rsvd_orth_workspace_size(rsvd_handle_t handle, int prec, int rows, int l,
+                                     size_t* bytes);
+rsvd_status rsvd_orth(rsvd_handle_t handle, int prec, int rows, int l, void* Y, int ldy, double* R,
+                      void* workspace, size_t ws_bytes, rsvd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVD_H */

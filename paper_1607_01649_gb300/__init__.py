@@ -1,0 +1,323 @@
+"""Thin Python binding of librsvd.so, the GB300 randomized-SVD library.
+
+Every function here marshals arguments (torch tensors -> device pointers, the
+current CUDA stream) and calls the C ABI declared in include/rsvd.h, under the
+same name.  All arithmetic happens in the library's CUDA kernels; there is no
+CPU or PyTorch fallback: if the library is missing, importing this package
+fails loudly.
+
+Convenience wrappers (``fixed_rank``, ``adaptive_tol``, ``orth``, ``sketch``)
+allocate outputs and workspace with torch and then make the same C calls.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsvd.so")
+
+RSVD_OK = 0
+RSVD_E_INVALID = 1
+RSVD_E_NOMEM = 2
+RSVD_E_CUDA = 3
+RSVD_E_BREAKDOWN = 4
+RSVD_E_NOT_CONVERGED = 5
+RSVD_E_NONFINITE = 6
+RSVD_E_TIMEOUT = 7
+RSVD_E_UNSUPPORTED = 8
+
+RSVD_F64 = 0
+RSVD_F32 = 1
+RSVD_MIXED_BF16 = 2
+RSVD_MIXED_FP8 = 3
+
+RSVD_DT_F64 = 0
+RSVD_DT_F32 = 1
+RSVD_DT_BF16 = 2
+
+RSVD_FLAG_RETURN_FULL_L = 1
+RSVD_FLAG_SYNC = 2
+RSVD_FLAG_CERTIFY = 4
+RSVD_FLAG_USE_CONTROLLER = 8
+
+STATUS_NAMES = {0: "RSVD_OK", 1: "RSVD_E_INVALID", 2: "RSVD_E_NOMEM", 3: "RSVD_E_CUDA", 4: "RSVD_E_BREAKDOWN",
+                5: "RSVD_E_NOT_CONVERGED", 6: "RSVD_E_NONFINITE", 7: "RSVD_E_TIMEOUT", 8: "RSVD_E_UNSUPPORTED"}
+
+# Every symbol include/rsvd.h declares (checked by the CPU test suite).
+EXPORTED = [
+    "rsvd_create", "rsvd_destroy", "rsvd_workspace_size", "rsvd_fixed_rank", "rsvd_adaptive_tol",
+    "rsvd_query_status", "rsvd_last_error_detail", "rsvd_philox_words", "rsvd_gaussian",
+    "rsvd_sketch_workspace_size", "rsvd_sketch", "rsvd_orth_workspace_size", "rsvd_orth",
+    "rsvd_project_workspace_size", "rsvd_project", "rsvd_kernel_launches", "rsvd_profile", "rsvd_profile_read",
+]
+
+
+class Params(ctypes.Structure):
+    """Mirror of rsvd_params."""
+    _fields_ = [("k", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("block", ctypes.c_int),
+                ("max_rank", ctypes.c_int), ("probe_cols", ctypes.c_int), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class RsvdError(RuntimeError):
+    def __init__(self, code, detail=""):
+        self.code = code
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), detail))
+
+
+_lib = None
+
+
+def load():
+    """Load librsvd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librsvd.so not found at %s; build it with `python -m paper_1607_01649_gb300.build`"
+                          % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, u32, u64, sz, dp = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                               ctypes.c_size_t, ctypes.c_void_p)
+    P = ctypes.POINTER(Params)
+    sig = {
+        "rsvd_create": [ctypes.POINTER(vp), i],
+        "rsvd_destroy": [vp],
+        "rsvd_workspace_size": [vp, i, i, P, ctypes.POINTER(sz)],
+        "rsvd_fixed_rank": [vp, i, i, vp, i, P, vp, i, dp, vp, i, vp, sz, vp],
+        "rsvd_adaptive_tol": [vp, i, i, vp, i, P, vp, i, dp, vp, i, vp, vp, vp, sz, vp],
+        "rsvd_query_status": [vp, vp, ctypes.POINTER(i), vp],
+        "rsvd_last_error_detail": [vp, ctypes.c_char_p, sz],
+        "rsvd_philox_words": [vp, i, i, u64, u32, i, vp, vp],
+        "rsvd_gaussian": [vp, i, i, u64, u32, i, i, vp, i, vp],
+        "rsvd_sketch_workspace_size": [vp, i, i, i, i, i, ctypes.POINTER(sz)],
+        "rsvd_sketch": [vp, i, i, i, i, i, vp, i, vp, i, vp, i, vp, sz, vp],
+        "rsvd_orth_workspace_size": [vp, i, i, i, ctypes.POINTER(sz)],
+        "rsvd_orth": [vp, i, i, i, vp, i, dp, vp, sz, vp],
+        "rsvd_project_workspace_size": [vp, i, i, i, i, ctypes.POINTER(sz)],
+        "rsvd_project": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp, sz, vp],
+        "rsvd_kernel_launches": [vp, ctypes.POINTER(ctypes.c_longlong)],
+        "rsvd_profile": [vp, i],
+        "rsvd_profile_read": [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+_handles = {}
+
+
+def handle(device=None):
+    """A library handle for `device` (cached per device)."""
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _handles:
+        h = ctypes.c_void_p()
+        _check(load().rsvd_create(ctypes.byref(h), int(device)), None)
+        _handles[device] = h
+    return _handles[device]
+
+
+def last_error(h):
+    buf = ctypes.create_string_buffer(512)
+    load().rsvd_last_error_detail(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(code, h):
+    if code != RSVD_OK:
+        raise RsvdError(code, last_error(h) if h is not None else "")
+    return code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _empty_ws(nbytes, device):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------- raw calls --
+def rsvd_workspace_size(h, m, n, params):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_workspace_size(h, m, n, ctypes.byref(params), ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_fixed_rank(h, m, n, A, lda, params, U, ldu, D, V, ldv, ws, stream=None):
+    return load().rsvd_fixed_rank(h, m, n, _ptr(A), lda, ctypes.byref(params), _ptr(U), ldu, _ptr(D), _ptr(V), ldv,
+                                  _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_adaptive_tol(h, m, n, A, lda, params, U, ldu, D, V, ldv, rank_out, err_out, ws, stream=None):
+    return load().rsvd_adaptive_tol(h, m, n, _ptr(A), lda, ctypes.byref(params), _ptr(U), ldu, _ptr(D), _ptr(V),
+                                    ldv, _ptr(rank_out), _ptr(err_out), _ptr(ws),
+                                    ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_query_status(h, ws, stream=None):
+    st = ctypes.c_int()
+    _check(load().rsvd_query_status(h, _ptr(ws), ctypes.byref(st), _stream(stream)), h)
+    return st.value
+
+
+def rsvd_philox_words(h, n_groups, l, seed, stream_id, col0, out, stream=None):
+    return load().rsvd_philox_words(h, n_groups, l, seed, stream_id, col0, _ptr(out), _stream(stream))
+
+
+def rsvd_gaussian(h, n, l, seed, stream_id, col0, dtype, out, ldo, stream=None):
+    return load().rsvd_gaussian(h, n, l, seed, stream_id, col0, dtype, _ptr(out), ldo, _stream(stream))
+
+
+def rsvd_sketch_workspace_size(h, prec, trans, m, n, l):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_sketch_workspace_size(h, prec, trans, m, n, l, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_sketch(h, prec, trans, m, n, l, A, lda, X, ldx, Y, ldy, ws, stream=None):
+    return load().rsvd_sketch(h, prec, trans, m, n, l, _ptr(A), lda, _ptr(X), ldx, _ptr(Y), ldy, _ptr(ws),
+                              ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_orth_workspace_size(h, prec, rows, l):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_orth_workspace_size(h, prec, rows, l, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_orth(h, prec, rows, l, Y, ldy, R, ws, stream=None):
+    return load().rsvd_orth(h, prec, rows, l, _ptr(Y), ldy, _ptr(R), _ptr(ws), ws.numel() if ws is not None else 0,
+                            _stream(stream))
+
+
+def rsvd_project_workspace_size(h, prec, m, n, l):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_project_workspace_size(h, prec, m, n, l, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_project(h, prec, m, n, l, A, lda, Q, ldq, Bt, ldb, ws, stream=None):
+    return load().rsvd_project(h, prec, m, n, l, _ptr(A), lda, _ptr(Q), ldq, _ptr(Bt), ldb, _ptr(ws),
+                               ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_kernel_launches(h):
+    out = ctypes.c_longlong()
+    _check(load().rsvd_kernel_launches(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_profile(h, on):
+    return _check(load().rsvd_profile(h, int(on)), h)
+
+
+def rsvd_profile_read(h, kind):
+    ms = ctypes.c_double()
+    cnt = ctypes.c_longlong()
+    _check(load().rsvd_profile_read(h, kind, ctypes.byref(ms), ctypes.byref(cnt)), h)
+    return ms.value, cnt.value
+
+
+# -------------------------------------------------------------- convenience --
+def make_params(k, p=10, q=1, seed=0, prec=RSVD_F32, flags=0, tol=0.0, block=16, max_rank=0):
+    return Params(k=k, p=p, q=q, block=block, max_rank=max_rank, probe_cols=0, tol=tol, seed=seed, prec=prec,
+                  flags=flags)
+
+
+def _prec_dtype(prec):
+    import torch
+    return torch.float64 if prec == RSVD_F64 else torch.float32
+
+
+def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws=None, out=None):
+    """A ~= U diag(D) V^T by rsvd_fixed_rank.  A: (m, n) row-major CUDA tensor
+    (float64 for RSVD_F64, else float32).  Returns (U, D, V)."""
+    import torch
+    h = handle(A.device.index)
+    m, n = A.shape
+    flags = (RSVD_FLAG_RETURN_FULL_L if full else 0) | (RSVD_FLAG_SYNC if sync else 0)
+    prm = make_params(k, p, q, seed, prec, flags)
+    kk = k + p if full else k
+    dt = _prec_dtype(prec)
+    if out is None:
+        U = torch.empty(m, kk, dtype=dt, device=A.device)
+        D = torch.empty(kk, dtype=torch.float64, device=A.device)
+        V = torch.empty(n, kk, dtype=dt, device=A.device)
+    else:
+        U, D, V = out
+    if ws is None:
+        ws = _empty_ws(rsvd_workspace_size(h, m, n, prm), A.device)
+    _check(rsvd_fixed_rank(h, m, n, A, A.stride(0), prm, U, U.stride(0), D, V, V.stride(0), ws), h)
+    return U, D, V
+
+
+def gaussian(n, l, seed, stream_id=0, col0=0, dtype=None, device="cuda"):
+    import torch
+    dtype = torch.float32 if dtype is None else dtype
+    code = {torch.float64: RSVD_DT_F64, torch.float32: RSVD_DT_F32, torch.bfloat16: RSVD_DT_BF16}[dtype]
+    out = torch.empty(n, l, dtype=dtype, device=device)
+    h = handle(out.device.index)
+    _check(rsvd_gaussian(h, n, l, seed, stream_id, col0, code, out, l), h)
+    return out
+
+
+def philox_words(n_groups, l, seed, stream_id=0, col0=0, device="cuda"):
+    import torch
+    out = torch.empty(l * n_groups * 4, dtype=torch.int32, device=device)
+    h = handle(out.device.index)
+    _check(rsvd_philox_words(h, n_groups, l, seed, stream_id, col0, out), h)
+    return out
+
+
+def sketch(A, X, trans=False, prec=RSVD_F32):
+    """Y = A X (trans=False) or A^T X (trans=True) through rsvd_sketch."""
+    import torch
+    h = handle(A.device.index)
+    m, n = A.shape
+    l = X.shape[1]
+    M = n if trans else m
+    ydt = torch.float64 if prec == RSVD_F64 else torch.float32
+    Y = torch.empty(M, l, dtype=ydt, device=A.device)
+    ws = _empty_ws(rsvd_sketch_workspace_size(h, prec, int(trans), m, n, l), A.device)
+    _check(rsvd_sketch(h, prec, int(trans), m, n, l, A, A.stride(0), X, X.stride(0), Y, Y.stride(0), ws), h)
+    return Y
+
+
+def project(A, Q, prec=RSVD_F32):
+    """B^T = A^T Q through rsvd_project."""
+    import torch
+    h = handle(A.device.index)
+    m, n = A.shape
+    l = Q.shape[1]
+    Bt = torch.empty(n, l, dtype=torch.float64 if prec == RSVD_F64 else torch.float32, device=A.device)
+    ws = _empty_ws(rsvd_project_workspace_size(h, prec, m, n, l), A.device)
+    _check(rsvd_project(h, prec, m, n, l, A, A.stride(0), Q, Q.stride(0), Bt, Bt.stride(0), ws), h)
+    return Bt
+
+
+def orth(Y, prec=RSVD_F32, want_r=True):
+    """Q, R with Y = Q R through rsvd_orth (Y is copied, not overwritten)."""
+    import torch
+    h = handle(Y.device.index)
+    rows, l = Y.shape
+    Q = Y.clone()
+    R = torch.empty(l, l, dtype=torch.float64, device=Y.device) if want_r else None
+    ws = _empty_ws(rsvd_orth_workspace_size(h, prec, rows, l), Y.device)
+    _check(rsvd_orth(h, prec, rows, l, Q, Q.stride(0), R, ws), h)
+    st = rsvd_query_status(h, ws)
+    if st != RSVD_OK:
+        raise RsvdError(st, "orth device status")
+    return Q, R

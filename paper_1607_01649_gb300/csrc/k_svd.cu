@@ -1,0 +1,374 @@
+// Small SVD of B (Fig. RSVDP_stabilized step 8; Sec. 3 Stage B step 2).
+//
+// B (l x n) enters as B^T = A^T Q (n x l).  B^T is orthonormalized with the
+// same CholeskyQR2 as Stage A: B^T = Q_B R_B.  Then B = R_B^T Q_B^T and the
+// SVD of the l x l matrix M = R_B^T is computed by one-sided (Hestenes)
+// Jacobi: M J = X with mutually orthogonal columns, X = W Sigma, so
+//   B = W Sigma (Q_B J)^T,  Uhat = W,  V = Q_B J.
+// Rotations on the QR factor's transpose converge in few sweeps (Drmac and
+// Veselic, SIMAX 29 (2008)).
+//
+// The Jacobi runs in one thread-block cluster of NC CTAs.  The 2 NC column
+// blocks (w columns each) follow a round-robin tournament; in every round a
+// CTA sweeps all column pairs of the two blocks it holds (one warp per pair),
+// then each CTA pulls the two blocks it needs next from the CTAs that hold
+// them, through distributed shared memory.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rsvd {
+
+template <typename C>
+struct JacobiTol;
+template <>
+struct JacobiTol<float> {
+  static constexpr double u = 5.9604644775390625e-08;
+};
+template <>
+struct JacobiTol<double> {
+  static constexpr double u = 1.1102230246251565e-16;
+};
+
+// position of player i (0 <= i < P) in round r of the circle method
+__device__ __forceinline__ int rr_pos(int i, int r, int P) {
+  return i == 0 ? 0 : 1 + ((i - 1 + r) % (P - 1));
+}
+// which position holds player x in round r
+__device__ __forceinline__ int rr_where(int x, int r, int P) {
+  if (x == 0) return 0;
+  int v = (x - 1 - r) % (P - 1);
+  if (v < 0) v += P - 1;
+  return 1 + v;
+}
+
+// Rx, Jx: buffers of w columns, each column l contiguous values.
+template <typename C>
+__global__ void __launch_bounds__(512)
+    jacobi_cluster_kernel(int l, int w, const double* __restrict__ Rb, C* __restrict__ Wt,
+                          C* __restrict__ Jt, double* __restrict__ sigma, DevStatus* st, int max_sweeps) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int NC = (int)cluster.num_blocks();
+  const int me = (int)cluster.block_rank();
+  const int P = 2 * NC;
+  extern __shared__ unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const size_t blk = (size_t)2 * w * l;  // X then J, w columns each
+  __shared__ int s_rot;
+  __shared__ int s_total;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const int nwarps = blockDim.x / 32;
+  const double tol = 16.0 * sqrt((double)l) * JacobiTol<C>::u;
+
+  // round 0: CTA me holds players rr_pos(me, 0), rr_pos(P-1-me, 0)
+  auto load_block = [&](C* dst, int bid) {
+    C* X = dst;
+    C* J = dst + (size_t)w * l;
+    for (int e = tid; e < w * l; e += blockDim.x) {
+      const int cc = e / l, r = e % l;
+      const int col = bid * w + cc;
+      C xv = C(0), jv = C(0);
+      if (col < l) {
+        xv = (C)Rb[(size_t)col * l + r];  // column col of M = row col of R_B
+        jv = (r == col) ? C(1) : C(0);
+      }
+      X[e] = xv;
+      J[e] = jv;
+    }
+  };
+  load_block(buf + 0 * blk, rr_pos(me, 0, P));
+  load_block(buf + 1 * blk, rr_pos(P - 1 - me, 0, P));
+  if (tid == 0) s_total = 0;
+  __syncthreads();
+
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < P - 1; ++r) {
+      const int par = (sweep * (P - 1) + r) & 1;
+      C* top = buf + (size_t)(2 * par) * blk;
+      C* bot = buf + (size_t)(2 * par + 1) * blk;
+      // ---- local sweep over the 2w columns (circle method on 2w players)
+      const int Q2 = 2 * w;
+      for (int step = 0; step < Q2 - 1; ++step) {
+        for (int pr = warp; pr < w; pr += nwarps) {
+          const int ia = rr_pos(pr, step, Q2), ib = rr_pos(Q2 - 1 - pr, step, Q2);
+          C* xa = (ia < w ? top : bot) + (size_t)(ia % w) * l;
+          C* xb = (ib < w ? top : bot) + (size_t)(ib % w) * l;
+          C* ja = xa + (size_t)w * l;
+          C* jb = xb + (size_t)w * l;
+          C al = C(0), be = C(0), ga = C(0);
+          for (int i = lane; i < l; i += 32) {
+            const C a = xa[i], b = xb[i];
+            al = fma(a, a, al);
+            be = fma(b, b, be);
+            ga = fma(a, b, ga);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          }
+          // lane 0 forms the rotation in binary64 and broadcasts it
+          int rot = 0;
+          C c = C(1), s = C(0);
+          if (lane == 0) {
+            const double A = (double)al, B = (double)be, G = (double)ga;
+            if (A > 0.0 && B > 0.0 && fabs(G) > tol * sqrt(A * B)) {
+              const double zeta = (B - A) / (2.0 * G);
+              const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+              const double cs = 1.0 / sqrt(1.0 + t * t);
+              c = (C)cs;
+              s = (C)(cs * t);
+              rot = 1;
+            }
+          }
+          rot = __shfl_sync(0xffffffffu, rot, 0);
+          if (rot) {
+            c = __shfl_sync(0xffffffffu, c, 0);
+            s = __shfl_sync(0xffffffffu, s, 0);
+            for (int i = lane; i < l; i += 32) {
+              const C a = xa[i], b = xb[i];
+              xa[i] = c * a - s * b;
+              xb[i] = s * a + c * b;
+              const C p = ja[i], q = jb[i];
+              ja[i] = c * p - s * q;
+              jb[i] = s * p + c * q;
+            }
+            if (lane == 0) atomicAdd(&s_rot, 1);
+          }
+        }
+        __syncthreads();
+      }
+      // ---- exchange: pull the blocks needed in the next round
+      if (P > 2) {
+        cluster.sync();
+        const int rn = r + 1;  // next round index within the tournament (mod P-1)
+        const int npar = par ^ 1;
+        C* ntop = buf + (size_t)(2 * npar) * blk;
+        C* nbot = buf + (size_t)(2 * npar + 1) * blk;
+        for (int half = 0; half < 2; ++half) {
+          const int pos_next = half == 0 ? me : P - 1 - me;
+          const int player = rr_pos(pos_next, rn % (P - 1), P);
+          const int pos_now = rr_where(player, r, P);
+          const int holder = pos_now < NC ? pos_now : P - 1 - pos_now;
+          const int slot = pos_now < NC ? 0 : 1;
+          C* src = cluster.map_shared_rank(buf + (size_t)(2 * par + slot) * blk, holder);
+          C* dst = half == 0 ? ntop : nbot;
+          for (size_t e = tid; e < blk; e += blockDim.x) dst[e] = src[e];
+        }
+        cluster.sync();
+      } else {
+        // single CTA: same two blocks; move them to the other buffer pair
+        const int npar = par ^ 1;
+        for (size_t e = tid; e < 2 * blk; e += blockDim.x)
+          buf[(size_t)(2 * npar) * blk + e] = buf[(size_t)(2 * par) * blk + e];
+        __syncthreads();
+      }
+    }
+    // ---- convergence: total rotations of this sweep over the cluster
+    if (tid == 0) {
+      int* tot0 = cluster.map_shared_rank(&s_total, 0);
+      atomicAdd(tot0, s_rot);
+    }
+    cluster.sync();
+    const int total = *cluster.map_shared_rank(&s_total, 0);
+    cluster.sync();
+    if (me == 0 && tid == 0) s_total = 0;
+    cluster.sync();
+    converged = (total == 0);
+  }
+  if (me == 0 && tid == 0) st->jacobi_sweeps = sweep;
+
+  // ---- outputs: after the last round the blocks sit in the buffer pair of
+  // parity (sweeps * (P-1)) & 1, at round 0 positions of the tournament
+  const int par = (sweep * (P - 1)) & 1;
+  for (int half = 0; half < 2; ++half) {
+    const int player = rr_pos(half == 0 ? me : P - 1 - me, (sweep * (P - 1)) % (P - 1), P);
+    const C* X = buf + (size_t)(2 * par + half) * blk;
+    const C* J = X + (size_t)w * l;
+    for (int cc = warp; cc < w; cc += nwarps) {
+      const int col = player * w + cc;
+      if (col >= l) continue;
+      const C* x = X + (size_t)cc * l;
+      const C* jv = J + (size_t)cc * l;
+      double ss = 0.0;
+      C part = C(0);
+      for (int i = lane; i < l; i += 32) part = fma(x[i], x[i], part);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      ss = (double)part;
+      const double sg = sqrt(ss);
+      const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
+      for (int i = lane; i < l; i += 32) {
+        Wt[(size_t)col * l + i] = (C)((double)x[i] * inv);
+        Jt[(size_t)col * l + i] = jv[i];
+      }
+      if (lane == 0) sigma[col] = sg;
+    }
+  }
+}
+
+int jacobi_cluster_size(int l) {
+  int nc = (l + 31) / 32;
+  if (nc > 8) nc = 8;
+  if (nc < 1) nc = 1;
+  return nc;
+}
+
+size_t jacobi_smem_bytes(int l, size_t csize) {
+  const int nc = jacobi_cluster_size(l);
+  const int w = (l + 2 * nc - 1) / (2 * nc);
+  return (size_t)4 * 2 * w * l * csize;
+}
+
+template <typename C>
+cudaError_t launch_jacobi(int l, const double* Rb, C* Wt, C* Jt, double* sigma, DevStatus* st, cudaStream_t s) {
+  const int nc = jacobi_cluster_size(l);
+  const int w = (l + 2 * nc - 1) / (2 * nc);
+  const size_t smem = jacobi_smem_bytes(l, sizeof(C));
+  auto kfn = jacobi_cluster_kernel<C>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc, 1, 1);
+  cfg.blockDim = dim3(32 * (w < 1 ? 1 : w), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, kfn, l, w, Rb, Wt, Jt, sigma, st, 40);
+}
+
+template cudaError_t launch_jacobi<float>(int, const double*, float*, float*, double*, DevStatus*, cudaStream_t);
+template cudaError_t launch_jacobi<double>(int, const double*, double*, double*, double*, DevStatus*,
+                                           cudaStream_t);
+
+// ------------------------------------------------------------ sort + gather --
+// perm[rank] = column with the rank-th largest sigma (ties: lower index
+// first); D[rank] = sigma for rank < kk; Wsel, Jsel (l x kk row-major) hold the
+// selected columns.
+template <typename C>
+__global__ void sort_gather_kernel(int l, int kk, const double* __restrict__ sigma, const C* __restrict__ Wt,
+                                   const C* __restrict__ Jt, double* __restrict__ D, C* __restrict__ Wsel,
+                                   C* __restrict__ Jsel, int* __restrict__ perm) {
+  __shared__ int sperm[512];
+  // Sort key: sigma, with NaN mapped to -inf so that (key desc, index asc) is
+  // a strict total order and the ranks form a permutation of 0..l-1.
+  for (int i = threadIdx.x; i < l; i += blockDim.x) sperm[i] = i;
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    const double si = isnan(sigma[i]) ? -INFINITY : sigma[i];
+    int rank = 0;
+    for (int j = 0; j < l; ++j) {
+      const double sj = isnan(sigma[j]) ? -INFINITY : sigma[j];
+      rank += (sj > si) || (sj == si && j < i);
+    }
+    sperm[rank] = i;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kk; c += blockDim.x) {
+    const int src = min(max(sperm[c], 0), l - 1);
+    D[c] = sigma[src];
+    if (perm) perm[c] = src;
+  }
+  for (int e = threadIdx.x; e < l * kk; e += blockDim.x) {
+    const int i = e / kk, c = e % kk;
+    const int src = min(max(sperm[c], 0), l - 1);
+    Wsel[e] = Wt[(size_t)src * l + i];
+    Jsel[e] = Jt[(size_t)src * l + i];
+  }
+}
+
+template <typename C>
+void launch_sort_gather(int l, int kk, const double* sigma, const C* Wt, const C* Jt, double* D, C* Wsel, C* Jsel,
+                        cudaStream_t s) {
+  sort_gather_kernel<C><<<1, 512, 0, s>>>(l, kk, sigma, Wt, Jt, D, Wsel, Jsel, nullptr);
+  note_launch();
+}
+template void launch_sort_gather<float>(int, int, const double*, const float*, const float*, double*, float*,
+                                        float*, cudaStream_t);
+template void launch_sort_gather<double>(int, int, const double*, const double*, const double*, double*, double*,
+                                         double*, cudaStream_t);
+
+// ------------------------------------------------------------------ signs --
+// For column c of V (rows x kk, ldv): the entry of largest magnitude (lowest
+// index on ties) is made positive; U's column c gets the same sign.
+template <typename T>
+__global__ void sign_fix_kernel(int m, int n, int kk, T* __restrict__ U, int ldu, T* __restrict__ V, int ldv) {
+  const int c = blockIdx.x;
+  if (c >= kk) return;
+  __shared__ double smax[32];
+  __shared__ int sidx[32];
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = fabs((double)V[(size_t)i * ldv + c]);
+    if (a > best) {
+      best = a;
+      bi = i;
+    }
+  }
+  // block arg-max with lowest-index tie break
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    smax[warp] = best;
+    sidx[warp] = bi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x / 32;
+    best = lane < nw ? smax[lane] : -1.0;
+    bi = lane < nw ? sidx[lane] : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) sidx[0] = bi;
+  }
+  __syncthreads();
+  const int imax = sidx[0];
+  if (imax >= n) return;
+  const bool flip = V[(size_t)imax * ldv + c] < T(0);
+  __syncthreads();
+  if (!flip) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)i * ldv + c] = -V[(size_t)i * ldv + c];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) U[(size_t)i * ldu + c] = -U[(size_t)i * ldu + c];
+}
+
+template <typename T>
+void launch_sign_fix(int m, int n, int kk, T* U, int ldu, T* V, int ldv, cudaStream_t s) {
+  if (kk == 0) return;
+  sign_fix_kernel<T><<<kk, 256, 0, s>>>(m, n, kk, U, ldu, V, ldv);
+  note_launch();
+}
+template void launch_sign_fix<float>(int, int, int, float*, int, float*, int, cudaStream_t);
+template void launch_sign_fix<double>(int, int, int, double*, int, double*, int, cudaStream_t);
+
+}  // namespace rsvd

@@ -1,0 +1,435 @@
+// tcgen05 sketch products for the mixed-precision path (Fig. RSVDP_stabilized
+// steps 2, 4, 5 and 7 on tensor cores):
+//
+//   NN:  Y[M x N] = A[M x K] X[K x N]      A bf16 row-major (K-major operand)
+//   TN:  Y[M x N] = A^T[M x K] X[K x N]    A bf16 K x M row-major (MN-major operand)
+//   split3 (TN only):  Y = Ah^T Xh + Ah^T Xl + Al^T Xh, the three-term split-bf16
+//                      product for B^T = A^T Q with A = Ah + Al, Q = Xh + Xl.
+//
+// X is bf16 K x N row-major (MN-major operand), Y fp32.  N <= 256 is one MMA
+// tile wide (M = 128 rows per tile, K = 64 per pipeline stage, K = 16 per MMA).
+//
+// Persistent stream-K schedule: the T x KB (tile, k-block) units are cut into
+// G equal contiguous ranges, one per CTA (G <= #SMs), so every SM streams the
+// same number of bytes of A.  A tile whose k-blocks span two or more CTAs is
+// written as partial sums and added in CTA order by a fix-up kernel, which
+// keeps the result bitwise reproducible.
+//
+// Roles: warp 0 issues TMA loads into a STAGES-deep ring; warp 1 owns the
+// tensor memory (two accumulators, so one tile's epilogue overlaps the next
+// tile's MMAs) and issues tcgen05.mma; warps 2-5 drain TMEM to global memory.
+// All waits are bounded; a timeout sets RSVD_E_TIMEOUT and the CTA winds down.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "sm100.cuh"
+
+#include <cudaTypedefs.h>
+
+namespace rsvd {
+
+using namespace sm100;
+
+struct TcArgs {
+  int M, N, K;
+  int KB;        // k-blocks per tile
+  int T;         // tiles
+  long long W;   // T * KB units
+  int G;         // CTAs
+  int Npad;      // MMA N (multiple of 16)
+  int NA;        // TMEM columns per accumulator (power of 2 >= 32)
+  int nchunk;    // 64-column TMA boxes per B tile
+  float* Y;
+  int ldy;
+  float* part;   // [G][2][128][Npad]
+  DevStatus* st;
+};
+
+__host__ __device__ inline long long su0(long long c, long long W, int G) { return (c * W) / G; }
+
+constexpr int TC_THREADS = 192;
+constexpr uint32_t A_TILE = 16384;   // 128 x 64 bf16
+constexpr uint32_t B_CHUNK = 8192;   // 64 x 64 bf16
+
+template <bool TRANS, bool SPLIT3>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX2, TcArgs g,
+                   int stages) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
+  constexpr int NT = SPLIT3 ? 2 : 1;  // operand copies per stage
+  const uint32_t b_bytes = (uint32_t)g.nchunk * B_CHUNK;
+  const uint32_t stage_bytes = NT * (A_TILE + b_bytes);
+  __shared__ uint64_t full[8], empty[8], tfull[2], tempty[2];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int c = blockIdx.x;
+  const long long u0 = su0(c, g.W, g.G), u1 = su0(c + 1, g.W, g.G);
+  const int t_first = (int)(u0 / g.KB);
+  const int t_last = (int)((u1 - 1) / g.KB);
+
+  if (warp == 1) {
+    tmem_alloc(&tslot, 2 * g.NA);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmX);
+    if (SPLIT3) {
+      tma_prefetch_desc(&tmA2);
+      tma_prefetch_desc(&tmX2);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    int it = 0;
+    for (int t = t_first; t <= t_last && !abort_flag; ++t) {
+      const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
+      const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
+      const int m0 = t * 128;
+      for (int kb = kb_lo; kb < kb_hi; ++kb, ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)(it / stages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          set_status(g.st, RSVD_E_TIMEOUT);
+          abort_flag = 1;
+          break;
+        }
+        unsigned char* sA = sm + (size_t)s * stage_bytes;
+        unsigned char* sB = sA + NT * A_TILE;
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
+        const int k0 = kb * 64;
+        if (!TRANS) {
+          tma_load_2d(sA, &tmA, k0, m0, &full[s]);
+        } else {
+          tma_load_2d(sA, &tmA, m0, k0, &full[s]);
+          tma_load_2d(sA + 8192, &tmA, m0 + 64, k0, &full[s]);
+          if (SPLIT3) {
+            tma_load_2d(sA + A_TILE, &tmA2, m0, k0, &full[s]);
+            tma_load_2d(sA + A_TILE + 8192, &tmA2, m0 + 64, k0, &full[s]);
+          }
+        }
+        for (int ch = 0; ch < g.nchunk; ++ch) {
+          tma_load_2d(sB + ch * B_CHUNK, &tmX, 64 * ch, k0, &full[s]);
+          if (SPLIT3) tma_load_2d(sB + b_bytes + ch * B_CHUNK, &tmX2, 64 * ch, k0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    const uint32_t idesc = idesc_bf16(128, g.Npad, TRANS ? 1 : 0, 1);
+    int it = 0, j = 0;
+    bool ok = true;
+    for (int t = t_first; t <= t_last && ok; ++t, ++j) {
+      const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
+      const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
+      const int acc = j & 1;
+      const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+      if (!mbar_wait(&tempty[acc], aph ^ 1u)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t dtm = tbase + (uint32_t)(acc * g.NA);
+      for (int kb = kb_lo; kb < kb_hi; ++kb, ++it) {
+        const int s = it % stages;
+        const uint32_t ph = (uint32_t)(it / stages) & 1u;
+        if (!mbar_wait(&full[s], ph)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t aA = smem_u32(sm + (size_t)s * stage_bytes);
+        const uint32_t aB = aA + NT * A_TILE;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t ad = TRANS ? umma_desc(aA + 2048 * k, 8192, 1024) : umma_desc(aA + 32 * k, 16, 1024);
+          const uint64_t bd = umma_desc(aB + 2048 * k, 8192, 1024);
+          const uint32_t accum = (kb > kb_lo || k > 0) ? 1u : 0u;
+          mma_bf16(dtm, ad, bd, idesc, accum);
+          if (SPLIT3) {
+            const uint64_t ad2 = umma_desc(aA + A_TILE + 2048 * k, 8192, 1024);
+            const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
+            mma_bf16(dtm, ad, bd2, idesc, 1u);   // Ah^T Xl
+            mma_bf16(dtm, ad2, bd, idesc, 1u);   // Al^T Xh
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      if (!ok) break;
+      mma_commit(&tfull[acc]);
+    }
+    if (!ok) {
+      set_status(g.st, RSVD_E_TIMEOUT);
+      abort_flag = 1;
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp % 4;
+    const int r = 32 * q + lane;
+    int j = 0;
+    for (int t = t_first; t <= t_last; ++t, ++j) {
+      const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
+      const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
+      const int acc = j & 1;
+      const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+      if (!mbar_wait(&tfull[acc], aph)) {
+        set_status(g.st, RSVD_E_TIMEOUT);
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const bool whole = (kb_lo == 0 && kb_hi == g.KB);
+      const int row = t * 128 + r;
+      float* dst;
+      bool store = true;
+      if (whole) {
+        dst = g.Y + (size_t)row * g.ldy;
+        store = row < g.M;
+      } else {
+        const int slot = (t == t_first) ? 0 : 1;
+        dst = g.part + (((size_t)c * 2 + slot) * 128 + r) * g.Npad;
+      }
+      const uint32_t taddr = tbase + (uint32_t)(acc * g.NA) + ((uint32_t)(32 * q) << 16);
+      for (int c16 = 0; c16 < g.Npad; c16 += 16) {
+        uint32_t v[16];
+        tmem_ld16(taddr + c16, v);
+        tmem_wait_ld();
+        if (store) {
+          if (whole) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (c16 + e < g.N) dst[c16 + e] = __uint_as_float(v[e]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; e += 4)
+              *reinterpret_cast<float4*>(dst + c16 + e) = make_float4(
+                  __uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+    }
+  }
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // best effort: let copies and MMAs already issued land before freeing smem/TMEM
+    for (int s = 0; s < stages; ++s) {
+      mbar_wait(&full[s], 0, 100000000ull);
+      mbar_wait(&full[s], 1, 100000000ull);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 2 * g.NA);
+  }
+}
+
+// Adds the partial tiles of tiles whose k-blocks were split between CTAs, in
+// CTA order.
+__global__ void tc_fixup_kernel(TcArgs g) {
+  const int t = blockIdx.x;
+  const long long ub = (long long)t * g.KB, ue = ub + g.KB - 1;
+  auto cta_of = [&](long long u) {
+    long long c = (u * g.G) / g.W;
+    while (c + 1 < g.G && su0(c + 1, g.W, g.G) <= u) ++c;
+    while (c > 0 && su0(c, g.W, g.G) > u) --c;
+    return (int)c;
+  };
+  const int cf = cta_of(ub), cl = cta_of(ue);
+  if (cf == cl) return;
+  for (int e = threadIdx.x; e < 128 * g.N; e += blockDim.x) {
+    const int r = e / g.N, col = e % g.N;
+    const int row = t * 128 + r;
+    if (row >= g.M) continue;
+    float s = 0.f;
+    for (int cc = cf; cc <= cl; ++cc) {
+      const int tf = (int)(su0(cc, g.W, g.G) / g.KB);
+      const int slot = (t == tf) ? 0 : 1;
+      s += g.part[(((size_t)cc * 2 + slot) * 128 + r) * g.Npad + col];
+    }
+    g.Y[(size_t)row * g.ldy + col] = s;
+  }
+}
+
+// -------------------------------------------------------------- host side --
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static bool get_encode() {
+  if (g_encode) return true;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return false;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return true;
+}
+
+// bf16 row-major matrix (rows x cols, ld elements) as a 2-D map with a
+// (box_in x box_out) box and 128-byte swizzle.
+static bool make_map(CUtensorMap* m, const void* ptr, int cols, int rows, int ld, int box_in, int box_out) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_in, (cuuint32_t)box_out};
+  cuuint32_t es[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int pow2_at_least(int v) {
+  int p = 32;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+size_t tc_gemm_workspace(int M, int N, int K, int sms) {
+  const int KB = ceil_div(K, 64), T = ceil_div(M, 128);
+  const long long W = (long long)T * KB;
+  const int G = (int)(W < sms ? W : sms);
+  const int Npad = ceil_div(N, 16) * 16;
+  return (size_t)G * 2 * 128 * Npad * sizeof(float);
+}
+
+bool tc_supported(int N) { return N >= 1 && N <= 256; }
+
+cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                           const __nv_bfloat16* A2, const __nv_bfloat16* X, int ldx, const __nv_bfloat16* X2, float* Y,
+                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  if (!get_encode()) return cudaErrorNotSupported;
+  if ((lda % 8) || (ldx % 8) || (((uintptr_t)A | (uintptr_t)X) & 15)) return cudaErrorInvalidValue;
+  TcArgs g;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.KB = ceil_div(K, 64);
+  g.T = ceil_div(M, 128);
+  g.W = (long long)g.T * g.KB;
+  g.G = (int)(g.W < sms ? g.W : sms);
+  g.Npad = ceil_div(N, 16) * 16;
+  g.NA = pow2_at_least(g.Npad);
+  g.nchunk = ceil_div(N, 64);
+  g.Y = Y;
+  g.ldy = ldy;
+  g.part = part;
+  g.st = st;
+  CUtensorMap mA, mA2, mX, mX2;
+  bool ok = true;
+  if (!trans)
+    ok &= make_map(&mA, A, K, M, lda, 64, 128);  // A: M x K row-major
+  else
+    ok &= make_map(&mA, A, M, K, lda, 64, 64);   // A: K x M row-major
+  ok &= make_map(&mX, X, N, K, ldx, 64, 64);     // X: K x N row-major
+  if (split3) {
+    ok &= make_map(&mA2, A2, M, K, lda, 64, 64);
+    ok &= make_map(&mX2, X2, N, K, ldx, 64, 64);
+  } else {
+    mA2 = mA;
+    mX2 = mX;
+  }
+  if (!ok) return cudaErrorInvalidValue;
+  const int NT = split3 ? 2 : 1;
+  const size_t stage_bytes = (size_t)NT * (A_TILE + (size_t)g.nchunk * B_CHUNK);
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return cudaErrorInvalidValue;
+  const size_t smem = stages * stage_bytes + 1024;
+  cudaError_t e;
+  if (!trans) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<false, false><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);
+    note_launch();
+  } else if (!split3) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<true, false><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);
+    note_launch();
+  } else {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<true, true><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);
+    note_launch();
+  }
+  tc_fixup_kernel<<<g.T, 256, 0, s>>>(g);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- converts --
+// A (fp32, rows x cols, lda) -> Ah = bf16(A), Al = bf16(A - Ah) (ld = ldb).
+__global__ void split_bf16_kernel(int rows, int cols, const float* __restrict__ A, int lda,
+                                  __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb) {
+  const long long total = (long long)rows * cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    const float a = A[(size_t)r * lda + c];
+    const __nv_bfloat16 h = __float2bfloat16_rn(a);
+    Ah[(size_t)r * ldb + c] = h;
+    if (Al) Al[(size_t)r * ldb + c] = __float2bfloat16_rn(a - __bfloat162float(h));
+  }
+}
+
+// Vectorized variant for cols % 4 == 0, lda % 4 == 0, ldb % 4 == 0.
+__global__ void split_bf16_vec_kernel(int rows, int cols, const float* __restrict__ A, int lda,
+                                      __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb) {
+  const int c4 = cols / 4;
+  const long long total = (long long)rows * c4;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / c4), c = (int)(e % c4) * 4;
+    const float4 a = *reinterpret_cast<const float4*>(A + (size_t)r * lda + c);
+    __nv_bfloat162 h01 = __floats2bfloat162_rn(a.x, a.y), h23 = __floats2bfloat162_rn(a.z, a.w);
+    uint2 hv;
+    hv.x = *reinterpret_cast<uint32_t*>(&h01);
+    hv.y = *reinterpret_cast<uint32_t*>(&h23);
+    *reinterpret_cast<uint2*>(Ah + (size_t)r * ldb + c) = hv;
+    if (Al) {
+      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+      __nv_bfloat162 l01 = __floats2bfloat162_rn(a.x - f01.x, a.y - f01.y);
+      __nv_bfloat162 l23 = __floats2bfloat162_rn(a.z - f23.x, a.w - f23.y);
+      uint2 lv;
+      lv.x = *reinterpret_cast<uint32_t*>(&l01);
+      lv.y = *reinterpret_cast<uint32_t*>(&l23);
+      *reinterpret_cast<uint2*>(Al + (size_t)r * ldb + c) = lv;
+    }
+  }
+}
+
+void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb,
+                       int sms, cudaStream_t s) {
+  if ((long long)rows * cols == 0) return;
+  const bool vec = (cols % 4 == 0) && (lda % 4 == 0) && (ldb % 4 == 0) && (((uintptr_t)A & 15) == 0);
+  const int blocks = sms * 8;
+  if (vec)
+    split_bf16_vec_kernel<<<blocks, 256, 0, s>>>(rows, cols, A, lda, Ah, Al, ldb);
+  else
+    split_bf16_kernel<<<blocks, 256, 0, s>>>(rows, cols, A, lda, Ah, Al, ldb);
+  note_launch();
+}
+
+}  // namespace rsvd

@@ -1,0 +1,56 @@
+// Launch wrappers shared between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace rsvd {
+
+// k_gauss.cu
+void launch_philox_words(int n_groups, int l, uint64_t seed, uint32_t stream_id, int col0, uint32_t* out,
+                         cudaStream_t s);
+void launch_gaussian(int n, int l, uint64_t seed, uint32_t stream_id, int col0, int dtype, void* out, int ldo,
+                     cudaStream_t s);
+
+// k_gemm.cu
+int simt_splits(int M, int N, int K, int sms);
+size_t simt_gemm_workspace(int M, int N, int K, int sms, size_t elem);
+template <typename T>
+void launch_gemm_simt(bool trans, int M, int N, int K, const T* A, int lda, const T* X, int ldx, T* Y, int ldy,
+                      T* partial, int sms, cudaStream_t s);
+
+// k_orth.cu
+int gram_splits(int rows, int l, int sms);
+template <typename T>
+void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, int sms, const int* gate,
+                 cudaStream_t s);
+size_t chol_smem_bytes(int l, size_t csize);
+size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize);
+template <typename T, typename C>
+void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws, DevStatus* st,
+              int sms, cudaStream_t s);
+template <typename T>
+void launch_copy_bf16(int rows, int l, const T* Y, int ldy, __nv_bfloat16* Yb, int lb, cudaStream_t s);
+void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const int* gate, int copy_if_gated,
+                    cudaStream_t s);
+
+// k_svd.cu
+int jacobi_cluster_size(int l);
+size_t jacobi_smem_bytes(int l, size_t csize);
+template <typename C>
+cudaError_t launch_jacobi(int l, const double* Rb, C* Wt, C* Jt, double* sigma, DevStatus* st, cudaStream_t s);
+template <typename C>
+void launch_sort_gather(int l, int kk, const double* sigma, const C* Wt, const C* Jt, double* D, C* Wsel, C* Jsel,
+                        cudaStream_t s);
+template <typename T>
+void launch_sign_fix(int m, int n, int kk, T* U, int ldu, T* V, int ldv, cudaStream_t s);
+
+// k_tc.cu
+size_t tc_gemm_workspace(int M, int N, int K, int sms);
+bool tc_supported(int N);
+cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                           const __nv_bfloat16* A2, const __nv_bfloat16* X, int ldx, const __nv_bfloat16* X2, float* Y,
+                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s);
+void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb,
+                       int sms, cudaStream_t s);
+
+}  // namespace rsvd

@@ -1,0 +1,614 @@
+// C ABI of the randomized-SVD library: argument checks, workspace layout and
+// the order of kernel launches on the caller's stream.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct rsvd_handle_s {
+  int device;
+  int sms;
+  char err[512];
+  // profiling: event pairs bracketing tensor-core products, per kind
+  bool profile;
+  std::vector<cudaEvent_t> pool;                     // free events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[2];
+};
+
+namespace rsvd {
+namespace {
+
+rsvd_status fail(rsvd_handle_t h, rsvd_status code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+rsvd_status check_launch(rsvd_handle_t h, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  return RSVD_OK;
+}
+
+int max_l_for(int prec) { return prec == RSVD_F64 ? 128 : 256; }
+
+size_t elem_size(int prec) { return prec == RSVD_F64 ? sizeof(double) : sizeof(float); }
+
+// ------------------------------------------------------ fixed-rank layout --
+struct FixedLayout {
+  DevStatus* st;
+  void* Om;      // n x l
+  void* Ybuf;    // m x l  (Y, then Q)
+  void* Zbuf;    // n x l  (Z, W, B^T, Q_B)
+  void* part;    // split-K partials
+  void* orthws;  // orth scratch
+  double* Rb;    // l x l
+  void* Wt;      // l x l
+  void* Jt;      // l x l
+  double* sigma; // l
+  void* Wsel;    // l x kk
+  void* Jsel;    // l x kk
+  size_t bytes;
+};
+
+FixedLayout fixed_layout(void* ws, int m, int n, int l, int kk, int prec, int sms) {
+  const size_t es = elem_size(prec);
+  Carver c(ws);
+  FixedLayout L;
+  L.st = c.take<DevStatus>(1);
+  L.Om = c.take<unsigned char>((size_t)n * l * es);
+  L.Ybuf = c.take<unsigned char>((size_t)m * l * es);
+  L.Zbuf = c.take<unsigned char>((size_t)n * l * es);
+  size_t pw = simt_gemm_workspace(m, l, n, sms, es);
+  const size_t pw2 = simt_gemm_workspace(n, l, m, sms, es);
+  if (pw2 > pw) pw = pw2;
+  L.part = c.take<unsigned char>(pw);
+  size_t ow = orth_workspace_bytes(m, l, sms, es);
+  const size_t ow2 = orth_workspace_bytes(n, l, sms, es);
+  if (ow2 > ow) ow = ow2;
+  L.orthws = c.take<unsigned char>(ow);
+  L.Rb = c.take<double>((size_t)l * l);
+  L.Wt = c.take<unsigned char>((size_t)l * l * es);
+  L.Jt = c.take<unsigned char>((size_t)l * l * es);
+  L.sigma = c.take<double>((size_t)l);
+  L.Wsel = c.take<unsigned char>((size_t)l * kk * es);
+  L.Jsel = c.take<unsigned char>((size_t)l * kk * es);
+  L.bytes = c.size();
+  return L;
+}
+
+rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda, const rsvd_params* p,
+                           const void* U, int ldu, const void* D, const void* V, int ldv, int* kk_out) {
+  if (!h) return RSVD_E_INVALID;
+  if (!p) return fail(h, RSVD_E_INVALID, "params is NULL");
+  if (m < 0 || n < 0) return fail(h, RSVD_E_INVALID, "negative size m=%d n=%d", m, n);
+  if (p->k < 0 || p->p < 0 || p->q < 0) return fail(h, RSVD_E_INVALID, "k, p, q must be >= 0");
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16)
+    return fail(h, RSVD_E_UNSUPPORTED, "precision %d is not implemented", p->prec);
+  const int l = p->k + p->p;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
+  *kk_out = kk;
+  if (p->k == 0) return RSVD_OK;
+  const int mn = m < n ? m : n;
+  if (l > mn) return fail(h, RSVD_E_INVALID, "l = k + p = %d exceeds min(m, n) = %d", l, mn);
+  if (l > max_l_for(p->prec))
+    return fail(h, RSVD_E_UNSUPPORTED, "l = %d exceeds the supported maximum %d", l, max_l_for(p->prec));
+  if (lda < n) return fail(h, RSVD_E_INVALID, "lda %d < n %d", lda, n);
+  if (ldu < kk || ldv < kk) return fail(h, RSVD_E_INVALID, "ldu/ldv smaller than the output rank %d", kk);
+  if (!A || !U || !D || !V) return fail(h, RSVD_E_INVALID, "NULL matrix pointer");
+  return RSVD_OK;
+}
+
+template <typename T, typename C>
+rsvd_status fixed_rank_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, const rsvd_params* p, T* U,
+                            int ldu, double* D, T* V, int ldv, const FixedLayout& L, cudaStream_t s) {
+  const int l = p->k + p->p;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
+  const int sms = h->sms;
+  T* Om = (T*)L.Om;
+  T* Y = (T*)L.Ybuf;
+  T* Z = (T*)L.Zbuf;
+  T* part = (T*)L.part;
+  const int dt = sizeof(T) == 8 ? RSVD_DT_F64 : RSVD_DT_F32;
+  // (1) G = randn(n, l)
+  launch_gaussian(n, l, p->seed, 0u, 0, dt, Om, l, s);
+  // (2) Q = orth(A G)
+  launch_gemm_simt<T>(false, m, l, n, A, lda, Om, l, Y, l, part, sms, s);
+  run_orth<T, C>(m, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  // (3-6) power steps with orth after every product
+  for (int j = 0; j < p->q; ++j) {
+    launch_gemm_simt<T>(true, n, l, m, A, lda, Y, l, Z, l, part, sms, s);
+    run_orth<T, C>(n, l, Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    launch_gemm_simt<T>(false, m, l, n, A, lda, Z, l, Y, l, part, sms, s);
+    run_orth<T, C>(m, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  }
+  // (7) B^T = A^T Q, then B^T = Q_B R_B
+  launch_gemm_simt<T>(true, n, l, m, A, lda, Y, l, Z, l, part, sms, s);
+  run_orth<T, C>(n, l, Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  // (8) SVD of R_B^T by one-sided Jacobi
+  cudaError_t e = launch_jacobi<C>(l, L.Rb, (C*)L.Wt, (C*)L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<C>(l, kk, L.sigma, (const C*)L.Wt, (const C*)L.Jt, D, (C*)L.Wsel, (C*)L.Jsel, s);
+  // (9) U = Q Uhat, V = Q_B J, truncated to kk; sign convention
+  launch_gemm_simt<T>(false, n, kk, l, Z, l, (const T*)L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_gemm_simt<T>(false, m, kk, l, Y, l, (const T*)L.Wsel, kk, U, ldu, nullptr, sms, s);
+  launch_sign_fix<T>(m, n, kk, U, ldu, V, ldv, s);
+  return check_launch(h, "rsvd_fixed_rank");
+}
+
+inline int round8(int v) { return (v + 7) / 8 * 8; }
+
+// ------------------------------------------------------------ mixed layout --
+struct MixedLayout {
+  DevStatus* st;
+  __nv_bfloat16* Ah;   // m x lda8: bf16(A)
+  __nv_bfloat16* Al;   // m x lda8: bf16(A - Ah)
+  __nv_bfloat16* Omb;  // n x l8
+  float* Y;            // m x l   (Y, then Q)
+  __nv_bfloat16* Yb;   // m x l8  bf16(Q)
+  __nv_bfloat16* Yl;   // m x l8  bf16(Q - bf16(Q))
+  float* Z;            // n x l   (Z, W, B^T, Q_B)
+  __nv_bfloat16* Zb;   // n x l8  bf16(W)
+  float* part;         // stream-K partials
+  void* orthws;
+  double* Rb;
+  float* Wt;
+  float* Jt;
+  double* sigma;
+  float* Wsel;
+  float* Jsel;
+  size_t bytes;
+};
+
+MixedLayout mixed_layout(void* ws, int m, int n, int l, int kk, int sms) {
+  Carver c(ws);
+  MixedLayout L;
+  const int n8 = round8(n), l8 = round8(l);
+  L.st = c.take<DevStatus>(1);
+  L.Ah = c.take<__nv_bfloat16>((size_t)m * n8);
+  L.Al = c.take<__nv_bfloat16>((size_t)m * n8);
+  L.Omb = c.take<__nv_bfloat16>((size_t)n * l8);
+  L.Y = c.take<float>((size_t)m * l);
+  L.Yb = c.take<__nv_bfloat16>((size_t)m * l8);
+  L.Yl = c.take<__nv_bfloat16>((size_t)m * l8);
+  L.Z = c.take<float>((size_t)n * l);
+  L.Zb = c.take<__nv_bfloat16>((size_t)n * l8);
+  size_t pw = tc_gemm_workspace(m, l, n, sms);
+  const size_t pw2 = tc_gemm_workspace(n, l, m, sms);
+  if (pw2 > pw) pw = pw2;
+  const size_t pw3 = simt_gemm_workspace(n, kk, l, sms, 4);
+  if (pw3 > pw) pw = pw3;
+  L.part = c.take<float>(pw / sizeof(float) + 1);
+  size_t ow = orth_workspace_bytes(m, l, sms, 4);
+  const size_t ow2 = orth_workspace_bytes(n, l, sms, 4);
+  if (ow2 > ow) ow = ow2;
+  L.orthws = c.take<unsigned char>(ow);
+  L.Rb = c.take<double>((size_t)l * l);
+  L.Wt = c.take<float>((size_t)l * l);
+  L.Jt = c.take<float>((size_t)l * l);
+  L.sigma = c.take<double>((size_t)l);
+  L.Wsel = c.take<float>((size_t)l * kk);
+  L.Jsel = c.take<float>((size_t)l * kk);
+  L.bytes = c.size();
+  return L;
+}
+
+cudaEvent_t prof_event(rsvd_handle_t h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one tensor-core product with events when profiling is on.
+struct ProfScope {
+  rsvd_handle_t h;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(rsvd_handle_t h_, int kind_, cudaStream_t s_) : h(h_), kind(kind_), s(s_) {
+    if (h->profile) {
+      e0 = prof_event(h);
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~ProfScope() {
+    if (e0) {
+      cudaEvent_t e1 = prof_event(h);
+      cudaEventRecord(e1, s);
+      h->rec[kind].push_back({e0, e1});
+    }
+  }
+};
+
+rsvd_status tc_call(rsvd_handle_t h, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return RSVD_OK;
+}
+
+// Mixed-precision fixed-rank path: bf16 tensor-core sketches with fp32
+// accumulation, binary64-accumulated Gram matrices, three-term split-bf16
+// projection B^T = A^T Q.
+rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int lda, const rsvd_params* p, float* U,
+                             int ldu, double* D, float* V, int ldv, const MixedLayout& L, cudaStream_t s) {
+  const int l = p->k + p->p;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
+  const int sms = h->sms;
+  const int n8 = round8(n), l8 = round8(l);
+  rsvd_status st;
+  // A = Ah + Al (bf16 pair); the sketches read Ah, the projection both
+  launch_split_bf16(m, n, A, lda, L.Ah, L.Al, n8, sms, s);
+  // (1) G = randn(n, l), bf16
+  launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_BF16, L.Omb, l8, s);
+  // (2) Q = orth(A G)
+  {
+    ProfScope ps(h, 0, s);
+    if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Omb, l8, nullptr, L.Y, l, L.part,
+                                        sms, L.st, s), "sketch A G")) != RSVD_OK)
+      return st;
+  }
+  run_orth<float, float>(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
+  // (3-6) power steps
+  for (int j = 0; j < p->q; ++j) {
+    {
+      ProfScope ps(h, 0, s);
+      if ((st = tc_call(h, launch_tc_gemm(true, false, n, l, m, L.Ah, n8, nullptr, L.Yb, l8, nullptr, L.Z, l,
+                                          L.part, sms, L.st, s), "sketch A^T Q")) != RSVD_OK)
+        return st;
+    }
+    run_orth<float, float>(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s);
+    {
+      ProfScope ps(h, 0, s);
+      if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Zb, l8, nullptr, L.Y, l,
+                                          L.part, sms, L.st, s), "sketch A W")) != RSVD_OK)
+        return st;
+    }
+    run_orth<float, float>(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
+  }
+  // (7) B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
+  launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);
+  {
+    ProfScope ps(h, 1, s);
+    if ((st = tc_call(h, launch_tc_gemm(true, true, n, l, m, L.Ah, n8, L.Al, L.Yb, l8, L.Yl, L.Z, l, L.part, sms,
+                                        L.st, s), "projection")) != RSVD_OK)
+      return st;
+  }
+  run_orth<float, float>(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  // (8) SVD of R_B^T
+  cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<float>(l, kk, L.sigma, L.Wt, L.Jt, D, L.Wsel, L.Jsel, s);
+  // (9) U = Q Uhat, V = Q_B J
+  launch_gemm_simt<float>(false, n, kk, l, L.Z, l, L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_gemm_simt<float>(false, m, kk, l, L.Y, l, L.Wsel, kk, U, ldu, nullptr, sms, s);
+  launch_sign_fix<float>(m, n, kk, U, ldu, V, ldv, s);
+  return check_launch(h, "rsvd_fixed_rank (mixed)");
+}
+
+rsvd_status finish_sync(rsvd_handle_t h, const rsvd_params* p, DevStatus* st, cudaStream_t s) {
+  if (!(p->flags & RSVD_FLAG_SYNC)) return RSVD_OK;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+  int code = 0;
+  e = cudaMemcpy(&code, &st->code, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "status read: %s", cudaGetErrorString(e));
+  if (code != 0) return fail(h, (rsvd_status)code, "device reported status %d", code);
+  return RSVD_OK;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+using namespace rsvd;
+
+extern "C" {
+
+rsvd_status rsvd_create(rsvd_handle_t* handle, int device) {
+  if (!handle) return RSVD_E_INVALID;
+  *handle = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return RSVD_E_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) return RSVD_E_CUDA;
+  rsvd_handle_s* h = new (std::nothrow) rsvd_handle_s();
+  if (!h) return RSVD_E_NOMEM;
+  h->device = device;
+  h->err[0] = 0;
+  h->profile = false;
+  if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete h;
+    return RSVD_E_CUDA;
+  }
+  *handle = h;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_destroy(rsvd_handle_t handle) {
+  if (!handle) return RSVD_OK;
+  for (auto e : handle->pool) cudaEventDestroy(e);
+  for (auto& r : handle->rec)
+    for (auto& pr : r) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  delete handle;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_kernel_launches(rsvd_handle_t handle, long long* count) {
+  if (!handle || !count) return RSVD_E_INVALID;
+  *count = launch_counter().load();
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_profile(rsvd_handle_t handle, int on) {
+  if (!handle) return RSVD_E_INVALID;
+  handle->profile = on != 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_profile_read(rsvd_handle_t handle, int kind, double* total_ms, long long* launches) {
+  if (!handle || kind < 0 || kind > 1 || !total_ms || !launches) return RSVD_E_INVALID;
+  double tot = 0.0;
+  long long cnt = 0;
+  for (auto& pr : handle->rec[kind]) {
+    if (cudaEventSynchronize(pr.second) != cudaSuccess) return fail(handle, RSVD_E_CUDA, "profile event");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pr.first, pr.second);
+    tot += ms;
+    ++cnt;
+    handle->pool.push_back(pr.first);
+    handle->pool.push_back(pr.second);
+  }
+  handle->rec[kind].clear();
+  *total_ms = tot;
+  *launches = cnt;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_last_error_detail(rsvd_handle_t handle, char* buf, size_t len) {
+  if (!handle || !buf || len == 0) return RSVD_E_INVALID;
+  strncpy(buf, handle->err, len - 1);
+  buf[len - 1] = 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_params* params, size_t* bytes) {
+  if (!handle || !params || !bytes) return RSVD_E_INVALID;
+  int kk = 0;
+  rsvd_status st = validate_fixed(handle, m, n, (const void*)1, n, params, (const void*)1, 1 << 30,
+                                  (const void*)1, (const void*)1, 1 << 30, &kk);
+  if (st != RSVD_OK) return st;
+  const int l = params->k + params->p;
+  if (params->prec == RSVD_MIXED_BF16)
+    *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes;
+  else
+    *bytes = fixed_layout(nullptr, m, n, l, kk, params->prec, handle->sms).bytes;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, int lda, const rsvd_params* params,
+                            void* U, int ldu, double* D, void* V, int ldv, void* workspace, size_t ws_bytes,
+                            rsvd_stream_t stream) {
+  int kk = 0;
+  rsvd_status st = validate_fixed(handle, m, n, A, lda, params, U, ldu, D, V, ldv, &kk);
+  if (st != RSVD_OK) return st;
+  if (params->k == 0) return RSVD_OK;
+  const int l = params->k + params->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t need = 0;
+  st = rsvd_workspace_size(handle, m, n, params, &need);
+  if (st != RSVD_OK) return st;
+  if (!workspace || ws_bytes < need)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  if (params->prec == RSVD_MIXED_BF16) {
+    if (((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
+    const MixedLayout M = mixed_layout(workspace, m, n, l, kk, handle->sms);
+    cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
+    st = fixed_rank_mixed(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, s);
+    if (st != RSVD_OK) return st;
+    return finish_sync(handle, params, M.st, s);
+  }
+  const FixedLayout L = fixed_layout(workspace, m, n, l, kk, params->prec, handle->sms);
+  cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
+  if (params->prec == RSVD_F64)
+    st = fixed_rank_simt<double, double>(handle, m, n, (const double*)A, lda, params, (double*)U, ldu, D,
+                                         (double*)V, ldv, L, s);
+  else
+    st = fixed_rank_simt<float, float>(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V,
+                                       ldv, L, s);
+  if (st != RSVD_OK) return st;
+  return finish_sync(handle, params, L.st, s);
+}
+
+rsvd_status rsvd_adaptive_tol(rsvd_handle_t handle, int m, int n, const void* A, int lda, const rsvd_params* params,
+                              void* U, int ldu, double* D, void* V, int ldv, int* rank_out, double* err_out,
+                              void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
+  (void)m; (void)n; (void)A; (void)lda; (void)params; (void)U; (void)ldu; (void)D; (void)V; (void)ldv;
+  (void)rank_out; (void)err_out; (void)workspace; (void)ws_bytes; (void)stream;
+  return fail(handle, RSVD_E_UNSUPPORTED, "rsvd_adaptive_tol is not built yet");
+}
+
+rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status, rsvd_stream_t stream) {
+  if (!handle || !workspace || !status) return RSVD_E_INVALID;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(status, &((const DevStatus*)workspace)->code, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "status read: %s", cudaGetErrorString(e));
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_philox_words(rsvd_handle_t handle, int n_groups, int l, uint64_t seed, uint32_t stream_id, int col0,
+                              uint32_t* out, rsvd_stream_t stream) {
+  if (!handle) return RSVD_E_INVALID;
+  if (n_groups < 0 || l < 0 || col0 < 0) return fail(handle, RSVD_E_INVALID, "negative size");
+  if ((long long)n_groups * l > 0 && !out) return fail(handle, RSVD_E_INVALID, "NULL output");
+  launch_philox_words(n_groups, l, seed, stream_id, col0, out, (cudaStream_t)stream);
+  return check_launch(handle, "rsvd_philox_words");
+}
+
+rsvd_status rsvd_gaussian(rsvd_handle_t handle, int n, int l, uint64_t seed, uint32_t stream_id, int col0, int dtype,
+                          void* out, int ldo, rsvd_stream_t stream) {
+  if (!handle) return RSVD_E_INVALID;
+  if (n < 0 || l < 0 || col0 < 0) return fail(handle, RSVD_E_INVALID, "negative size");
+  if (dtype != RSVD_DT_F64 && dtype != RSVD_DT_F32 && dtype != RSVD_DT_BF16)
+    return fail(handle, RSVD_E_INVALID, "unknown dtype %d", dtype);
+  if (ldo < l) return fail(handle, RSVD_E_INVALID, "ldo %d < l %d", ldo, l);
+  if ((long long)n * l > 0 && !out) return fail(handle, RSVD_E_INVALID, "NULL output");
+  launch_gaussian(n, l, seed, stream_id, col0, dtype, out, ldo, (cudaStream_t)stream);
+  return check_launch(handle, "rsvd_gaussian");
+}
+
+rsvd_status rsvd_sketch_workspace_size(rsvd_handle_t handle, int prec, int trans, int m, int n, int l, size_t* bytes) {
+  if (!handle || !bytes || m < 0 || n < 0 || l < 0) return RSVD_E_INVALID;
+  const int M = trans ? n : m, K = trans ? m : n;
+  if (prec == RSVD_F64 || prec == RSVD_F32)
+    *bytes = simt_gemm_workspace(M, l, K, handle->sms, elem_size(prec)) + 512;
+  else if (prec == RSVD_MIXED_BF16)
+    *bytes = tc_gemm_workspace(M, l, K, handle->sms) + 512;
+  else
+    return fail(handle, RSVD_E_UNSUPPORTED, "precision %d is not built yet", prec);
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_sketch(rsvd_handle_t handle, int prec, int trans, int m, int n, int l, const void* A, int lda,
+                        const void* X, int ldx, void* Y, int ldy, void* workspace, size_t ws_bytes,
+                        rsvd_stream_t stream) {
+  if (!handle) return RSVD_E_INVALID;
+  if (m < 0 || n < 0 || l < 0) return fail(handle, RSVD_E_INVALID, "negative size");
+  const int M = trans ? n : m, K = trans ? m : n;
+  if (lda < n || ldx < l || ldy < l) return fail(handle, RSVD_E_INVALID, "leading dimension too small");
+  if ((long long)M * l == 0) return RSVD_OK;
+  if (!A || !X || !Y) return fail(handle, RSVD_E_INVALID, "NULL matrix pointer");
+  size_t need = 0;
+  rsvd_status st = rsvd_sketch_workspace_size(handle, prec, trans, m, n, l, &need);
+  if (st != RSVD_OK) return st;
+  if (need > 512 && (!workspace || ws_bytes < need))
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == RSVD_MIXED_BF16) {
+    if (l > 256) return fail(handle, RSVD_E_UNSUPPORTED, "l = %d > 256", l);
+    if ((lda % 8) || (ldx % 8) || (((uintptr_t)A | (uintptr_t)X) & 15))
+      return fail(handle, RSVD_E_INVALID, "bf16 operands need 16-byte aligned rows (lda, ldx multiples of 8)");
+    Carver c(workspace);
+    DevStatus* dst = c.take<DevStatus>(1);
+    float* part = c.take<float>(tc_gemm_workspace(M, l, K, handle->sms) / sizeof(float) + 1);
+    cudaMemsetAsync(dst, 0, sizeof(DevStatus), s);
+    cudaError_t e = launch_tc_gemm(trans != 0, false, M, l, K, (const __nv_bfloat16*)A, lda, nullptr,
+                                   (const __nv_bfloat16*)X, ldx, nullptr, (float*)Y, ldy, part, handle->sms, dst, s);
+    if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_sketch: %s", cudaGetErrorString(e));
+    return check_launch(handle, "rsvd_sketch");
+  }
+  if (prec == RSVD_F64)
+    launch_gemm_simt<double>(trans != 0, M, l, K, (const double*)A, lda, (const double*)X, ldx, (double*)Y, ldy,
+                             (double*)workspace, handle->sms, s);
+  else
+    launch_gemm_simt<float>(trans != 0, M, l, K, (const float*)A, lda, (const float*)X, ldx, (float*)Y, ldy,
+                            (float*)workspace, handle->sms, s);
+  return check_launch(handle, "rsvd_sketch");
+}
+
+rsvd_status rsvd_project_workspace_size(rsvd_handle_t handle, int prec, int m, int n, int l, size_t* bytes) {
+  if (!handle || !bytes || m < 0 || n < 0 || l < 0) return RSVD_E_INVALID;
+  Carver c(nullptr);
+  c.take<DevStatus>(1);
+  if (prec == RSVD_MIXED_BF16) {
+    c.take<__nv_bfloat16>((size_t)2 * m * round8(n));
+    c.take<__nv_bfloat16>((size_t)2 * m * round8(l));
+    c.take<unsigned char>(tc_gemm_workspace(n, l, m, handle->sms));
+  } else if (prec == RSVD_F64 || prec == RSVD_F32) {
+    c.take<unsigned char>(simt_gemm_workspace(n, l, m, handle->sms, elem_size(prec)));
+  } else {
+    return fail(handle, RSVD_E_UNSUPPORTED, "precision %d", prec);
+  }
+  *bytes = c.size();
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_project(rsvd_handle_t handle, int prec, int m, int n, int l, const void* A, int lda, const void* Q,
+                         int ldq, void* Bt, int ldb, void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
+  if (!handle) return RSVD_E_INVALID;
+  if (m < 0 || n < 0 || l < 0) return fail(handle, RSVD_E_INVALID, "negative size");
+  if (lda < n || ldq < l || ldb < l) return fail(handle, RSVD_E_INVALID, "leading dimension too small");
+  if ((long long)n * l == 0) return RSVD_OK;
+  if (!A || !Q || !Bt) return fail(handle, RSVD_E_INVALID, "NULL matrix pointer");
+  size_t need = 0;
+  rsvd_status st = rsvd_project_workspace_size(handle, prec, m, n, l, &need);
+  if (st != RSVD_OK) return st;
+  if (!workspace || ws_bytes < need) return fail(handle, RSVD_E_NOMEM, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver c(workspace);
+  DevStatus* dst = c.take<DevStatus>(1);
+  cudaMemsetAsync(dst, 0, sizeof(DevStatus), s);
+  if (prec == RSVD_MIXED_BF16) {
+    if (l > 256) return fail(handle, RSVD_E_UNSUPPORTED, "l = %d > 256", l);
+    const int n8 = round8(n), l8 = round8(l);
+    __nv_bfloat16* Ah = c.take<__nv_bfloat16>((size_t)m * n8);
+    __nv_bfloat16* Al = c.take<__nv_bfloat16>((size_t)m * n8);
+    __nv_bfloat16* Qh = c.take<__nv_bfloat16>((size_t)m * l8);
+    __nv_bfloat16* Ql = c.take<__nv_bfloat16>((size_t)m * l8);
+    float* part = c.take<float>(tc_gemm_workspace(n, l, m, handle->sms) / sizeof(float) + 1);
+    launch_split_bf16(m, n, (const float*)A, lda, Ah, Al, n8, handle->sms, s);
+    launch_split_bf16(m, l, (const float*)Q, ldq, Qh, Ql, l8, handle->sms, s);
+    cudaError_t e = launch_tc_gemm(true, true, n, l, m, Ah, n8, Al, Qh, l8, Ql, (float*)Bt, ldb, part, handle->sms,
+                                   dst, s);
+    if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_project: %s", cudaGetErrorString(e));
+  } else if (prec == RSVD_F64) {
+    launch_gemm_simt<double>(true, n, l, m, (const double*)A, lda, (const double*)Q, ldq, (double*)Bt, ldb,
+                             c.take<double>(simt_gemm_workspace(n, l, m, handle->sms, 8) / 8 + 1), handle->sms, s);
+  } else {
+    launch_gemm_simt<float>(true, n, l, m, (const float*)A, lda, (const float*)Q, ldq, (float*)Bt, ldb,
+                            c.take<float>(simt_gemm_workspace(n, l, m, handle->sms, 4) / 4 + 1), handle->sms, s);
+  }
+  return check_launch(handle, "rsvd_project");
+}
+
+rsvd_status rsvd_orth_workspace_size(rsvd_handle_t handle, int prec, int rows, int l, size_t* bytes) {
+  if (!handle || !bytes || rows < 0 || l < 0) return RSVD_E_INVALID;
+  if (prec != RSVD_F64 && prec != RSVD_F32) return fail(handle, RSVD_E_UNSUPPORTED, "precision %d", prec);
+  Carver c(nullptr);
+  c.take<DevStatus>(1);
+  c.take<unsigned char>(orth_workspace_bytes(rows, l, handle->sms, elem_size(prec)));
+  *bytes = c.size();
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_orth(rsvd_handle_t handle, int prec, int rows, int l, void* Y, int ldy, double* R, void* workspace,
+                      size_t ws_bytes, rsvd_stream_t stream) {
+  if (!handle) return RSVD_E_INVALID;
+  if (rows < 0 || l < 0) return fail(handle, RSVD_E_INVALID, "negative size");
+  if (l == 0) return RSVD_OK;
+  if (l > rows) return fail(handle, RSVD_E_INVALID, "l = %d exceeds rows = %d", l, rows);
+  if (l > max_l_for(prec)) return fail(handle, RSVD_E_UNSUPPORTED, "l = %d too large", l);
+  if (ldy < l) return fail(handle, RSVD_E_INVALID, "ldy %d < l %d", ldy, l);
+  if (!Y) return fail(handle, RSVD_E_INVALID, "NULL Y");
+  size_t need = 0;
+  rsvd_status st = rsvd_orth_workspace_size(handle, prec, rows, l, &need);
+  if (st != RSVD_OK) return st;
+  if (!workspace || ws_bytes < need) return fail(handle, RSVD_E_NOMEM, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver c(workspace);
+  DevStatus* dst = c.take<DevStatus>(1);
+  void* ows = c.take<unsigned char>(orth_workspace_bytes(rows, l, handle->sms, elem_size(prec)));
+  cudaMemsetAsync(dst, 0, sizeof(DevStatus), s);
+  if (prec == RSVD_F64)
+    run_orth<double, double>(rows, l, (double*)Y, ldy, R, nullptr, 0, ows, dst, handle->sms, s);
+  else
+    run_orth<float, float>(rows, l, (float*)Y, ldy, R, nullptr, 0, ows, dst, handle->sms, s);
+  return check_launch(handle, "rsvd_orth");
+}
+
+}  // extern "C"

@@ -266,6 +266,7 @@ def run_ours(a):
         raise rs.RsvdError(st, "device status after timing")
     ms_per_step = ms / a.steps
     value = world * a.steps / (ms / 1000.0)
+    diag = rs.status_block(ws)
 
     # ---- accuracy of the last solve (not timed): singular values against the
     # construction sigma_j = j^-1.5, Frobenius residual in float64 blockwise
@@ -370,7 +371,10 @@ def run_ours(a):
                        "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB)" % (m * n * 4 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "error": err, "plain_f32": f32}
+            "error": err, "plain_f32": f32,
+            "diagnostics": {"jacobi_sweeps_last_solve": diag["jacobi_sweeps"],
+                            "shifted_cholesky_last_solve": diag["shift_count"],
+                            "sketch_launches_timed": sk_n, "projection_launches_timed": pj_n}}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -203,6 +203,15 @@ def rsvd_orth(h, prec, rows, l, Y, ldy, R, ws, stream=None):
                             _stream(stream))
 
 
+def status_block(ws):
+    """Diagnostic fields of the device status block at the start of a workspace:
+    code, CholeskyQR shift flag, Jacobi sweeps of the last small SVD, number
+    of shifted Cholesky factorizations."""
+    import numpy as np
+    raw = ws[:32].cpu().numpy().view(np.int32)
+    return {"code": int(raw[0]), "shifted": int(raw[1]), "jacobi_sweeps": int(raw[3]), "shift_count": int(raw[6])}
+
+
 def rsvd_project_workspace_size(h, prec, m, n, l):
     out = ctypes.c_size_t()
     _check(load().rsvd_project_workspace_size(h, prec, m, n, l, ctypes.byref(out)), h)

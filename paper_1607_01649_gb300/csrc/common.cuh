@@ -20,7 +20,8 @@ struct DevStatus {
   int jacobi_sweeps;
   int rank;         // adaptive: current rank
   int done;         // adaptive: tolerance met / loop finished
-  int pad[2];
+  int shift_count;  // Cholesky factorizations that needed a diagonal shift
+  int pad;
   double fro2_a;    // adaptive: ||A||_Fro^2
   double fro2_res;  // adaptive: ||A_j||_Fro^2 of the current remainder
   double scratch[6];

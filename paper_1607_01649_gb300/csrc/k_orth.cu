@@ -185,11 +185,13 @@ __global__ void __launch_bounds__(1024)
   const double tau = 1024.0 * u;
   const double s0 = 16384.0 * u;
 
+  C* rdc = diag + l;  // 1 / d_i in the working precision
   bool bad = false;
   for (int i = tid; i < l; i += nt) {
     const double gii = G[(size_t)i * l + i];
     if (!isfinite(gii)) bad = true;
     d[i] = gii > 0.0 ? sqrt(gii) : 1.0;
+    rdc[i] = (C)(1.0 / d[i]);
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -204,13 +206,15 @@ __global__ void __launch_bounds__(1024)
   int attempt = 0;
   for (;;) {
     const int npk = l * (l + 1) / 2;
+    // unit-diagonal scaling Gt = D^-1 G D^-1 in the working precision (a
+    // binary64 divide per entry would cost more than the factorization here)
     for (int e = tid; e < l * l; e += nt) {
       const int i = e / l, j = e % l;
       if (i < j) continue;
-      double v = G[(size_t)i * l + j] / (d[i] * d[j]);
-      if (i == j) v += shift;
-      if (!isfinite(v)) v = 0.0;
-      a[pk(l, i, j)] = (C)v;
+      C v = (C)G[(size_t)i * l + j] * rdc[i] * rdc[j];
+      if (i == j) v += (C)shift;
+      if (!isfinite(v)) v = C(0);
+      a[pk(l, i, j)] = v;
     }
     (void)npk;
     if (tid == 0) s_fail = 0;
@@ -226,11 +230,24 @@ __global__ void __launch_bounds__(1024)
       const C rp = C(1) / piv;
       for (int i = k + 1 + tid; i < l; i += nt) a[pk(l, i, k)] *= rp;
       __syncthreads();
-      // trailing update: columns j in (k, l), rows i in [j, l)
+      // trailing update a(i, j) -= l(i, k) l(j, k) for k < j <= i < l.  Lane
+      // owns rows i = lane + 32 r (r < 8); its multipliers l(i, k) are loaded
+      // once, then each column of the warp is updated with 8 independent FMAs.
+      C lik[8];
+      const int ck = pk(l, k, k);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = lane + 32 * r;
+        lik[r] = (i > k && i < l) ? a[ck + (i - k)] : C(0);
+      }
       for (int j = k + 1 + warp; j < l; j += nw) {
-        const C ljk = a[pk(l, j, k)];
-        const int cj = pk(l, j, j), ck = pk(l, j, k);
-        for (int i = j + lane; i < l; i += 32) a[cj + (i - j)] -= a[ck + (i - j)] * ljk;
+        const C ljk = a[ck + (j - k)];
+        const int cj = pk(l, j, j);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int i = lane + 32 * r;
+          if (i >= j && i < l) a[cj + (i - j)] -= lik[r] * ljk;
+        }
       }
       __syncthreads();
     }
@@ -249,42 +266,49 @@ __global__ void __launch_bounds__(1024)
       st->shifted = shift > 0.0 ? 1 : 0;
     else if (shift > 0.0)
       st->shifted = 1;
+    if (shift > 0.0) atomicAdd(&st->shift_count, 1);
   }
   // outputs
   for (int e = tid; e < l * l; e += nt) {
     const int i = e / l, j = e % l;  // R[i][j] = Lt[j][i] d_j for i <= j
-    double v = 0.0;
-    if (i < j)
-      v = (double)a[pk(l, j, i)] * d[j];
-    else if (i == j)
-      v = (double)diag[i] * d[i];
-    R[e] = v;
+    if (R) {
+      C v = C(0);
+      if (i < j)
+        v = a[pk(l, j, i)] * (C)d[j];
+      else if (i == j)
+        v = diag[i] * (C)d[i];
+      R[e] = (double)v;
+    }
     if (i <= j) {
       const int off = i * l - (i * (i - 1)) / 2 + (j - i);  // packed row-major upper
       Ut[off] = (i == j) ? diag[i] : a[pk(l, j, i)];
     }
   }
-  for (int i = tid; i < l; i += nt) dinv[i] = (C)(1.0 / d[i]);
+  for (int i = tid; i < l; i += nt) dinv[i] = rdc[i];
 }
 
 size_t chol_smem_bytes(int l, size_t csize) {
   return (((size_t)l * (l + 1) / 2 * csize + 15) & ~(size_t)15) + (size_t)l * sizeof(double) +
-         (size_t)l * csize;
+         (size_t)2 * l * csize;
 }
 
 // ----------------------------------------------------------------- apply --
-// In place: each warp takes whole rows y; ytilde = y * dinv; solves
-// q Lt^T = ytilde by forward substitution (lanes own columns c = lane + 32 t).
+// In place: each warp takes RW rows y at a time; ytilde = y * dinv; solves
+// q Lt^T = ytilde by forward substitution (lanes own columns c = lane + 32 t;
+// the RW independent rows give the warp RW-way instruction-level parallelism).
 // Optionally writes a bf16 copy of Q (row-major, ld = lb).
 template <typename T, typename C, int NT>
 __global__ void __launch_bounds__(1024)
     apply_kernel(int rows, int l, T* __restrict__ Y, int ldy, const C* __restrict__ Ut,
                  const C* __restrict__ dinv, __nv_bfloat16* __restrict__ Ybf, int lb, const int* gate) {
   if (gate && *gate == 0) return;
+  constexpr int RW = 4;
   extern __shared__ unsigned char smem_raw[];
   C* u = reinterpret_cast<C*>(smem_raw);
+  C* rdiag = u + (size_t)l * (l + 1) / 2;
   const int npk = l * (l + 1) / 2;
   for (int e = threadIdx.x; e < npk; e += blockDim.x) u[e] = Ut[e];
+  for (int c = threadIdx.x; c < l; c += blockDim.x) rdiag[c] = C(1) / Ut[c * l - (c * (c - 1)) / 2];
   __syncthreads();
   const int lane = threadIdx.x % 32;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -295,42 +319,57 @@ __global__ void __launch_bounds__(1024)
     const int c = lane + 32 * t;
     dv[t] = c < l ? dinv[c] : C(0);
   }
-  for (int r = gw; r < rows; r += nwarps) {
-    T* y = Y + (size_t)r * ldy;
-    C s[NT];
+  for (int r0 = gw * RW; r0 < rows; r0 += nwarps * RW) {
+    C s[RW][NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int c = lane + 32 * t;
-      s[t] = c < l ? (C)y[c] * dv[t] : C(0);
+    for (int w = 0; w < RW; ++w) {
+      const int r = r0 + w;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int c = lane + 32 * t;
+        s[w][t] = (r < rows && c < l) ? (C)Y[(size_t)r * ldy + c] * dv[t] : C(0);
+      }
     }
-    // column c: q_c = s_c / Ut[c][c]; then s_c' -= q_c Ut[c][c'] for c' > c
     int off = 0;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       for (int cl = 0; cl < 32; ++cl) {
         const int c = 32 * t + cl;
         if (c >= l) break;
-        C qc = C(0);
-        if (lane == cl) {
-          qc = s[t] / u[off];
-          s[t] = qc;
+        const C rd = rdiag[c];
+        C qc[RW];
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+          C v = C(0);
+          if (lane == cl) {
+            v = s[w][t] * rd;
+            s[w][t] = v;
+          }
+          qc[w] = __shfl_sync(0xffffffffu, v, cl);
         }
-        qc = __shfl_sync(0xffffffffu, qc, cl);
-        // update the columns after c
 #pragma unroll
         for (int t2 = 0; t2 < NT; ++t2) {
           const int c2 = lane + 32 * t2;
-          if (t2 >= t && c2 > c && c2 < l) s[t2] -= qc * u[off + (c2 - c)];
+          if (t2 >= t && c2 > c && c2 < l) {
+            const C uc = u[off + (c2 - c)];
+#pragma unroll
+            for (int w = 0; w < RW; ++w) s[w][t2] -= qc[w] * uc;
+          }
         }
         off += l - c;
       }
     }
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int c = lane + 32 * t;
-      if (c < l) {
-        y[c] = (T)s[t];
-        if (Ybf) Ybf[(size_t)r * lb + c] = __float2bfloat16_rn((float)s[t]);
+    for (int w = 0; w < RW; ++w) {
+      const int r = r0 + w;
+      if (r >= rows) continue;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int c = lane + 32 * t;
+        if (c < l) {
+          Y[(size_t)r * ldy + c] = (T)s[w][t];
+          if (Ybf) Ybf[(size_t)r * lb + c] = __float2bfloat16_rn((float)s[w][t]);
+        }
       }
     }
   }
@@ -339,7 +378,7 @@ __global__ void __launch_bounds__(1024)
 template <typename T, typename C>
 void launch_apply(int rows, int l, T* Y, int ldy, const C* Ut, const C* dinv, __nv_bfloat16* Ybf, int lb,
                   int sms, const int* gate, cudaStream_t s) {
-  const size_t smem = (size_t)l * (l + 1) / 2 * sizeof(C);
+  const size_t smem = ((size_t)l * (l + 1) / 2 + l) * sizeof(C);
   const int threads = 1024;
   const int blocks = sms;
 #define RSVD_APPLY(NTV)                                                                              \
@@ -419,7 +458,7 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
   for (int pass = 1; pass <= 3; ++pass) {
     const int* gate = pass == 3 ? gate3 : nullptr;
     launch_gram<T>(rows, l, Y, ldy, P, G, sms, gate, s);
-    launch_chol<C>(l, G, Ut, dinv, Rp + (size_t)(pass - 1) * l * l, st, pass, gate, s);
+    launch_chol<C>(l, G, Ut, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s);
     launch_apply<T, C>(rows, l, Y, ldy, Ut, dinv, nullptr, lb, sms, gate, s);
   }
   if (Ybf) launch_copy_bf16<T>(rows, l, Y, ldy, Ybf, lb, s);

@@ -93,11 +93,23 @@ __global__ void __launch_bounds__(512)
       const int par = (sweep * (P - 1) + r) & 1;
       C* top = buf + (size_t)(2 * par) * blk;
       C* bot = buf + (size_t)(2 * par + 1) * blk;
-      // ---- local sweep over the 2w columns (circle method on 2w players)
+      // ---- local sweep.  Round 0 of a sweep visits every pair of the 2w
+      // columns (circle method on 2w players), which covers the pairs inside
+      // each block once per sweep; the other rounds visit only the w*w pairs
+      // across the two blocks (step s pairs top i with bottom (i + s) mod w).
       const int Q2 = 2 * w;
-      for (int step = 0; step < Q2 - 1; ++step) {
+      const bool full_round = (r == 0);
+      const int nsteps = full_round ? Q2 - 1 : w;
+      for (int step = 0; step < nsteps; ++step) {
         for (int pr = warp; pr < w; pr += nwarps) {
-          const int ia = rr_pos(pr, step, Q2), ib = rr_pos(Q2 - 1 - pr, step, Q2);
+          int ia, ib;
+          if (full_round) {
+            ia = rr_pos(pr, step, Q2);
+            ib = rr_pos(Q2 - 1 - pr, step, Q2);
+          } else {
+            ia = pr;
+            ib = w + (pr + step) % w;
+          }
           C* xa = (ia < w ? top : bot) + (size_t)(ia % w) * l;
           C* xb = (ib < w ? top : bot) + (size_t)(ib % w) * l;
           C* ja = xa + (size_t)w * l;
@@ -109,30 +121,23 @@ __global__ void __launch_bounds__(512)
             be = fma(b, b, be);
             ga = fma(a, b, ga);
           }
+          // xor butterflies leave the identical sums in every lane (each level
+          // adds the same two operands, only swapped), so the rotation
+          // decision below is warp-uniform without a broadcast
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             al += __shfl_xor_sync(0xffffffffu, al, o);
             be += __shfl_xor_sync(0xffffffffu, be, o);
             ga += __shfl_xor_sync(0xffffffffu, ga, o);
           }
-          // lane 0 forms the rotation in binary64 and broadcasts it
-          int rot = 0;
-          C c = C(1), s = C(0);
-          if (lane == 0) {
-            const double A = (double)al, B = (double)be, G = (double)ga;
-            if (A > 0.0 && B > 0.0 && fabs(G) > tol * sqrt(A * B)) {
-              const double zeta = (B - A) / (2.0 * G);
-              const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-              const double cs = 1.0 / sqrt(1.0 + t * t);
-              c = (C)cs;
-              s = (C)(cs * t);
-              rot = 1;
-            }
-          }
-          rot = __shfl_sync(0xffffffffu, rot, 0);
-          if (rot) {
-            c = __shfl_sync(0xffffffffu, c, 0);
-            s = __shfl_sync(0xffffffffu, s, 0);
+          if (al > C(0) && be > C(0) && fabs(ga) > (C)tol * sqrt(al * be)) {
+            // Rutishauser's formulas: zeta = (beta - alpha) / (2 gamma),
+            // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
+            const C zeta = (be - al) / (C(2) * ga);
+            const C az = fabs(zeta);
+            const C t = (az > C(1e15) ? C(0.5) / az : C(1) / (az + sqrt(C(1) + zeta * zeta))) *
+                        (zeta >= C(0) ? C(1) : C(-1));
+            const C c = C(1) / sqrt(C(1) + t * t), s = c * t;
             for (int i = lane; i < l; i += 32) {
               const C a = xa[i], b = xb[i];
               xa[i] = c * a - s * b;
@@ -161,7 +166,21 @@ __global__ void __launch_bounds__(512)
           const int slot = pos_now < NC ? 0 : 1;
           C* src = cluster.map_shared_rank(buf + (size_t)(2 * par + slot) * blk, holder);
           C* dst = half == 0 ? ntop : nbot;
-          for (size_t e = tid; e < blk; e += blockDim.x) dst[e] = src[e];
+          // 16-byte remote loads, four in flight per thread
+          const size_t nv = blk * sizeof(C) / 16;
+          const float4* s4 = reinterpret_cast<const float4*>(src);
+          float4* d4 = reinterpret_cast<float4*>(dst);
+          size_t e = tid;
+          for (; e + 3 * blockDim.x < nv; e += 4 * blockDim.x) {
+            const float4 v0 = s4[e], v1 = s4[e + blockDim.x], v2 = s4[e + 2 * blockDim.x],
+                         v3 = s4[e + 3 * blockDim.x];
+            d4[e] = v0;
+            d4[e + blockDim.x] = v1;
+            d4[e + 2 * blockDim.x] = v2;
+            d4[e + 3 * blockDim.x] = v3;
+          }
+          for (; e < nv; e += blockDim.x) d4[e] = s4[e];
+          for (size_t x = nv * 16 / sizeof(C) + tid; x < blk; x += blockDim.x) dst[x] = src[x];
         }
         cluster.sync();
       } else {
@@ -269,12 +288,20 @@ __global__ void sort_gather_kernel(int l, int kk, const double* __restrict__ sig
   // a strict total order and the ranks form a permutation of 0..l-1.
   for (int i = threadIdx.x; i < l; i += blockDim.x) sperm[i] = i;
   __syncthreads();
+  // Keys: the IEEE bit patterns of the (non-negative) sigmas order like the
+  // values; NaN maps to -1.  Integer compares avoid binary64 arithmetic.
+  __shared__ long long key[512];
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
-    const double si = isnan(sigma[i]) ? -INFINITY : sigma[i];
+    const double v = sigma[i];
+    key[i] = (v >= 0.0) ? __double_as_longlong(v) : -1LL;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    const long long ki = key[i];
     int rank = 0;
     for (int j = 0; j < l; ++j) {
-      const double sj = isnan(sigma[j]) ? -INFINITY : sigma[j];
-      rank += (sj > si) || (sj == si && j < i);
+      const long long kj = key[j];
+      rank += (kj > ki) || (kj == ki && j < i);
     }
     sperm[rank] = i;
   }
@@ -304,71 +331,75 @@ template void launch_sort_gather<double>(int, int, const double*, const double*,
                                          double*, cudaStream_t);
 
 // ------------------------------------------------------------------ signs --
-// For column c of V (rows x kk, ldv): the entry of largest magnitude (lowest
-// index on ties) is made positive; U's column c gets the same sign.
+// Sign convention: for column c of V (n x kk, ldv) the entry of largest
+// magnitude (lowest row index on ties) is made positive, and U's column c gets
+// the same sign.  Pass 1: each CTA scans a chunk of rows (coalesced along the
+// row) and writes the per-column (|v|, row) maximum of its chunk.  Pass 2:
+// per column, reduce the chunks, flip V's column if needed and record the
+// sign, which pass 3 (the U lift) applies by scaling the selected Uhat columns.
 template <typename T>
-__global__ void sign_fix_kernel(int m, int n, int kk, T* __restrict__ U, int ldu, T* __restrict__ V, int ldv) {
-  const int c = blockIdx.x;
+__global__ void colmax_partial_kernel(int n, int kk, const T* __restrict__ V, int ldv, int rows_per,
+                                      float* __restrict__ pmax, int* __restrict__ pidx) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= kk) return;
-  __shared__ double smax[32];
-  __shared__ int sidx[32];
-  double best = -1.0;
+  const int r0 = blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+  float best = -1.f;
   int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double a = fabs((double)V[(size_t)i * ldv + c]);
+  for (int r = r0; r < r1; ++r) {
+    const float a = fabsf((float)V[(size_t)r * ldv + c]);
     if (a > best) {
       best = a;
-      bi = i;
+      bi = r;
     }
   }
-  // block arg-max with lowest-index tie break
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
-    }
-  }
-  if (lane == 0) {
-    smax[warp] = best;
-    sidx[warp] = bi;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x / 32;
-    best = lane < nw ? smax[lane] : -1.0;
-    bi = lane < nw ? sidx[lane] : 0x7fffffff;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    if (lane == 0) sidx[0] = bi;
-  }
-  __syncthreads();
-  const int imax = sidx[0];
-  if (imax >= n) return;
-  const bool flip = V[(size_t)imax * ldv + c] < T(0);
-  __syncthreads();
-  if (!flip) return;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)i * ldv + c] = -V[(size_t)i * ldv + c];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) U[(size_t)i * ldu + c] = -U[(size_t)i * ldu + c];
+  pmax[(size_t)blockIdx.x * kk + c] = best;
+  pidx[(size_t)blockIdx.x * kk + c] = bi;
 }
 
-template <typename T>
-void launch_sign_fix(int m, int n, int kk, T* U, int ldu, T* V, int ldv, cudaStream_t s) {
-  if (kk == 0) return;
-  sign_fix_kernel<T><<<kk, 256, 0, s>>>(m, n, kk, U, ldu, V, ldv);
+template <typename T, typename C>
+__global__ void colsign_kernel(int n, int kk, int chunks, const float* __restrict__ pmax, const int* __restrict__ pidx,
+                               T* __restrict__ V, int ldv, C* __restrict__ Wsel, int l) {
+  const int c = blockIdx.x;
+  __shared__ int s_flip;
+  if (threadIdx.x == 0) {
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    for (int z = 0; z < chunks; ++z) {
+      const float b = pmax[(size_t)z * kk + c];
+      const int i = pidx[(size_t)z * kk + c];
+      if (b > best || (b == best && i < bi)) {
+        best = b;
+        bi = i;
+      }
+    }
+    s_flip = (bi < n && V[(size_t)bi * ldv + c] < T(0)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_flip) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)i * ldv + c] = -V[(size_t)i * ldv + c];
+  for (int i = threadIdx.x; i < l; i += blockDim.x) Wsel[(size_t)i * kk + c] = -Wsel[(size_t)i * kk + c];
+}
+
+size_t sign_workspace_bytes(int n, int kk) {
+  const int chunks = (n + 255) / 256;
+  return (size_t)chunks * kk * (sizeof(float) + sizeof(int)) + 512;
+}
+
+template <typename T, typename C>
+void launch_sign_fix(int n, int kk, int l, T* V, int ldv, C* Wsel, void* ws, cudaStream_t s) {
+  if (kk == 0 || n == 0) return;
+  const int rows_per = 256;
+  const int chunks = (n + rows_per - 1) / rows_per;
+  float* pmax = (float*)ws;
+  int* pidx = (int*)((char*)ws + (((size_t)chunks * kk * sizeof(float) + 255) & ~(size_t)255));
+  const int tx = kk >= 128 ? 128 : 64;
+  dim3 grid(chunks, (kk + tx - 1) / tx);
+  colmax_partial_kernel<T><<<grid, tx, 0, s>>>(n, kk, V, ldv, rows_per, pmax, pidx);
+  note_launch();
+  colsign_kernel<T, C><<<kk, 256, 0, s>>>(n, kk, chunks, pmax, pidx, V, ldv, Wsel, l);
   note_launch();
 }
-template void launch_sign_fix<float>(int, int, int, float*, int, float*, int, cudaStream_t);
-template void launch_sign_fix<double>(int, int, int, double*, int, double*, int, cudaStream_t);
+template void launch_sign_fix<float, float>(int, int, int, float*, int, float*, void*, cudaStream_t);
+template void launch_sign_fix<double, double>(int, int, int, double*, int, double*, void*, cudaStream_t);
 
 }  // namespace rsvd

@@ -47,6 +47,7 @@ struct TcArgs {
 __host__ __device__ inline long long su0(long long c, long long W, int G) { return (c * W) / G; }
 
 constexpr int TC_THREADS = 192;
+constexpr int TC_MAX_CTAS = 256;  // persistent grid cap (>= #SMs of the part)
 constexpr uint32_t A_TILE = 16384;   // 128 x 64 bf16
 constexpr uint32_t B_CHUNK = 8192;   // 64 x 64 bf16
 
@@ -247,29 +248,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // Adds the partial tiles of tiles whose k-blocks were split between CTAs, in
-// CTA order.
+// CTA order.  One CTA per tile; tiles computed whole by one CTA return at once.
 __global__ void tc_fixup_kernel(TcArgs g) {
   const int t = blockIdx.x;
-  const long long ub = (long long)t * g.KB, ue = ub + g.KB - 1;
-  auto cta_of = [&](long long u) {
-    long long c = (u * g.G) / g.W;
-    while (c + 1 < g.G && su0(c + 1, g.W, g.G) <= u) ++c;
-    while (c > 0 && su0(c, g.W, g.G) > u) --c;
-    return (int)c;
-  };
-  const int cf = cta_of(ub), cl = cta_of(ue);
+  __shared__ int s_cf, s_cl, s_slot[TC_MAX_CTAS + 1];
+  if (threadIdx.x == 0) {
+    const long long ub = (long long)t * g.KB, ue = ub + g.KB - 1;
+    auto cta_of = [&](long long u) {
+      long long c = (u * g.G) / g.W;
+      while (c + 1 < g.G && su0(c + 1, g.W, g.G) <= u) ++c;
+      while (c > 0 && su0(c, g.W, g.G) > u) --c;
+      return (int)c;
+    };
+    s_cf = cta_of(ub);
+    s_cl = cta_of(ue);  // s_cl - s_cf < G <= TC_MAX_CTAS
+    for (int cc = s_cf; cc <= s_cl; ++cc) s_slot[cc - s_cf] = ((int)(su0(cc, g.W, g.G) / g.KB) == t) ? 0 : 1;
+  }
+  __syncthreads();
+  const int cf = s_cf, cl = s_cl;
   if (cf == cl) return;
-  for (int e = threadIdx.x; e < 128 * g.N; e += blockDim.x) {
-    const int r = e / g.N, col = e % g.N;
-    const int row = t * 128 + r;
-    if (row >= g.M) continue;
-    float s = 0.f;
-    for (int cc = cf; cc <= cl; ++cc) {
-      const int tf = (int)(su0(cc, g.W, g.G) / g.KB);
-      const int slot = (t == tf) ? 0 : 1;
-      s += g.part[(((size_t)cc * 2 + slot) * 128 + r) * g.Npad + col];
+  const int rows = min(128, g.M - t * 128);
+  for (int r = threadIdx.x / 32; r < rows; r += blockDim.x / 32) {
+    for (int col = threadIdx.x % 32; col < g.N; col += 32) {
+      float s = 0.f;
+      for (int cc = cf; cc <= cl; ++cc)
+        s += g.part[(((size_t)cc * 2 + s_slot[cc - cf]) * 128 + r) * g.Npad + col];
+      g.Y[(size_t)(t * 128 + r) * g.ldy + col] = s;
     }
-    g.Y[(size_t)row * g.ldy + col] = s;
   }
 }
 
@@ -308,7 +313,8 @@ static int pow2_at_least(int v) {
 size_t tc_gemm_workspace(int M, int N, int K, int sms) {
   const int KB = ceil_div(K, 64), T = ceil_div(M, 128);
   const long long W = (long long)T * KB;
-  const int G = (int)(W < sms ? W : sms);
+  int G = (int)(W < sms ? W : sms);
+  if (G > TC_MAX_CTAS) G = TC_MAX_CTAS;
   const int Npad = ceil_div(N, 16) * 16;
   return (size_t)G * 2 * 128 * Npad * sizeof(float);
 }
@@ -329,6 +335,7 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   g.T = ceil_div(M, 128);
   g.W = (long long)g.T * g.KB;
   g.G = (int)(g.W < sms ? g.W : sms);
+  if (g.G > TC_MAX_CTAS) g.G = TC_MAX_CTAS;
   g.Npad = ceil_div(N, 16) * 16;
   g.NA = pow2_at_least(g.Npad);
   g.nchunk = ceil_div(N, 64);

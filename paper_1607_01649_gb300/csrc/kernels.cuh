@@ -41,8 +41,9 @@ cudaError_t launch_jacobi(int l, const double* Rb, C* Wt, C* Jt, double* sigma, 
 template <typename C>
 void launch_sort_gather(int l, int kk, const double* sigma, const C* Wt, const C* Jt, double* D, C* Wsel, C* Jsel,
                         cudaStream_t s);
-template <typename T>
-void launch_sign_fix(int m, int n, int kk, T* U, int ldu, T* V, int ldv, cudaStream_t s);
+size_t sign_workspace_bytes(int n, int kk);
+template <typename T, typename C>
+void launch_sign_fix(int n, int kk, int l, T* V, int ldv, C* Wsel, void* ws, cudaStream_t s);
 
 // k_tc.cu
 size_t tc_gemm_workspace(int M, int N, int K, int sms);

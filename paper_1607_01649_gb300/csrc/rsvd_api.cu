@@ -71,6 +71,7 @@ FixedLayout fixed_layout(void* ws, int m, int n, int l, int kk, int prec, int sm
   size_t pw = simt_gemm_workspace(m, l, n, sms, es);
   const size_t pw2 = simt_gemm_workspace(n, l, m, sms, es);
   if (pw2 > pw) pw = pw2;
+  if (sign_workspace_bytes(n, kk) > pw) pw = sign_workspace_bytes(n, kk);
   L.part = c.take<unsigned char>(pw);
   size_t ow = orth_workspace_bytes(m, l, sms, es);
   const size_t ow2 = orth_workspace_bytes(n, l, sms, es);
@@ -140,8 +141,8 @@ rsvd_status fixed_rank_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, 
   launch_sort_gather<C>(l, kk, L.sigma, (const C*)L.Wt, (const C*)L.Jt, D, (C*)L.Wsel, (C*)L.Jsel, s);
   // (9) U = Q Uhat, V = Q_B J, truncated to kk; sign convention
   launch_gemm_simt<T>(false, n, kk, l, Z, l, (const T*)L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_sign_fix<T, C>(n, kk, l, V, ldv, (C*)L.Wsel, L.part, s);
   launch_gemm_simt<T>(false, m, kk, l, Y, l, (const T*)L.Wsel, kk, U, ldu, nullptr, sms, s);
-  launch_sign_fix<T>(m, n, kk, U, ldu, V, ldv, s);
   return check_launch(h, "rsvd_fixed_rank");
 }
 
@@ -187,6 +188,7 @@ MixedLayout mixed_layout(void* ws, int m, int n, int l, int kk, int sms) {
   if (pw2 > pw) pw = pw2;
   const size_t pw3 = simt_gemm_workspace(n, kk, l, sms, 4);
   if (pw3 > pw) pw = pw3;
+  if (sign_workspace_bytes(n, kk) > pw) pw = sign_workspace_bytes(n, kk);
   L.part = c.take<float>(pw / sizeof(float) + 1);
   size_t ow = orth_workspace_bytes(m, l, sms, 4);
   const size_t ow2 = orth_workspace_bytes(n, l, sms, 4);
@@ -293,8 +295,8 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
   launch_sort_gather<float>(l, kk, L.sigma, L.Wt, L.Jt, D, L.Wsel, L.Jsel, s);
   // (9) U = Q Uhat, V = Q_B J
   launch_gemm_simt<float>(false, n, kk, l, L.Z, l, L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_sign_fix<float, float>(n, kk, l, V, ldv, L.Wsel, L.part, s);
   launch_gemm_simt<float>(false, m, kk, l, L.Y, l, L.Wsel, kk, U, ldu, nullptr, sms, s);
-  launch_sign_fix<float>(m, n, kk, U, ldu, V, ldv, s);
   return check_launch(h, "rsvd_fixed_rank (mixed)");
 }
 

@@ -105,9 +105,11 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// G[i][j] = sum over splits (fixed order) of the upper-triangular partials.
+// G[i][j] = sum over splits (fixed order) of the upper-triangular partials;
+// Gf receives G rounded to binary32 (the Cholesky kernel's input on the
+// binary32 path; converting here spreads the binary64 conversions over the GPU).
 __global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__ P, double* __restrict__ G,
-                                   const int* gate) {
+                                   float* __restrict__ Gf, const int* gate) {
   if (gate && *gate == 0) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= l * l) return;
@@ -121,6 +123,7 @@ __global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__
   double s = 0.0;
   for (int z = 0; z < splits; ++z) s += P[(size_t)z * l * l + (size_t)i * l + j];
   G[idx] = s;
+  if (Gf) Gf[idx] = (float)s;
 }
 
 int gram_splits(int rows, int l, int sms) {
@@ -135,7 +138,7 @@ int gram_splits(int rows, int l, int sms) {
 }
 
 template <typename T>
-void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, int sms, const int* gate,
+void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
                  cudaStream_t s) {
   const int nb = ceil_div(l, GT);
   const int tiles = nb * (nb + 1) / 2;
@@ -144,7 +147,7 @@ void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, int
   const int used = ceil_div(rows, rps);
   gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate);
   note_launch();
-  gram_reduce_kernel<<<ceil_div(l * l, 256), 256, 0, s>>>(l, used, P, G, gate);
+  gram_reduce_kernel<<<ceil_div(l * l, 256), 256, 0, s>>>(l, used, P, G, Gf, gate);
   note_launch();
 }
 
@@ -163,35 +166,106 @@ struct Eps<double> {
   static constexpr double u = 1.1102230246251565e-16;  // 2^-53
 };
 
-// Single CTA.  In:  G (l x l binary64).  Out:
-//   Ut : packed row-major upper triangle of Lt^T (row r holds columns r..l-1), type C
-//   dinv : 1 / d (type C), d_i = sqrt(G_ii)
-//   R  : l x l row-major binary64, R = Lt^T D (zeros below the diagonal)
-// Pivots below tau (unit-diagonal scale) restart the factorization on Gt + s I,
-// s = s0, 32 s0, ...; four failures give RSVD_E_BREAKDOWN.
+// Single CTA of 1024 threads.  In: G (l x l binary64) and Gf (G rounded to
+// binary32, used on the binary32 path).  Out:
+//   Ub   : l x l row-major, type C: the upper triangular factor Lt^T whose
+//          32 x 32 diagonal blocks are replaced by their inverses; with
+//          dinv it defines Q = (Y D^-1) Lt^-T (blocked triangular solve)
+//   dinv : 1 / d_i, d_i = sqrt(G_ii)
+//   R    : optional l x l row-major binary64, R = Lt^T D (zeros below the diagonal)
+// where G = D Gt D and Gt = Lt Lt^T.  Pivots below tau (unit-diagonal scale)
+// restart the factorization on Gt + s I, s = s0, 32 s0, ...; four failures
+// give RSVD_E_BREAKDOWN.
+//
+// Factorization: blocked right-looking on 32-column panels.  For each panel:
+//   (b) the 32 x 32 diagonal block is factored by warp 0, lane i holding row i
+//       in registers (pivot columns broadcast by shuffles);
+//   (c) the rows below are solved against it, one thread per row;
+//   (d) the trailing lower triangle is updated, A22 -= L21 L21^T, by all
+//       threads in 4 x 4 register tiles.
+// Finally the diagonal blocks are inverted, one warp per block.
+
+// Warp-level Cholesky of a w x w block held as rows (lane i: row[0..31] =
+// A(i, 0..31), lower part valid).  On return row[] holds row i of L.  Returns
+// false (warp-uniformly) on a pivot below tau.
 template <typename C>
-__global__ void __launch_bounds__(1024)
-    chol_kernel(int l, const double* __restrict__ G, C* __restrict__ Ut, C* __restrict__ dinv,
-                double* __restrict__ R, DevStatus* st, int pass, const int* gate) {
+__device__ __forceinline__ bool warp_chol32(C (&row)[32], int w, C tau) {
+  const int lane = threadIdx.x % 32;
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    if (q < w && ok) {  // warp-uniform; no break, so q stays a compile-time index
+      const C akk = __shfl_sync(0xffffffffu, row[q], q);
+      if (!(akk > tau) || !isfinite(akk)) {
+        ok = false;
+      } else {
+        const C piv = sqrt(akk), rp = C(1) / piv;
+        const C liq = (lane == q) ? piv : (lane > q ? row[q] * rp : C(0));
+        row[q] = liq;
+        // row i -= l(i, q) * l(j, q) for q < j <= i
+#pragma unroll
+        for (int j = q + 1; j < 32; ++j) {
+          const C ljq = __shfl_sync(0xffffffffu, liq, j);
+          if (lane >= j) row[j] = fma(-liq, ljq, row[j]);
+        }
+      }
+    }
+  }
+  return ok;
+}
+
+// Warp-level inverse of the lower triangular w x w diagonal block at
+// (c0, c0) of the packed factor.  Lane i ends with x[] = row i of L^-1.
+// x doubles as the accumulator: lanes i > k add L(i, k) X(k, :) at step k,
+// when lane k turns its accumulator into its final row.
+template <typename C>
+__device__ __forceinline__ void warp_trinv32(const C* a, const int* cb, int c0, int w, C (&x)[32]) {
+  const int lane = threadIdx.x % 32;
+  const int i = c0 + lane;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) x[c] = C(0);
+  const C rd = (lane < w) ? C(1) / a[cb[i] + i] : C(0);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k >= w) continue;  // warp-uniform; keeps k a compile-time index
+    if (lane == k) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = ((c == k ? C(1) : C(0)) - x[c]) * rd;
+    }
+    const C lik = (lane > k && lane < w) ? a[cb[c0 + k] + i] : C(0);
+#pragma unroll
+    for (int c = 0; c <= k; ++c) {
+      const C xkc = __shfl_sync(0xffffffffu, x[c], k);
+      if (lane > k) x[c] = fma(lik, xkc, x[c]);
+    }
+  }
+}
+
+template <typename C, int NT>
+__global__ void __launch_bounds__(NT)
+    chol_kernel(int l, const double* __restrict__ G, const float* __restrict__ Gf, C* __restrict__ Ub,
+                C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate) {
   if (gate && *gate == 0) return;
   extern __shared__ unsigned char smem_raw[];
-  C* a = reinterpret_cast<C*>(smem_raw);                    // packed lower, l(l+1)/2
+  C* a = reinterpret_cast<C*>(smem_raw);  // packed lower, l(l+1)/2
   double* d = reinterpret_cast<double*>(smem_raw + (((size_t)l * (l + 1) / 2 * sizeof(C) + 15) & ~15));
-  C* diag = reinterpret_cast<C*>(d + l);
+  C* rdiag = reinterpret_cast<C*>(d + l);
+  C* rdc = rdiag + l;
+  int* cb = reinterpret_cast<int*>(rdc + l);  // pk(i, j) = cb[j] + i
   __shared__ int s_fail;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
+  const int warp = tid / 32, lane = tid % 32;
   const double u = Eps<C>::u;
-  const double tau = 1024.0 * u;
+  const C ctau = (C)(1024.0 * u);
   const double s0 = 16384.0 * u;
 
-  C* rdc = diag + l;  // 1 / d_i in the working precision
   bool bad = false;
   for (int i = tid; i < l; i += nt) {
     const double gii = G[(size_t)i * l + i];
     if (!isfinite(gii)) bad = true;
     d[i] = gii > 0.0 ? sqrt(gii) : 1.0;
     rdc[i] = (C)(1.0 / d[i]);
+    cb[i] = i * l - (i * (i - 1)) / 2 - i;
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -202,54 +276,107 @@ __global__ void __launch_bounds__(1024)
     return;
   }
 
-  double shift = 0.0;
+  C shift = C(0);
   int attempt = 0;
   for (;;) {
-    const int npk = l * (l + 1) / 2;
     // unit-diagonal scaling Gt = D^-1 G D^-1 in the working precision (a
-    // binary64 divide per entry would cost more than the factorization here)
-    for (int e = tid; e < l * l; e += nt) {
-      const int i = e / l, j = e % l;
-      if (i < j) continue;
-      C v = (C)G[(size_t)i * l + j] * rdc[i] * rdc[j];
-      if (i == j) v += (C)shift;
-      if (!isfinite(v)) v = C(0);
-      a[pk(l, i, j)] = v;
+    // binary64 divide per entry would cost more than the factorization)
+    for (int j = warp; j < l; j += nt / 32) {
+      const int base = cb[j];
+      const C rj = rdc[j];
+      for (int i = j + lane; i < l; i += 32) {
+        C v = (sizeof(C) == 4 ? (C)Gf[(size_t)i * l + j] : (C)G[(size_t)i * l + j]) * rdc[i] * rj;
+        if (i == j) v += shift;
+        if (!isfinite(v)) v = C(0);
+        a[base + i] = v;
+      }
     }
-    (void)npk;
     if (tid == 0) s_fail = 0;
     __syncthreads();
-    for (int k = 0; k < l; ++k) {
-      const C akk = a[pk(l, k, k)];
-      if (!((double)akk > tau) || !isfinite((double)akk)) {  // uniform decision
-        if (tid == 0) s_fail = 1;
-        break;
-      }
-      const C piv = sqrt(akk);
-      if (tid == 0) diag[k] = piv;
-      const C rp = C(1) / piv;
-      for (int i = k + 1 + tid; i < l; i += nt) a[pk(l, i, k)] *= rp;
-      __syncthreads();
-      // trailing update a(i, j) -= l(i, k) l(j, k) for k < j <= i < l.  Lane
-      // owns rows i = lane + 32 r (r < 8); its multipliers l(i, k) are loaded
-      // once, then each column of the warp is updated with 8 independent FMAs.
-      C lik[8];
-      const int ck = pk(l, k, k);
+    for (int c0 = 0; c0 < l; c0 += 32) {
+      const int w = min(32, l - c0);
+      // (b) diagonal block
+      if (warp == 0) {
+        C row[32];
+        const int i = c0 + lane;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = lane + 32 * r;
-        lik[r] = (i > k && i < l) ? a[ck + (i - k)] : C(0);
-      }
-      for (int j = k + 1 + warp; j < l; j += nw) {
-        const C ljk = a[ck + (j - k)];
-        const int cj = pk(l, j, j);
+        for (int j = 0; j < 32; ++j) row[j] = (lane < w && j < w && j <= lane) ? a[cb[c0 + j] + i] : C(0);
+        const bool ok = warp_chol32<C>(row, w, ctau);
+        if (!ok) {
+          if (lane == 0) s_fail = 1;
+        } else if (lane < w) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int i = lane + 32 * r;
-          if (i >= j && i < l) a[cj + (i - j)] -= lik[r] * ljk;
+          for (int j = 0; j < 32; ++j)
+            if (j <= lane) a[cb[c0 + j] + i] = row[j];
+          C dii = C(1);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j == lane) dii = row[j];
+          rdiag[i] = C(1) / dii;
         }
       }
       __syncthreads();
+      if (s_fail) break;
+      // (c) rows below: x L11^T = a(i, c0 : c0 + w), thread per row
+      for (int i = c0 + w + tid; i < l; i += nt) {
+        C x[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) x[q] = q < w ? a[cb[c0 + q] + i] : C(0);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          if (q < w) {
+            x[q] *= rdiag[c0 + q];
+            const int bq = cb[c0 + q];
+#pragma unroll
+            for (int r2 = q + 1; r2 < 32; ++r2)
+              if (r2 < w) x[r2] = fma(-x[q], a[bq + c0 + r2], x[r2]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q < w) a[cb[c0 + q] + i] = x[q];
+      }
+      __syncthreads();
+      // (d) trailing update A22 -= L21 L21^T over the lower triangle, 4 x 4 tiles
+      const int t0 = c0 + w;
+      const int n2 = l - t0;
+      if (n2 > 0) {
+        const int nq = (n2 + 3) / 4;             // row/column quads
+        const int ntiles = nq * (nq + 1) / 2;    // lower-triangular tiles
+        for (int tI = tid; tI < ntiles; tI += nt) {
+          // tile index -> (rq, cq) with cq <= rq
+          int rq = (int)((sqrtf(8.0f * tI + 1.0f) - 1.0f) * 0.5f);
+          while ((rq + 1) * (rq + 2) / 2 <= tI) ++rq;
+          while (rq * (rq + 1) / 2 > tI) --rq;
+          const int cq = tI - rq * (rq + 1) / 2;
+          const int i0 = t0 + 4 * rq, j0 = t0 + 4 * cq;
+          C acc[4][4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = C(0);
+          for (int k = c0; k < c0 + w; ++k) {
+            const int base = cb[k];
+            C av[4], bv[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) av[x] = (i0 + x < l) ? a[base + i0 + x] : C(0);
+#pragma unroll
+            for (int y = 0; y < 4; ++y) bv[y] = (j0 + y < l) ? a[base + j0 + y] : C(0);
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              const int ii = i0 + x, jj = j0 + y;
+              if (ii < l && jj < l && ii >= jj) a[cb[jj] + ii] -= acc[x][y];
+            }
+        }
+        __syncthreads();
+      }
     }
     __syncthreads();
     if (s_fail == 0) break;
@@ -258,30 +385,37 @@ __global__ void __launch_bounds__(1024)
       if (tid == 0) set_status(st, RSVD_E_BREAKDOWN);
       return;
     }
-    shift = (shift == 0.0) ? s0 : shift * 32.0;
+    shift = (shift == C(0)) ? (C)s0 : shift * C(32);
     __syncthreads();
   }
   if (tid == 0) {
     if (pass == 1)
-      st->shifted = shift > 0.0 ? 1 : 0;
-    else if (shift > 0.0)
+      st->shifted = shift > C(0) ? 1 : 0;
+    else if (shift > C(0))
       st->shifted = 1;
-    if (shift > 0.0) atomicAdd(&st->shift_count, 1);
+    if (shift > C(0)) atomicAdd(&st->shift_count, 1);
   }
-  // outputs
-  for (int e = tid; e < l * l; e += nt) {
-    const int i = e / l, j = e % l;  // R[i][j] = Lt[j][i] d_j for i <= j
-    if (R) {
-      C v = C(0);
-      if (i < j)
-        v = a[pk(l, j, i)] * (C)d[j];
-      else if (i == j)
-        v = diag[i] * (C)d[i];
-      R[e] = (double)v;
+  // outputs, row i of Ub / R by warp, columns by lane: Lt^T[i][j] = L(j, i), j >= i
+  for (int i = warp; i < l; i += nt / 32) {
+    const int bi = i >> 5;
+    for (int j = lane; j < l; j += 32) {
+      const C v = (j >= i) ? a[cb[i] + j] : C(0);
+      if (R) R[(size_t)i * l + j] = (double)(v * (C)d[j]);
+      if (bi != (j >> 5)) Ub[(size_t)i * l + j] = v;
     }
-    if (i <= j) {
-      const int off = i * l - (i * (i - 1)) / 2 + (j - i);  // packed row-major upper
-      Ut[off] = (i == j) ? diag[i] : a[pk(l, j, i)];
+  }
+  // diagonal blocks of Ub: (L(bb, bb)^-1)^T, one warp per block
+  const int nb = (l + 31) / 32;
+  for (int bb = warp; bb < nb; bb += nt / 32) {
+    const int c0 = 32 * bb, w = min(32, l - c0);
+    const int i = c0 + lane;
+    C x[32];
+    warp_trinv32<C>(a, cb, c0, w, x);
+    // x = row `lane` of L^-1; Ub(c0 + c, c0 + lane) = L^-1(lane, c), i.e. column lane of the transposed inverse
+    if (lane < w) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < w) Ub[(size_t)(c0 + c) * l + c0 + lane] = x[c];
     }
   }
   for (int i = tid; i < l; i += nt) dinv[i] = rdc[i];
@@ -289,124 +423,122 @@ __global__ void __launch_bounds__(1024)
 
 size_t chol_smem_bytes(int l, size_t csize) {
   return (((size_t)l * (l + 1) / 2 * csize + 15) & ~(size_t)15) + (size_t)l * sizeof(double) +
-         (size_t)2 * l * csize;
+         (size_t)2 * l * csize + (size_t)l * sizeof(int);
 }
 
 // ----------------------------------------------------------------- apply --
-// In place: each warp takes RW rows y at a time; ytilde = y * dinv; solves
-// q Lt^T = ytilde by forward substitution (lanes own columns c = lane + 32 t;
-// the RW independent rows give the warp RW-way instruction-level parallelism).
-// Optionally writes a bf16 copy of Q (row-major, ld = lb).
-template <typename T, typename C, int NT>
-__global__ void __launch_bounds__(1024)
-    apply_kernel(int rows, int l, T* __restrict__ Y, int ldy, const C* __restrict__ Ut,
-                 const C* __restrict__ dinv, __nv_bfloat16* __restrict__ Ybf, int lb, const int* gate) {
+// In place Q = (Y D^-1) Lt^-T as a blocked triangular solve.  One CTA per
+// 64-row stripe, staged in shared memory before any row is rewritten.  For
+// each 32-column block b (in order), with the block's 32 rows of Ub streamed
+// into shared memory:
+//   r_b = ytilde_b - (sum over earlier blocks, held in registers)
+//   q_b = r_b Ub(b, b)                      (Ub(b, b) = inverse of the diagonal block)
+//   acc_c += q_b Ub(b, c) for later blocks c (each thread owns a 8 x 8 tile:
+//            rows ty + 8 x, columns tx + 32 y)
+// Optionally writes a bf16 copy of Q.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+    apply_kernel(int rows, int l, T* __restrict__ Y, int ldy, const C* __restrict__ Ub, const C* __restrict__ dinv,
+                 __nv_bfloat16* __restrict__ Ybf, int lb, const int* gate) {
   if (gate && *gate == 0) return;
-  constexpr int RW = 4;
   extern __shared__ unsigned char smem_raw[];
-  C* u = reinterpret_cast<C*>(smem_raw);
-  C* rdiag = u + (size_t)l * (l + 1) / 2;
-  const int npk = l * (l + 1) / 2;
-  for (int e = threadIdx.x; e < npk; e += blockDim.x) u[e] = Ut[e];
-  for (int c = threadIdx.x; c < l; c += blockDim.x) rdiag[c] = C(1) / Ut[c * l - (c * (c - 1)) / 2];
-  __syncthreads();
-  const int lane = threadIdx.x % 32;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int nwarps = gridDim.x * blockDim.x / 32;
-  C dv[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int c = lane + 32 * t;
-    dv[t] = c < l ? dinv[c] : C(0);
+  C* ys = reinterpret_cast<C*>(smem_raw);  // 64 x l
+  C* rs = ys + (size_t)64 * l;             // 32 x l rows of Ub
+  const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
+  const int r0 = blockIdx.x * 64;
+  const int nr = min(64, rows - r0);
+  for (int e = tid; e < 64 * l; e += 256) {
+    const int r = e / l, c = e % l;
+    ys[e] = (r < nr) ? (C)Y[(size_t)(r0 + r) * ldy + c] * dinv[c] : C(0);
   }
-  for (int r0 = gw * RW; r0 < rows; r0 += nwarps * RW) {
-    C s[RW][NT];
+  C acc[8][8];
 #pragma unroll
-    for (int w = 0; w < RW; ++w) {
-      const int r = r0 + w;
+  for (int x = 0; x < 8; ++x)
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int c = lane + 32 * t;
-        s[w][t] = (r < rows && c < l) ? (C)Y[(size_t)r * ldy + c] * dv[t] : C(0);
+    for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
+  const int nb = (l + 31) / 32;
+#pragma unroll 1
+  for (int b = 0; b < nb; ++b) {
+    const int k0 = 32 * b, kw = min(32, l - k0);
+    __syncthreads();  // previous block's reads of rs / ys are done
+    for (int e = tid; e < 32 * l; e += 256) {
+      const int kk = e / l, c = e % l;
+      rs[e] = (kk < kw && c >= k0) ? Ub[(size_t)(k0 + kk) * l + c] : C(0);
+    }
+    // r_b into ys (thread's column k0 + tx, rows ty + 8 x)
+    const int cb_ = k0 + tx;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      if (y == b && tx < kw) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) ys[(size_t)(ty + 8 * x) * l + cb_] -= acc[x][y];
       }
     }
-    int off = 0;
+    __syncthreads();
+    // q_b = r_b Ub(b, b)
+    C qv[8];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      for (int cl = 0; cl < 32; ++cl) {
-        const int c = 32 * t + cl;
-        if (c >= l) break;
-        const C rd = rdiag[c];
-        C qc[RW];
+    for (int x = 0; x < 8; ++x) qv[x] = C(0);
+    if (tx < kw) {
+      for (int kk = 0; kk < kw; ++kk) {
+        const C ub = rs[(size_t)kk * l + cb_];
 #pragma unroll
-        for (int w = 0; w < RW; ++w) {
-          C v = C(0);
-          if (lane == cl) {
-            v = s[w][t] * rd;
-            s[w][t] = v;
-          }
-          qc[w] = __shfl_sync(0xffffffffu, v, cl);
-        }
-#pragma unroll
-        for (int t2 = 0; t2 < NT; ++t2) {
-          const int c2 = lane + 32 * t2;
-          if (t2 >= t && c2 > c && c2 < l) {
-            const C uc = u[off + (c2 - c)];
-#pragma unroll
-            for (int w = 0; w < RW; ++w) s[w][t2] -= qc[w] * uc;
-          }
-        }
-        off += l - c;
+        for (int x = 0; x < 8; ++x) qv[x] = fma(ys[(size_t)(ty + 8 * x) * l + k0 + kk], ub, qv[x]);
       }
     }
+    __syncthreads();  // all reads of r_b done
+    if (tx < kw) {
 #pragma unroll
-    for (int w = 0; w < RW; ++w) {
-      const int r = r0 + w;
-      if (r >= rows) continue;
+      for (int x = 0; x < 8; ++x) ys[(size_t)(ty + 8 * x) * l + cb_] = qv[x];
+    }
+    __syncthreads();
+    // acc_c += q_b Ub(b, c), c in later blocks
+    if (b + 1 < nb) {
+      for (int kk = 0; kk < kw; ++kk) {
+        C yv[8], rv[8];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int c = lane + 32 * t;
-        if (c < l) {
-          Y[(size_t)r * ldy + c] = (T)s[w][t];
-          if (Ybf) Ybf[(size_t)r * lb + c] = __float2bfloat16_rn((float)s[w][t]);
+        for (int x = 0; x < 8; ++x) yv[x] = ys[(size_t)(ty + 8 * x) * l + k0 + kk];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int c = tx + 32 * y;
+          rv[y] = (y > b && c < l) ? rs[(size_t)kk * l + c] : C(0);
         }
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = fma(yv[x], rv[y], acc[x][y]);
       }
     }
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * l; e += 256) {
+    const int r = e / l, c = e % l;
+    const C v = ys[e];
+    Y[(size_t)(r0 + r) * ldy + c] = (T)v;
+    if (Ybf) Ybf[(size_t)(r0 + r) * lb + c] = __float2bfloat16_rn((float)v);
   }
 }
 
 template <typename T, typename C>
-void launch_apply(int rows, int l, T* Y, int ldy, const C* Ut, const C* dinv, __nv_bfloat16* Ybf, int lb,
-                  int sms, const int* gate, cudaStream_t s) {
-  const size_t smem = ((size_t)l * (l + 1) / 2 + l) * sizeof(C);
-  const int threads = 1024;
-  const int blocks = sms;
-#define RSVD_APPLY(NTV)                                                                              \
-  do {                                                                                               \
-    auto kfn = apply_kernel<T, C, NTV>;                                                              \
-    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);              \
-    kfn<<<blocks, threads, smem, s>>>(rows, l, Y, ldy, Ut, dinv, Ybf, lb, gate);                     \
-  } while (0)
-  const int nt = ceil_div(l, 32);
+void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __nv_bfloat16* Ybf, int lb,
+                  const int* gate, cudaStream_t s) {
+  if (rows == 0) return;
+  const size_t smem = (size_t)(64 + 32) * l * sizeof(C);
+  auto kfn = apply_kernel<T, C>;
+  cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kfn<<<ceil_div(rows, 64), 256, smem, s>>>(rows, l, Y, ldy, Ub, dinv, Ybf, lb, gate);
   note_launch();
-  if (nt <= 1)
-    RSVD_APPLY(1);
-  else if (nt <= 2)
-    RSVD_APPLY(2);
-  else if (nt <= 4)
-    RSVD_APPLY(4);
-  else
-    RSVD_APPLY(8);
-#undef RSVD_APPLY
 }
 
 template <typename C>
-void launch_chol(int l, const double* G, C* Ut, C* dinv, double* R, DevStatus* st, int pass,
+void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
                  const int* gate, cudaStream_t s) {
+  // binary32: 1024 threads; binary64 (l <= 128): 256 threads with room for registers
+  constexpr int NT = sizeof(C) == 4 ? 1024 : 256;
   const size_t smem = chol_smem_bytes(l, sizeof(C));
-  auto kfn = chol_kernel<C>;
+  auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<1, 1024, smem, s>>>(l, G, Ut, dinv, R, st, pass, gate);
+  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate);
   note_launch();
 }
 
@@ -437,7 +569,8 @@ size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize) {
   Carver c(nullptr);
   c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);  // Gram partials
   c.take<double>((size_t)l * l);                              // G
-  c.take<unsigned char>((size_t)l * (l + 1) / 2 * csize);     // Ut
+  c.take<float>((size_t)l * l);                               // Gf
+  c.take<unsigned char>((size_t)l * l * csize);               // Ub
   c.take<unsigned char>((size_t)l * csize);                   // dinv
   c.take<double>((size_t)3 * l * l);                          // R per pass
   c.take<double>((size_t)2 * l * l);                          // R products
@@ -450,16 +583,17 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
   Carver c(ws);
   double* P = c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
   double* G = c.take<double>((size_t)l * l);
-  C* Ut = c.take<C>((size_t)l * (l + 1) / 2);
+  float* Gf = c.take<float>((size_t)l * l);
+  C* Ub = c.take<C>((size_t)l * l);
   C* dinv = c.take<C>((size_t)l);
   double* Rp = c.take<double>((size_t)3 * l * l);
   double* Rm = c.take<double>((size_t)2 * l * l);
   const int* gate3 = &st->shifted;
   for (int pass = 1; pass <= 3; ++pass) {
     const int* gate = pass == 3 ? gate3 : nullptr;
-    launch_gram<T>(rows, l, Y, ldy, P, G, sms, gate, s);
-    launch_chol<C>(l, G, Ut, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s);
-    launch_apply<T, C>(rows, l, Y, ldy, Ut, dinv, nullptr, lb, sms, gate, s);
+    launch_gram<T>(rows, l, Y, ldy, P, G, sizeof(C) == 4 ? Gf : nullptr, sms, gate, s);
+    launch_chol<C>(l, G, Gf, Ub, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s);
+    launch_apply<T, C>(rows, l, Y, ldy, Ub, dinv, nullptr, lb, gate, s);
   }
   if (Ybf) launch_copy_bf16<T>(rows, l, Y, ldy, Ybf, lb, s);
   if (Rout) {
@@ -473,8 +607,9 @@ template void run_orth<float, float>(int, int, float*, int, double*, __nv_bfloat
                                      int, cudaStream_t);
 template void run_orth<double, double>(int, int, double*, int, double*, __nv_bfloat16*, int, void*,
                                        DevStatus*, int, cudaStream_t);
-template void launch_gram<float>(int, int, const float*, int, double*, double*, int, const int*, cudaStream_t);
-template void launch_gram<double>(int, int, const double*, int, double*, double*, int, const int*,
+template void launch_gram<float>(int, int, const float*, int, double*, double*, float*, int, const int*,
+                                 cudaStream_t);
+template void launch_gram<double>(int, int, const double*, int, double*, double*, float*, int, const int*,
                                   cudaStream_t);
 
 // ------------------------------------------------------------ bf16 copy --

@@ -21,7 +21,7 @@ void launch_gemm_simt(bool trans, int M, int N, int K, const T* A, int lda, cons
 // k_orth.cu
 int gram_splits(int rows, int l, int sms);
 template <typename T>
-void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, int sms, const int* gate,
+void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
                  cudaStream_t s);
 size_t chol_smem_bytes(int l, size_t csize);
 size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize);

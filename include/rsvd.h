@@ -201,6 +201,27 @@ rsvd_status rsvd_kernel_launches(rsvd_handle_t handle, long long* count);
 rsvd_status rsvd_profile(rsvd_handle_t handle, int on);
 rsvd_status rsvd_profile_read(rsvd_handle_t handle, int kind, double* total_ms, long long* launches);
 
+/* Allocation-free variant of rsvd_sketch for RSVD_MIXED_BF16 (the paper has
+ * no counterpart: this is a deployment convenience).  For callers that may
+ * not allocate device memory at all -- code running inside another
+ * framework's memory pool, an allocation-free real-time loop, a plugin that is
+ * handed only its input and output buffers -- and so cannot provide the
+ * workspace rsvd_sketch needs.  Same product, same arguments as rsvd_sketch
+ * minus the workspace: Y (fp32) = A X (trans = 0) or A^T X (trans = 1), A and X
+ * bf16 with leading dimensions that are multiples of 8 elements and 16-byte
+ * aligned rows.
+ * Scratch: a fixed 20 MiB array inside the library's device image (partial
+ * sums for at most 160 CTAs of 128 x 128 fp32 tiles, plus a status word);
+ * every GPU that loads the library keeps it until the process exits.
+ * Limits: l <= 128; larger l returns RSVD_E_INVALID ("l exceeds the fixed
+ * scratch limit").  No cudaMalloc, cudaFree or other allocating call is made.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before capturing a stream.
+ * Every call reuses the same array: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialized. */
+rsvd_status rsvd_sketch_noalloc(rsvd_handle_t handle, int trans, int m, int n, int l, const void* A, int lda,
+                                const void* X, int ldx, float* Y, int ldy, rsvd_stream_t stream);
+
 /* Orthonormalization (Sec. 2.3, "orth", unpivoted): Q = Y R^-1 with R upper
  * triangular, diag(R) > 0, by CholeskyQR2 (a shifted first pass is added when
  * the Gram matrix is too ill-conditioned, Fukaya et al., SISC 2020).  Y is

@@ -48,6 +48,7 @@ EXPORTED = [
     "rsvd_query_status", "rsvd_last_error_detail", "rsvd_philox_words", "rsvd_gaussian",
     "rsvd_sketch_workspace_size", "rsvd_sketch", "rsvd_orth_workspace_size", "rsvd_orth",
     "rsvd_project_workspace_size", "rsvd_project", "rsvd_kernel_launches", "rsvd_profile", "rsvd_profile_read",
+    "rsvd_sketch_noalloc",
 ]
 
 
@@ -98,6 +99,7 @@ def load():
         "rsvd_kernel_launches": [vp, ctypes.POINTER(ctypes.c_longlong)],
         "rsvd_profile": [vp, i],
         "rsvd_profile_read": [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+        "rsvd_sketch_noalloc": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -221,6 +223,11 @@ def rsvd_project_workspace_size(h, prec, m, n, l):
 def rsvd_project(h, prec, m, n, l, A, lda, Q, ldq, Bt, ldb, ws, stream=None):
     return load().rsvd_project(h, prec, m, n, l, _ptr(A), lda, _ptr(Q), ldq, _ptr(Bt), ldb, _ptr(ws),
                                ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_sketch_noalloc(h, trans, m, n, l, A, lda, X, ldx, Y, ldy, stream=None):
+    """bf16 tensor-core sketch product with library-owned scratch (no workspace argument)."""
+    return load().rsvd_sketch_noalloc(h, trans, m, n, l, _ptr(A), lda, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream))
 
 
 def rsvd_kernel_launches(h):

@@ -312,6 +312,12 @@ rsvd_status finish_sync(rsvd_handle_t h, const rsvd_params* p, DevStatus* st, cu
 }
 
 }  // namespace
+
+// Accessors for translation units that only see the opaque handle.
+int handle_device(rsvd_handle_t h) { return h->device; }
+int handle_sms(rsvd_handle_t h) { return h->sms; }
+rsvd_status handle_fail(rsvd_handle_t h, rsvd_status code, const char* msg) { return fail(h, code, "%s", msg); }
+
 }  // namespace rsvd
 
 using namespace rsvd;

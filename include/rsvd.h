@@ -156,7 +156,7 @@ rsvd_status rsvd_last_error_detail(rsvd_handle_t handle, char* buf, size_t len);
 rsvd_status rsvd_philox_words(rsvd_handle_t handle, int n_groups, int l, uint64_t seed,
                               uint32_t stream_id, int col0, uint32_t* out, rsvd_stream_t stream);
 
-/* Gaussian test matrix (the paper's randn; Fig. RSVD step 1): out is n x l,
+/* Gaussian test matrix (the paper's randn that draws G in Fig. RSVD): out is n x l,
  * row-major with leading dimension ldo >= l, element type `dtype`.
  * Entry (i, j) uses counter (i / 4, col0 + j, stream_id, 0); its words
  * (w0, w1) serve rows 4g, 4g+1 and (w2, w3) rows 4g+2, 4g+3 through
@@ -166,7 +166,7 @@ rsvd_status rsvd_philox_words(rsvd_handle_t handle, int n_groups, int l, uint64_
 rsvd_status rsvd_gaussian(rsvd_handle_t handle, int n, int l, uint64_t seed, uint32_t stream_id,
                           int col0, int dtype, void* out, int ldo, rsvd_stream_t stream);
 
-/* One sketch product (Fig. RSVDP_stabilized steps 2, 4, 5, 7):
+/* One sketch product (A G, A^T Q, A W of Fig. RSVDP_stabilized):
  *   trans = 0:  Y (m x l) = A (m x n) X (n x l)
  *   trans = 1:  Y (n x l) = A^T (n x m) X (m x l)
  * A row-major m x n (lda).  prec RSVD_F64: A, X, Y double; RSVD_F32: float
@@ -179,7 +179,7 @@ rsvd_status rsvd_sketch(rsvd_handle_t handle, int prec, int trans, int m, int n,
                         const void* A, int lda, const void* X, int ldx, void* Y, int ldy,
                         void* workspace, size_t ws_bytes, rsvd_stream_t stream);
 
-/* Projection B = Q^T A of Stage B (Sec. 3 step 1; Fig. RSVDP_stabilized step 7),
+/* Projection B = Q^T A of Stage B (Sec. 3; Fig. RSVDP_stabilized),
  * returned transposed:  Bt (n x l, row-major, ldb) = A^T Q  for A m x n (lda)
  * and Q m x l (ldq).  RSVD_F64: double; RSVD_F32: float, SIMT; RSVD_MIXED_BF16:
  * A and Q float, each split into a bf16 pair (x = hi + lo) and

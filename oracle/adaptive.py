@@ -16,7 +16,8 @@ Readings taken where the paper is silent:
 * the relative tolerance: eps = tol * ||A||_Fro;
 * before qr(A_j G) the sample is projected once against the current Q
   ((I - Q Q*) A_j G).  In exact arithmetic A_j already has range orthogonal to
-  Q, so this changes nothing but round-off (as Fig. adaptive2 line (7) notes);
+  Q, so this changes nothing but round-off (the caption of Fig. adaptive2 makes
+  the same point about its own redundant projection);
 * Gaussian blocks come from STREAM_ADAPTIVE, block t holding columns
   t b .. t b + b - 1 of that stream;
 * the loop stops with converged=False at max_rank or min(m, n).

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 
-The paper only says ``G = randn(n, k+p)`` (Sec. 4, Fig. RSVD step 1; Sec. 8,
-Fig. "Accuracy enhanced randomized SVD (with orthonormalization)" step 1) and
+The paper only says ``G = randn(n, k+p)`` (Sec. 4, Fig. RSVD; Sec. 8,
+Fig. "Accuracy enhanced randomized SVD (with orthonormalization)") and
 draws further Gaussian blocks in Fig. "greedy_blocked" (Sec. 12.3) and
 Fig. "adaptive2" (Sec. 13).  It fixes neither a generator nor a layout, so this
 project reads ``randn`` as:

@@ -97,9 +97,9 @@ def rsvd_power_plain(A, k, p, q, seed, full=False):
 def rsvd_power(A, k, p, q, seed, full=False):
     """Fig. RSVDP_stabilized (Sec. 8.1), the library's path.
 
-    (1) G = randn(n, k+p); (2) Q = orth(A G);
-    (3-6) q times: W = orth(A* Q), Q = orth(A W);
-    (7) B = Q* A; (8) [Uhat, D, V] = svd(B); (9) U = Q Uhat;
+    G = randn(n, k+p); Q = orth(A G);
+    q times: W = orth(A* Q), Q = orth(A W);
+    B = Q* A; [Uhat, D, V] = svd(B); U = Q Uhat;
     then truncation to k (Remark "How many basis vectors").
 
     Returns the outputs and every intermediate (Y, W, Q per step, B) so that

@@ -1,5 +1,5 @@
 // Gaussian test matrices from the Philox4x32-10 counter stream
-// (the paper's "randn", Fig. RSVD step 1 and Fig. RSVDP_stabilized step 1).
+// (the paper's "randn" that draws G in Fig. RSVD and Fig. RSVDP_stabilized).
 #include "common.cuh"
 #include "kernels.cuh"
 

@@ -1,5 +1,5 @@
 // SIMT sketch products for the binary64 and plain-binary32 paths
-// (Fig. RSVDP_stabilized steps 2, 4, 5 and 7: A G, A^T Q, A W, Q^T A).
+// (Fig. RSVDP_stabilized: the products A G, A^T Q, A W and Q^T A).
 //
 //   NN:  Y[M x N] = A[M x K] X[K x N]        A row-major (lda)
 //   TN:  Y[M x N] = A^T[M x K] X[K x N]      A is K x M row-major (lda)

@@ -1,4 +1,4 @@
-// Small SVD of B (Fig. RSVDP_stabilized step 8; Sec. 3 Stage B step 2).
+// Small SVD of B (Fig. RSVDP_stabilized; Sec. 3, Stage B: svd of the small matrix B).
 //
 // B (l x n) enters as B^T = A^T Q (n x l).  B^T is orthonormalized with the
 // same CholeskyQR2 as Stage A: B^T = Q_B R_B.  Then B = R_B^T Q_B^T and the

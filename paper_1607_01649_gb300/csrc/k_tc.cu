@@ -1,5 +1,5 @@
-// tcgen05 sketch products for the mixed-precision path (Fig. RSVDP_stabilized
-// steps 2, 4, 5 and 7 on tensor cores):
+// tcgen05 sketch products for the mixed-precision path (the products A G, A^T Q,
+// A W and Q^T A of Fig. RSVDP_stabilized, on tensor cores):
 //
 //   NN:  Y[M x N] = A[M x K] X[K x N]      A bf16 row-major (K-major operand)
 //   TN:  Y[M x N] = A^T[M x K] X[K x N]    A bf16 K x M row-major (MN-major operand)

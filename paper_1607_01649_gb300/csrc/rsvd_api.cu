@@ -120,26 +120,26 @@ rsvd_status fixed_rank_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, 
   T* Z = (T*)L.Zbuf;
   T* part = (T*)L.part;
   const int dt = sizeof(T) == 8 ? RSVD_DT_F64 : RSVD_DT_F32;
-  // (1) G = randn(n, l)
+  // G = randn(n, l)
   launch_gaussian(n, l, p->seed, 0u, 0, dt, Om, l, s);
-  // (2) Q = orth(A G)
+  // Q = orth(A G)
   launch_gemm_simt<T>(false, m, l, n, A, lda, Om, l, Y, l, part, sms, s);
   run_orth<T, C>(m, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
-  // (3-6) power steps with orth after every product
+  // q power steps with orth after every product
   for (int j = 0; j < p->q; ++j) {
     launch_gemm_simt<T>(true, n, l, m, A, lda, Y, l, Z, l, part, sms, s);
     run_orth<T, C>(n, l, Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
     launch_gemm_simt<T>(false, m, l, n, A, lda, Z, l, Y, l, part, sms, s);
     run_orth<T, C>(m, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   }
-  // (7) B^T = A^T Q, then B^T = Q_B R_B
+  // B^T = A^T Q, then B^T = Q_B R_B
   launch_gemm_simt<T>(true, n, l, m, A, lda, Y, l, Z, l, part, sms, s);
   run_orth<T, C>(n, l, Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
-  // (8) SVD of R_B^T by one-sided Jacobi
+  // SVD of R_B^T by one-sided Jacobi
   cudaError_t e = launch_jacobi<C>(l, L.Rb, (C*)L.Wt, (C*)L.Jt, L.sigma, L.st, s);
   if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
   launch_sort_gather<C>(l, kk, L.sigma, (const C*)L.Wt, (const C*)L.Jt, D, (C*)L.Wsel, (C*)L.Jsel, s);
-  // (9) U = Q Uhat, V = Q_B J, truncated to kk; sign convention
+  // U = Q Uhat, V = Q_B J, truncated to kk; sign convention
   launch_gemm_simt<T>(false, n, kk, l, Z, l, (const T*)L.Jsel, kk, V, ldv, nullptr, sms, s);
   launch_sign_fix<T, C>(n, kk, l, V, ldv, (C*)L.Wsel, L.part, s);
   launch_gemm_simt<T>(false, m, kk, l, Y, l, (const T*)L.Wsel, kk, U, ldu, nullptr, sms, s);
@@ -253,9 +253,9 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
   rsvd_status st;
   // A = Ah + Al (bf16 pair); the sketches read Ah, the projection both
   launch_split_bf16(m, n, A, lda, L.Ah, L.Al, n8, sms, s);
-  // (1) G = randn(n, l), bf16
+  // G = randn(n, l), bf16
   launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_BF16, L.Omb, l8, s);
-  // (2) Q = orth(A G)
+  // Q = orth(A G)
   {
     ProfScope ps(h, 0, s);
     if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Omb, l8, nullptr, L.Y, l, L.part,
@@ -263,7 +263,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
       return st;
   }
   run_orth<float, float>(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
-  // (3-6) power steps
+  // power steps
   for (int j = 0; j < p->q; ++j) {
     {
       ProfScope ps(h, 0, s);
@@ -280,7 +280,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
     }
     run_orth<float, float>(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
   }
-  // (7) B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
+  // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
   launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);
   {
     ProfScope ps(h, 1, s);
@@ -289,11 +289,11 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
       return st;
   }
   run_orth<float, float>(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
-  // (8) SVD of R_B^T
+  // SVD of R_B^T
   cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
   if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
   launch_sort_gather<float>(l, kk, L.sigma, L.Wt, L.Jt, D, L.Wsel, L.Jsel, s);
-  // (9) U = Q Uhat, V = Q_B J
+  // U = Q Uhat, V = Q_B J
   launch_gemm_simt<float>(false, n, kk, l, L.Z, l, L.Jsel, kk, V, ldv, nullptr, sms, s);
   launch_sign_fix<float, float>(n, kk, l, V, ldv, L.Wsel, L.part, s);
   launch_gemm_simt<float>(false, m, kk, l, L.Y, l, L.Wsel, kk, U, ldu, nullptr, sms, s);

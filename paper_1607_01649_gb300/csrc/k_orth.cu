@@ -447,76 +447,74 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
   const int r0 = blockIdx.x * 64;
   const int nr = min(64, rows - r0);
-  for (int e = tid; e < 64 * l; e += 256) {
-    const int r = e / l, c = e % l;
-    ys[e] = (r < nr) ? (C)Y[(size_t)(r0 + r) * ldy + c] * dinv[c] : C(0);
-  }
+  // stage the stripe (row by row, no index division), scaled by dinv
+  for (int r = 0; r < 64; ++r)
+    for (int c = tid; c < l; c += 256)
+      ys[(size_t)r * l + c] = (r < nr) ? (C)Y[(size_t)(r0 + r) * ldy + c] * dinv[c] : C(0);
   C acc[8][8];
 #pragma unroll
   for (int x = 0; x < 8; ++x)
 #pragma unroll
     for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
   const int nb = (l + 31) / 32;
-#pragma unroll 1
-  for (int b = 0; b < nb; ++b) {
-    const int k0 = 32 * b, kw = min(32, l - k0);
-    __syncthreads();  // previous block's reads of rs / ys are done
-    for (int e = tid; e < 32 * l; e += 256) {
-      const int kk = e / l, c = e % l;
-      rs[e] = (kk < kw && c >= k0) ? Ub[(size_t)(k0 + kk) * l + c] : C(0);
-    }
-    // r_b into ys (thread's column k0 + tx, rows ty + 8 x)
-    const int cb_ = k0 + tx;
+  // block b is a compile-time index, so the update below touches only the
+  // later column blocks y > b
 #pragma unroll
-    for (int y = 0; y < 8; ++y) {
-      if (y == b && tx < kw) {
+  for (int b = 0; b < 8; ++b) {
+    if (b < nb) {
+      const int k0 = 32 * b, kw = min(32, l - k0);
+      __syncthreads();  // previous block's reads of rs / ys are done
+      for (int kk = ty; kk < 32; kk += 8)
+        for (int c = tx; c < l; c += 32)
+          rs[(size_t)kk * l + c] = (kk < kw && c >= k0) ? Ub[(size_t)(k0 + kk) * l + c] : C(0);
+      // r_b into ys (thread's column k0 + tx, rows ty + 8 x)
+      const int cb_ = k0 + tx;
+      if (tx < kw) {
 #pragma unroll
-        for (int x = 0; x < 8; ++x) ys[(size_t)(ty + 8 * x) * l + cb_] -= acc[x][y];
+        for (int x = 0; x < 8; ++x) ys[(size_t)(ty + 8 * x) * l + cb_] -= acc[x][b];
       }
-    }
-    __syncthreads();
-    // q_b = r_b Ub(b, b)
-    C qv[8];
+      __syncthreads();
+      // q_b = r_b Ub(b, b)
+      C qv[8];
 #pragma unroll
-    for (int x = 0; x < 8; ++x) qv[x] = C(0);
-    if (tx < kw) {
-      for (int kk = 0; kk < kw; ++kk) {
-        const C ub = rs[(size_t)kk * l + cb_];
+      for (int x = 0; x < 8; ++x) qv[x] = C(0);
+      if (tx < kw) {
+        for (int kk = 0; kk < kw; ++kk) {
+          const C ub = rs[(size_t)kk * l + cb_];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) qv[x] = fma(ys[(size_t)(ty + 8 * x) * l + k0 + kk], ub, qv[x]);
-      }
-    }
-    __syncthreads();  // all reads of r_b done
-    if (tx < kw) {
-#pragma unroll
-      for (int x = 0; x < 8; ++x) ys[(size_t)(ty + 8 * x) * l + cb_] = qv[x];
-    }
-    __syncthreads();
-    // acc_c += q_b Ub(b, c), c in later blocks
-    if (b + 1 < nb) {
-      for (int kk = 0; kk < kw; ++kk) {
-        C yv[8], rv[8];
-#pragma unroll
-        for (int x = 0; x < 8; ++x) yv[x] = ys[(size_t)(ty + 8 * x) * l + k0 + kk];
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-          const int c = tx + 32 * y;
-          rv[y] = (y > b && c < l) ? rs[(size_t)kk * l + c] : C(0);
+          for (int x = 0; x < 8; ++x) qv[x] = fma(ys[(size_t)(ty + 8 * x) * l + k0 + kk], ub, qv[x]);
         }
+      }
+      __syncthreads();  // all reads of r_b done
+      if (tx < kw) {
 #pragma unroll
-        for (int x = 0; x < 8; ++x)
+        for (int x = 0; x < 8; ++x) ys[(size_t)(ty + 8 * x) * l + cb_] = qv[x];
+      }
+      __syncthreads();
+      // acc_c += q_b Ub(b, c) for the later column blocks c > b
+      if (b + 1 < nb) {
+        for (int kk = 0; kk < kw; ++kk) {
+          C yv[8];
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = fma(yv[x], rv[y], acc[x][y]);
+          for (int x = 0; x < 8; ++x) yv[x] = ys[(size_t)(ty + 8 * x) * l + k0 + kk];
+#pragma unroll
+          for (int y = b + 1; y < 8; ++y) {
+            const int c = tx + 32 * y;
+            const C rv = (c < l) ? rs[(size_t)kk * l + c] : C(0);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) acc[x][y] = fma(yv[x], rv, acc[x][y]);
+          }
+        }
       }
     }
   }
   __syncthreads();
-  for (int e = tid; e < nr * l; e += 256) {
-    const int r = e / l, c = e % l;
-    const C v = ys[e];
-    Y[(size_t)(r0 + r) * ldy + c] = (T)v;
-    if (Ybf) Ybf[(size_t)(r0 + r) * lb + c] = __float2bfloat16_rn((float)v);
-  }
+  for (int r = 0; r < nr; ++r)
+    for (int c = tid; c < l; c += 256) {
+      const C v = ys[(size_t)r * l + c];
+      Y[(size_t)(r0 + r) * ldy + c] = (T)v;
+      if (Ybf) Ybf[(size_t)(r0 + r) * lb + c] = __float2bfloat16_rn((float)v);
+    }
 }
 
 template <typename T, typename C>

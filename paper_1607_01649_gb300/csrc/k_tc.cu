@@ -38,9 +38,10 @@ struct TcArgs {
   int Npad;      // MMA N (multiple of 16)
   int NA;        // TMEM columns per accumulator (power of 2 >= 32)
   int nchunk;    // 64-column TMA boxes per B tile
+  int nbuf;      // TMEM accumulator sets (2: one tile's epilogue overlaps the next tile's MMAs)
   float* Y;
   int ldy;
-  float* part;   // [G][2][128][Npad]
+  float* part;   // [G][2][BM][Npad]
   DevStatus* st;
 };
 
@@ -51,16 +52,18 @@ constexpr int TC_MAX_CTAS = 256;  // persistent grid cap (>= #SMs of the part)
 constexpr uint32_t A_TILE = 16384;   // 128 x 64 bf16
 constexpr uint32_t B_CHUNK = 8192;   // 64 x 64 bf16
 
-template <bool TRANS, bool SPLIT3>
+template <bool TRANS, bool SPLIT3, int SUB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX2, TcArgs g,
                    int stages) {
+  static_assert(!SPLIT3 || SUB == 1, "the split-bf16 projection uses 128-row tiles");
+  constexpr int BM = 128 * SUB;       // rows per tile: SUB sub-tiles of 128 share each X tile
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   constexpr int NT = SPLIT3 ? 2 : 1;  // operand copies per stage
   const uint32_t b_bytes = (uint32_t)g.nchunk * B_CHUNK;
-  const uint32_t stage_bytes = NT * (A_TILE + b_bytes);
+  const uint32_t stage_bytes = NT * (SUB * A_TILE + b_bytes);
   __shared__ uint64_t full[8], empty[8], tfull[2], tempty[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
@@ -71,8 +74,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int t_first = (int)(u0 / g.KB);
   const int t_last = (int)((u1 - 1) / g.KB);
 
+  const uint32_t tcols = (uint32_t)(g.nbuf * SUB * g.NA);  // a power of 2 <= 512
   if (warp == 1) {
-    tmem_alloc(&tslot, 2 * g.NA);
+    tmem_alloc(&tslot, tcols);
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < g.nbuf; ++a) {
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], 128);
     }
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = t_first; t <= t_last && !abort_flag; ++t) {
       const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
       const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
-      const int m0 = t * 128;
+      const int m0 = t * BM;
       for (int kb = kb_lo; kb < kb_hi; ++kb, ++it) {
         const int s = it % stages;
         const uint32_t ph = (uint32_t)(it / stages) & 1u;
@@ -116,17 +120,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         unsigned char* sA = sm + (size_t)s * stage_bytes;
-        unsigned char* sB = sA + NT * A_TILE;
+        unsigned char* sB = sA + NT * SUB * A_TILE;
         mbar_arrive_expect_tx(&full[s], stage_bytes);
         const int k0 = kb * 64;
-        if (!TRANS) {
-          tma_load_2d(sA, &tmA, k0, m0, &full[s]);
-        } else {
-          tma_load_2d(sA, &tmA, m0, k0, &full[s]);
-          tma_load_2d(sA + 8192, &tmA, m0 + 64, k0, &full[s]);
-          if (SPLIT3) {
-            tma_load_2d(sA + A_TILE, &tmA2, m0, k0, &full[s]);
-            tma_load_2d(sA + A_TILE + 8192, &tmA2, m0 + 64, k0, &full[s]);
+#pragma unroll
+        for (int sb = 0; sb < SUB; ++sb) {
+          unsigned char* sAs = sA + sb * A_TILE;
+          const int ms = m0 + 128 * sb;
+          if (!TRANS) {
+            tma_load_2d(sAs, &tmA, k0, ms, &full[s]);
+          } else {
+            tma_load_2d(sAs, &tmA, ms, k0, &full[s]);
+            tma_load_2d(sAs + 8192, &tmA, ms + 64, k0, &full[s]);
+            if (SPLIT3) {
+              tma_load_2d(sAs + A_TILE, &tmA2, ms, k0, &full[s]);
+              tma_load_2d(sAs + A_TILE + 8192, &tmA2, ms + 64, k0, &full[s]);
+            }
           }
         }
         for (int ch = 0; ch < g.nchunk; ++ch) {
@@ -143,14 +152,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = t_first; t <= t_last && ok; ++t, ++j) {
       const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
       const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
-      const int acc = j & 1;
-      const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+      const int acc = j % g.nbuf;
+      const uint32_t aph = (uint32_t)(j / g.nbuf) & 1u;
       if (!mbar_wait(&tempty[acc], aph ^ 1u)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t dtm = tbase + (uint32_t)(acc * g.NA);
+      const uint32_t dtm = tbase + (uint32_t)(acc * SUB * g.NA);
       for (int kb = kb_lo; kb < kb_hi; ++kb, ++it) {
         const int s = it % stages;
         const uint32_t ph = (uint32_t)(it / stages) & 1u;
@@ -160,18 +169,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t aA = smem_u32(sm + (size_t)s * stage_bytes);
-        const uint32_t aB = aA + NT * A_TILE;
+        const uint32_t aB = aA + NT * SUB * A_TILE;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const uint64_t ad = TRANS ? umma_desc(aA + 2048 * k, 8192, 1024) : umma_desc(aA + 32 * k, 16, 1024);
           const uint64_t bd = umma_desc(aB + 2048 * k, 8192, 1024);
           const uint32_t accum = (kb > kb_lo || k > 0) ? 1u : 0u;
-          mma_bf16(dtm, ad, bd, idesc, accum);
-          if (SPLIT3) {
-            const uint64_t ad2 = umma_desc(aA + A_TILE + 2048 * k, 8192, 1024);
-            const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
-            mma_bf16(dtm, ad, bd2, idesc, 1u);   // Ah^T Xl
-            mma_bf16(dtm, ad2, bd, idesc, 1u);   // Al^T Xh
+#pragma unroll
+          for (int sb = 0; sb < SUB; ++sb) {
+            const uint32_t aAs = aA + sb * A_TILE;
+            const uint64_t ad = TRANS ? umma_desc(aAs + 2048 * k, 8192, 1024) : umma_desc(aAs + 32 * k, 16, 1024);
+            mma_bf16(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
+            if (SPLIT3) {
+              const uint64_t ad2 = umma_desc(aAs + A_TILE + 2048 * k, 8192, 1024);
+              const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
+              mma_bf16(dtm, ad, bd2, idesc, 1u);   // Ah^T Xl
+              mma_bf16(dtm, ad2, bd, idesc, 1u);   // Al^T Xh
+            }
           }
         }
         mma_commit(&empty[s]);
@@ -191,8 +204,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = t_first; t <= t_last; ++t, ++j) {
       const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
       const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
-      const int acc = j & 1;
-      const uint32_t aph = (uint32_t)(j >> 1) & 1u;
+      const int acc = j % g.nbuf;
+      const uint32_t aph = (uint32_t)(j / g.nbuf) & 1u;
       if (!mbar_wait(&tfull[acc], aph)) {
         set_status(g.st, RSVD_E_TIMEOUT);
         abort_flag = 1;
@@ -200,7 +213,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       tc_fence_after();
       const bool whole = (kb_lo == 0 && kb_hi == g.KB);
-      const int row = t * 128 + r;
+#pragma unroll 1
+      for (int sb = 0; sb < SUB; ++sb) {
+      const int row = t * BM + 128 * sb + r;
       float* dst;
       bool store = true;
       if (whole) {
@@ -208,9 +223,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         store = row < g.M;
       } else {
         const int slot = (t == t_first) ? 0 : 1;
-        dst = g.part + (((size_t)c * 2 + slot) * 128 + r) * g.Npad;
+        dst = g.part + (((size_t)c * 2 + slot) * BM + 128 * sb + r) * g.Npad;
       }
-      const uint32_t taddr = tbase + (uint32_t)(acc * g.NA) + ((uint32_t)(32 * q) << 16);
+      const uint32_t taddr = tbase + (uint32_t)((acc * SUB + sb) * g.NA) + ((uint32_t)(32 * q) << 16);
       for (int c16 = 0; c16 < g.Npad; c16 += 16) {
         uint32_t v[16];
         tmem_ld16(taddr + c16, v);
@@ -228,6 +243,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
     }
@@ -243,14 +259,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tbase, 2 * g.NA);
+    tmem_dealloc(tbase, tcols);
   }
 }
 
 // Adds the partial tiles of tiles whose k-blocks were split between CTAs, in
-// CTA order.  One CTA per tile; tiles computed whole by one CTA return at once.
-__global__ void tc_fixup_kernel(TcArgs g) {
+// CTA order.  Grid: (tile, 16-row chunk); tiles computed whole by one CTA
+// return at once.  Partial rows are Npad floats (a multiple of 16), read as
+// float4.
+constexpr int FIX_ROWS = 16;
+__global__ void __launch_bounds__(256) tc_fixup_kernel(TcArgs g, int BM) {
   const int t = blockIdx.x;
+  const int r0 = blockIdx.y * FIX_ROWS;
   __shared__ int s_cf, s_cl, s_slot[TC_MAX_CTAS + 1];
   if (threadIdx.x == 0) {
     const long long ub = (long long)t * g.KB, ue = ub + g.KB - 1;
@@ -267,14 +287,25 @@ __global__ void tc_fixup_kernel(TcArgs g) {
   __syncthreads();
   const int cf = s_cf, cl = s_cl;
   if (cf == cl) return;
-  const int rows = min(128, g.M - t * 128);
-  for (int r = threadIdx.x / 32; r < rows; r += blockDim.x / 32) {
-    for (int col = threadIdx.x % 32; col < g.N; col += 32) {
-      float s = 0.f;
-      for (int cc = cf; cc <= cl; ++cc)
-        s += g.part[(((size_t)cc * 2 + s_slot[cc - cf]) * 128 + r) * g.Npad + col];
-      g.Y[(size_t)(t * 128 + r) * g.ldy + col] = s;
+  const int rows = min(FIX_ROWS, g.M - t * BM - r0);
+  if (rows <= 0) return;
+  const int nv = g.Npad / 4;  // float4 per partial row
+  for (int e = threadIdx.x; e < rows * nv; e += blockDim.x) {
+    const int r = r0 + e / nv, c4 = (e % nv) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int cc = cf; cc <= cl; ++cc) {
+      const float4 v =
+          *reinterpret_cast<const float4*>(g.part + (((size_t)cc * 2 + s_slot[cc - cf]) * BM + r) * g.Npad + c4);
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
     }
+    float* y = g.Y + (size_t)(t * BM + r) * g.ldy + c4;
+    if (c4 + 0 < g.N) y[0] = acc.x;
+    if (c4 + 1 < g.N) y[1] = acc.y;
+    if (c4 + 2 < g.N) y[2] = acc.z;
+    if (c4 + 3 < g.N) y[3] = acc.w;
   }
 }
 
@@ -310,35 +341,43 @@ static int pow2_at_least(int v) {
   return p;
 }
 
+// Rows per tile the launcher picks: 256 (two sub-tiles sharing X) for the
+// plain sketch when M spans at least two 256-row tiles, else 128.
+int tc_rows_per_tile(int M, bool split3) { return (!split3 && M >= 512) ? 256 : 128; }
+
 size_t tc_gemm_workspace(int M, int N, int K, int sms) {
-  const int KB = ceil_div(K, 64), T = ceil_div(M, 128);
+  const int KB = ceil_div(K, 64), T = ceil_div(M, 128);  // sized for 128-row tiles: enough for 256 too
   const long long W = (long long)T * KB;
   int G = (int)(W < sms ? W : sms);
   if (G > TC_MAX_CTAS) G = TC_MAX_CTAS;
   const int Npad = ceil_div(N, 16) * 16;
-  return (size_t)G * 2 * 128 * Npad * sizeof(float);
+  return (size_t)G * 2 * 256 * Npad * sizeof(float);
 }
 
 bool tc_supported(int N) { return N >= 1 && N <= 256; }
 
 cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const __nv_bfloat16* A, int lda,
                            const __nv_bfloat16* A2, const __nv_bfloat16* X, int ldx, const __nv_bfloat16* X2, float* Y,
-                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s) {
+                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm) {
   if (M == 0 || N == 0) return cudaSuccess;
   if (!get_encode()) return cudaErrorNotSupported;
   if ((lda % 8) || (ldx % 8) || (((uintptr_t)A | (uintptr_t)X) & 15)) return cudaErrorInvalidValue;
+  if (bm <= 0) bm = tc_rows_per_tile(M, split3);
+  if (split3) bm = 128;
+  const int SUBT = bm / 128;
   TcArgs g;
   g.M = M;
   g.N = N;
   g.K = K;
   g.KB = ceil_div(K, 64);
-  g.T = ceil_div(M, 128);
+  g.T = ceil_div(M, bm);
   g.W = (long long)g.T * g.KB;
   g.G = (int)(g.W < sms ? g.W : sms);
   if (g.G > TC_MAX_CTAS) g.G = TC_MAX_CTAS;
   g.Npad = ceil_div(N, 16) * 16;
   g.NA = pow2_at_least(g.Npad);
   g.nchunk = ceil_div(N, 64);
+  g.nbuf = (2 * SUBT * g.NA <= 512) ? 2 : 1;
   g.Y = Y;
   g.ldy = ldy;
   g.part = part;
@@ -359,29 +398,31 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   }
   if (!ok) return cudaErrorInvalidValue;
   const int NT = split3 ? 2 : 1;
-  const size_t stage_bytes = (size_t)NT * (A_TILE + (size_t)g.nchunk * B_CHUNK);
+  const size_t stage_bytes = (size_t)NT * (SUBT * A_TILE + (size_t)g.nchunk * B_CHUNK);
   int stages = (int)((200 * 1024) / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) return cudaErrorInvalidValue;
   const size_t smem = stages * stage_bytes + 1024;
   cudaError_t e;
-  if (!trans) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<false, false><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);
-    note_launch();
-  } else if (!split3) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<true, false><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);
-    note_launch();
-  } else {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<true, true><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);
-    note_launch();
-  }
-  tc_fixup_kernel<<<g.T, 256, 0, s>>>(g);
+#define RSVD_TC_LAUNCH(TR, SP, SB)                                                                           \
+  do {                                                                                                       \
+    e = cudaFuncSetAttribute(tc_gemm_kernel<TR, SP, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                                          \
+    tc_gemm_kernel<TR, SP, SB><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);                   \
+  } while (0)
+  if (split3)
+    RSVD_TC_LAUNCH(true, true, 1);
+  else if (!trans && SUBT == 1)
+    RSVD_TC_LAUNCH(false, false, 1);
+  else if (!trans)
+    RSVD_TC_LAUNCH(false, false, 2);
+  else if (SUBT == 1)
+    RSVD_TC_LAUNCH(true, false, 1);
+  else
+    RSVD_TC_LAUNCH(true, false, 2);
+#undef RSVD_TC_LAUNCH
+  note_launch();
+  tc_fixup_kernel<<<dim3(g.T, bm / FIX_ROWS), 256, 0, s>>>(g, bm);
   note_launch();
   return cudaGetLastError();
 }

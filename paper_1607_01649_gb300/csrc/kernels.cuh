@@ -48,9 +48,11 @@ void launch_sign_fix(int n, int kk, int l, T* V, int ldv, C* Wsel, void* ws, cud
 // k_tc.cu
 size_t tc_gemm_workspace(int M, int N, int K, int sms);
 bool tc_supported(int N);
+int tc_rows_per_tile(int M, bool split3);
+// bm: rows per tile (128 or 256); 0 lets the launcher choose (tc_rows_per_tile).
 cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const __nv_bfloat16* A, int lda,
                            const __nv_bfloat16* A2, const __nv_bfloat16* X, int ldx, const __nv_bfloat16* X2, float* Y,
-                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s);
+                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm = 0);
 void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb,
                        int sms, cudaStream_t s);
 

@@ -89,8 +89,9 @@ extern "C" rsvd_status rsvd_sketch_noalloc(rsvd_handle_t handle, int trans, int 
     return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: status clear failed");
   int sms = handle_sms(handle);
   if (sms > NOALLOC_MAX_CTAS) sms = NOALLOC_MAX_CTAS;  // partial tiles for at most 160 CTAs
+  // 128-row tiles: the fixed scratch holds two 128-row partial tiles per CTA
   const cudaError_t e = launch_tc_gemm(trans != 0, false, M, l, K, (const __nv_bfloat16*)A, lda, nullptr,
-                                       (const __nv_bfloat16*)X, ldx, nullptr, Y, ldy, part, sms, dst, s);
+                                       (const __nv_bfloat16*)X, ldx, nullptr, Y, ldy, part, sms, dst, s, 128);
   if (e != cudaSuccess) return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: launch failed");
   if (cudaGetLastError() != cudaSuccess) return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: launch failed");
   return RSVD_OK;

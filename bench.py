@@ -31,7 +31,7 @@ METRIC = "RSVD solves/s and % roofline at stated FP64-oracle error; mixed vs pla
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "f32"])
@@ -71,7 +71,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -115,6 +115,37 @@ def cpu_cores():
 
 
 # ------------------------------------------------------------- oracle leg --
+TC_PROFILE = os.path.join(ROOT, "profiles", "tc_gemm_kernel_poly_decay.md")
+TC_SOURCES = [os.path.join(ROOT, "paper_1607_01649_gb300", "csrc", f) for f in ("k_tc.cu", "sm100.cuh")]
+
+
+def tc_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TC_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def tc_traffic(m, n):
+    """DRAM bytes (read + write) of one sketch launch from the committed ncu
+    summary, scaled from its capture size to m x n (the kernel's traffic is
+    proportional to the bytes of A it streams).  None when the kernel sources
+    changed since the capture or no summary exists."""
+    try:
+        fields = {}
+        for line in open(TC_PROFILE):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_sources_sha256_16") != tc_source_hash():
+            return None
+        cm, cn = (int(x) for x in fields["capture_shape"].split("x"))
+        return float(fields["dram_bytes_per_launch"]) * (m * n) / float(cm * cn)
+    except Exception:
+        return None
+
+
 def oracle_sample(a, seconds=12.0, device=None):
     """Time the float64 oracle on a sample x sample matrix of the same family
     (same k, p, q), scaled to the full workload by the m*n ratio (the sketch
@@ -298,7 +329,8 @@ def run_ours(a):
         alg_bytes = 2.0 * m * n + 2.0 * n * l + 4.0 * m * l
         achieved = alg_bytes / (per_launch_ms / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "tc_gemm_kernel (bf16 sketch A*X / A^T*X, stream-K)",
+                "traffic": tc_traffic(m, n), "algorithmic_bytes": alg_bytes,
+                "kernel": "tc_gemm_kernel (bf16 sketch A*X / A^T*X, stream-K)",
                 "launches": sk_n, "avg_ms": per_launch_ms, "peak_source": peak_src,
                 "projection_split3_avg_ms": (pj_ms / pj_n) if pj_n else None}
     elif prec == rs.RSVD_F32:

@@ -18,6 +18,11 @@ Readings taken where the paper is silent:
   ((I - Q Q*) A_j G).  In exact arithmetic A_j already has range orthogonal to
   Q, so this changes nothing but round-off (the caption of Fig. adaptive2 makes
   the same point about its own redundant projection);
+* the deflation A_j <- A_j - Q_new B_new is applied twice (B2 = Q_new* A_j,
+  A_j <- A_j - Q_new B2, B_new <- B_new + B2).  In exact arithmetic the second
+  pass is zero; in floating point it removes what a not-quite-orthonormal
+  Q_new leaves of A_j inside span(Q_new), which the projection of later
+  samples would otherwise hide from every later step;
 * Gaussian blocks come from STREAM_ADAPTIVE, block t holding columns
   t b .. t b + b - 1 of that stream;
 * the loop stops with converged=False at max_rank or min(m, n).
@@ -52,9 +57,12 @@ def adaptive_blocked(A, tol, b=16, seed=0, q=0, max_rank=None):
         Y = Y - Q @ (Q.T @ Y)
         Qn, _ = orth(Y)
         Bn = Qn.T @ Aj
+        Aj = Aj - Qn @ Bn
+        B2 = Qn.T @ Aj
+        Aj = Aj - Qn @ B2
+        Bn = Bn + B2
         Q = np.hstack([Q, Qn])
         B = np.vstack([B, Bn])
-        Aj = Aj - Qn @ Bn
         nd = float(np.sqrt(np.sum(Aj * Aj)))
         norms_direct.append(nd)
         norms_downdate.append(float(np.sqrt(max(a2 - np.sum(B * B), 0.0))))

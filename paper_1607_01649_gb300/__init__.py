@@ -280,6 +280,28 @@ def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws
     return U, D, V
 
 
+def adaptive_tol(A, tol, block=16, max_rank=0, seed=0, prec=RSVD_F32):
+    """Tolerance-driven randomized SVD by rsvd_adaptive_tol.  Returns
+    (U, D, V, rank, err, status): U, V have max_rank columns, the first `rank`
+    valid; status is RSVD_OK or RSVD_E_NOT_CONVERGED (other failures raise)."""
+    import torch
+    h = handle(A.device.index)
+    m, n = A.shape
+    prm = make_params(0, 0, 0, seed, prec, 0, tol=tol, block=block, max_rank=max_rank)
+    R = max_rank if max_rank > 0 else min(m, n, 128 if prec == RSVD_F64 else 256)
+    dt = _prec_dtype(prec)
+    U = torch.empty(m, R, dtype=dt, device=A.device)
+    D = torch.empty(R, dtype=torch.float64, device=A.device)
+    V = torch.empty(n, R, dtype=dt, device=A.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=A.device)
+    err = torch.zeros(1, dtype=torch.float64, device=A.device)
+    ws = _empty_ws(rsvd_workspace_size(h, m, n, prm), A.device)
+    code = rsvd_adaptive_tol(h, m, n, A, A.stride(0), prm, U, U.stride(0), D, V, V.stride(0), rank, err, ws)
+    if code not in (RSVD_OK, RSVD_E_NOT_CONVERGED):
+        raise RsvdError(code, last_error(h))
+    return U, D, V, int(rank.item()), float(err.item()), code
+
+
 def gaussian(n, l, seed, stream_id=0, col0=0, dtype=None, device="cuda"):
     import torch
     dtype = torch.float32 if dtype is None else dtype

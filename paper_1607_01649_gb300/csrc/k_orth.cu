@@ -30,8 +30,8 @@ constexpr int GFOLD = 4;     // chunks per binary64 fold (128 rows)
 template <typename T>
 __global__ void __launch_bounds__(256)
     gram_partial_kernel(int rows, int l, const T* __restrict__ Y, int ldy, double* __restrict__ P,
-                        int rows_per_split, const int* gate) {
-  if (gate && *gate == 0) return;
+                        int rows_per_split, const int* gate, const int* skip) {
+  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   __shared__ T Yi[GCH][GT];
   __shared__ T Yj[GCH][GT];
   // tile index -> (bi, bj) with bi <= bj
@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256)
 // Gf receives G rounded to binary32 (the Cholesky kernel's input on the
 // binary32 path; converting here spreads the binary64 conversions over the GPU).
 __global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__ P, double* __restrict__ G,
-                                   float* __restrict__ Gf, const int* gate) {
-  if (gate && *gate == 0) return;
+                                   float* __restrict__ Gf, const int* gate, const int* skip) {
+  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= l * l) return;
   int i = idx / l, j = idx % l;
@@ -139,15 +139,15 @@ int gram_splits(int rows, int l, int sms) {
 
 template <typename T>
 void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
-                 cudaStream_t s) {
+                 cudaStream_t s, const int* skip) {
   const int nb = ceil_div(l, GT);
   const int tiles = nb * (nb + 1) / 2;
   const int splits = gram_splits(rows, l, sms);
   const int rps = ceil_div(ceil_div(rows, splits), GCH) * GCH;
   const int used = ceil_div(rows, rps);
-  gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate);
+  gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate, skip);
   note_launch();
-  gram_reduce_kernel<<<ceil_div(l * l, 256), 256, 0, s>>>(l, used, P, G, Gf, gate);
+  gram_reduce_kernel<<<ceil_div(l * l, 256), 256, 0, s>>>(l, used, P, G, Gf, gate, skip);
   note_launch();
 }
 
@@ -244,8 +244,9 @@ __device__ __forceinline__ void warp_trinv32(const C* a, const int* cb, int c0, 
 template <typename C, int NT>
 __global__ void __launch_bounds__(NT)
     chol_kernel(int l, const double* __restrict__ G, const float* __restrict__ Gf, C* __restrict__ Ub,
-                C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate) {
-  if (gate && *gate == 0) return;
+                C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate,
+                const int* skip) {
+  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   extern __shared__ unsigned char smem_raw[];
   C* a = reinterpret_cast<C*>(smem_raw);  // packed lower, l(l+1)/2
   double* d = reinterpret_cast<double*>(smem_raw + (((size_t)l * (l + 1) / 2 * sizeof(C) + 15) & ~15));
@@ -439,8 +440,8 @@ size_t chol_smem_bytes(int l, size_t csize) {
 template <typename T, typename C>
 __global__ void __launch_bounds__(256)
     apply_kernel(int rows, int l, T* __restrict__ Y, int ldy, const C* __restrict__ Ub, const C* __restrict__ dinv,
-                 __nv_bfloat16* __restrict__ Ybf, int lb, const int* gate) {
-  if (gate && *gate == 0) return;
+                 __nv_bfloat16* __restrict__ Ybf, int lb, const int* gate, const int* skip) {
+  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   extern __shared__ unsigned char smem_raw[];
   C* ys = reinterpret_cast<C*>(smem_raw);  // 64 x l
   C* rs = ys + (size_t)64 * l;             // 32 x l rows of Ub
@@ -519,33 +520,34 @@ __global__ void __launch_bounds__(256)
 
 template <typename T, typename C>
 void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __nv_bfloat16* Ybf, int lb,
-                  const int* gate, cudaStream_t s) {
+                  const int* gate, cudaStream_t s, const int* skip) {
   if (rows == 0) return;
   const size_t smem = (size_t)(64 + 32) * l * sizeof(C);
   auto kfn = apply_kernel<T, C>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<ceil_div(rows, 64), 256, smem, s>>>(rows, l, Y, ldy, Ub, dinv, Ybf, lb, gate);
+  kfn<<<ceil_div(rows, 64), 256, smem, s>>>(rows, l, Y, ldy, Ub, dinv, Ybf, lb, gate, skip);
   note_launch();
 }
 
 template <typename C>
 void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
-                 const int* gate, cudaStream_t s) {
+                 const int* gate, cudaStream_t s, const int* skip) {
   // binary32: 1024 threads; binary64 (l <= 128): 256 threads with room for registers
   constexpr int NT = sizeof(C) == 4 ? 1024 : 256;
   const size_t smem = chol_smem_bytes(l, sizeof(C));
   auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate);
+  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip);
   note_launch();
 }
 
 // ------------------------------------------------- triangular products --
 // C = A B for l x l row-major binary64 upper-triangular A, B (C upper too).
 __global__ void triu_mm_kernel(int l, const double* __restrict__ A, const double* __restrict__ B,
-                               double* __restrict__ Cm, const int* gate, int copy_if_gated) {
+                               double* __restrict__ Cm, const int* gate, int copy_if_gated, const int* skip) {
   const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
   if (i >= l || j >= l) return;
+  if (skip && *skip != 0) return;
   if (gate && *gate == 0) {
     if (copy_if_gated) Cm[(size_t)i * l + j] = B[(size_t)i * l + j];
     return;
@@ -556,9 +558,9 @@ __global__ void triu_mm_kernel(int l, const double* __restrict__ A, const double
 }
 
 void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const int* gate, int copy_if_gated,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int* skip) {
   dim3 grid(ceil_div(l, 16), ceil_div(l, 16));
-  triu_mm_kernel<<<grid, dim3(16, 16), 0, s>>>(l, A, B, Cm, gate, copy_if_gated);
+  triu_mm_kernel<<<grid, dim3(16, 16), 0, s>>>(l, A, B, Cm, gate, copy_if_gated, skip);
   note_launch();
 }
 
@@ -577,7 +579,7 @@ size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize) {
 
 template <typename T, typename C>
 void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
-              DevStatus* st, int sms, cudaStream_t s) {
+              DevStatus* st, int sms, cudaStream_t s, const int* skip) {
   Carver c(ws);
   double* P = c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
   double* G = c.take<double>((size_t)l * l);
@@ -589,26 +591,26 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
   const int* gate3 = &st->shifted;
   for (int pass = 1; pass <= 3; ++pass) {
     const int* gate = pass == 3 ? gate3 : nullptr;
-    launch_gram<T>(rows, l, Y, ldy, P, G, sizeof(C) == 4 ? Gf : nullptr, sms, gate, s);
-    launch_chol<C>(l, G, Gf, Ub, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s);
-    launch_apply<T, C>(rows, l, Y, ldy, Ub, dinv, nullptr, lb, gate, s);
+    launch_gram<T>(rows, l, Y, ldy, P, G, sizeof(C) == 4 ? Gf : nullptr, sms, gate, s, skip);
+    launch_chol<C>(l, G, Gf, Ub, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s, skip);
+    launch_apply<T, C>(rows, l, Y, ldy, Ub, dinv, nullptr, lb, gate, s, skip);
   }
   if (Ybf) launch_copy_bf16<T>(rows, l, Y, ldy, Ybf, lb, s);
   if (Rout) {
     // R = R3 R2 R1 (R3 only if the third pass ran)
-    launch_triu_mm(l, Rp + (size_t)l * l, Rp, Rm, nullptr, 0, s);
-    launch_triu_mm(l, Rp + (size_t)2 * l * l, Rm, Rout, gate3, 1, s);
+    launch_triu_mm(l, Rp + (size_t)l * l, Rp, Rm, nullptr, 0, s, skip);
+    launch_triu_mm(l, Rp + (size_t)2 * l * l, Rm, Rout, gate3, 1, s, skip);
   }
 }
 
 template void run_orth<float, float>(int, int, float*, int, double*, __nv_bfloat16*, int, void*, DevStatus*,
-                                     int, cudaStream_t);
+                                     int, cudaStream_t, const int*);
 template void run_orth<double, double>(int, int, double*, int, double*, __nv_bfloat16*, int, void*,
-                                       DevStatus*, int, cudaStream_t);
+                                       DevStatus*, int, cudaStream_t, const int*);
 template void launch_gram<float>(int, int, const float*, int, double*, double*, float*, int, const int*,
-                                 cudaStream_t);
+                                 cudaStream_t, const int*);
 template void launch_gram<double>(int, int, const double*, int, double*, double*, float*, int, const int*,
-                                  cudaStream_t);
+                                  cudaStream_t, const int*);
 
 // ------------------------------------------------------------ bf16 copy --
 template <typename T>

@@ -22,16 +22,17 @@ void launch_gemm_simt(bool trans, int M, int N, int K, const T* A, int lda, cons
 int gram_splits(int rows, int l, int sms);
 template <typename T>
 void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
-                 cudaStream_t s);
+                 cudaStream_t s, const int* skip = nullptr);
 size_t chol_smem_bytes(int l, size_t csize);
 size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize);
 template <typename T, typename C>
+// skip (optional): every kernel returns at once while *skip != 0 (device-side loop control)
 void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws, DevStatus* st,
-              int sms, cudaStream_t s);
+              int sms, cudaStream_t s, const int* skip = nullptr);
 template <typename T>
 void launch_copy_bf16(int rows, int l, const T* Y, int ldy, __nv_bfloat16* Yb, int lb, cudaStream_t s);
 void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const int* gate, int copy_if_gated,
-                    cudaStream_t s);
+                    cudaStream_t s, const int* skip = nullptr);
 
 // k_svd.cu
 int jacobi_cluster_size(int l);
@@ -55,5 +56,11 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
                            int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm = 0);
 void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb,
                        int sms, cudaStream_t s);
+
+// k_adapt.cu
+size_t adapt_workspace_bytes(int m, int n, int R, int b, int sms, size_t es);
+template <typename T, typename C>
+void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, uint64_t seed, void* ws, void* orthws,
+                  DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout);
 
 }  // namespace rsvd

@@ -300,6 +300,127 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
   return check_launch(h, "rsvd_fixed_rank (mixed)");
 }
 
+// ---------------------------------------------------------- adaptive path --
+struct AdaptParams {
+  int R;  // max rank
+  int b;  // block
+};
+
+AdaptParams adapt_params(int m, int n, const rsvd_params* p) {
+  AdaptParams a;
+  const int mn = m < n ? m : n;
+  const int cap = max_l_for(p->prec);
+  a.b = p->block > 0 ? p->block : 16;
+  a.R = p->max_rank > 0 ? p->max_rank : (mn < cap ? mn : cap);
+  return a;
+}
+
+rsvd_status validate_adaptive(rsvd_handle_t h, int m, int n, const void* A, int lda, const rsvd_params* p) {
+  if (!h) return RSVD_E_INVALID;
+  if (!p) return fail(h, RSVD_E_INVALID, "params is NULL");
+  if (m < 1 || n < 1) return fail(h, RSVD_E_INVALID, "m and n must be >= 1");
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32)
+    return fail(h, RSVD_E_UNSUPPORTED, "rsvd_adaptive_tol supports RSVD_F64 and RSVD_F32");
+  if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  const AdaptParams a = adapt_params(m, n, p);
+  if (a.b < 1 || a.b > 32) return fail(h, RSVD_E_INVALID, "block must lie in [1, 32]");
+  const int mn = m < n ? m : n;
+  if (a.R < 1 || a.R > mn) return fail(h, RSVD_E_INVALID, "max_rank must lie in [1, min(m, n)]");
+  if (a.R > max_l_for(p->prec))
+    return fail(h, RSVD_E_UNSUPPORTED, "max_rank %d exceeds the supported maximum %d", a.R, max_l_for(p->prec));
+  if (lda < n) return fail(h, RSVD_E_INVALID, "lda %d < n %d", lda, n);
+  if (!A) return fail(h, RSVD_E_INVALID, "NULL A");
+  return RSVD_OK;
+}
+
+struct AdaptLayout {
+  DevStatus* st;
+  void* abufs;
+  void* orthws;
+  void* part;
+  double* Rb;
+  void *Wt, *Jt, *Wsel, *Jsel;
+  double* sigma;
+  size_t bytes;
+};
+
+AdaptLayout adapt_layout(void* ws, int m, int n, const rsvd_params* p, int sms) {
+  const AdaptParams a = adapt_params(m, n, p);
+  const size_t es = elem_size(p->prec);
+  Carver c(ws);
+  AdaptLayout L;
+  L.st = c.take<DevStatus>(1);
+  L.abufs = c.take<unsigned char>(adapt_workspace_bytes(m, n, a.R, a.b, sms, es));
+  size_t ow = orth_workspace_bytes(m, a.b, sms, es);
+  const size_t ow2 = orth_workspace_bytes(n, a.R, sms, es);
+  if (ow2 > ow) ow = ow2;
+  L.orthws = c.take<unsigned char>(ow);
+  size_t pw = simt_gemm_workspace(n, a.R, a.R, sms, es);
+  if (sign_workspace_bytes(n, a.R) > pw) pw = sign_workspace_bytes(n, a.R);
+  L.part = c.take<unsigned char>(pw + 256);
+  L.Rb = c.take<double>((size_t)a.R * a.R);
+  L.Wt = c.take<unsigned char>((size_t)a.R * a.R * es);
+  L.Jt = c.take<unsigned char>((size_t)a.R * a.R * es);
+  L.Wsel = c.take<unsigned char>((size_t)a.R * a.R * es);
+  L.Jsel = c.take<unsigned char>((size_t)a.R * a.R * es);
+  L.sigma = c.take<double>((size_t)a.R);
+  L.bytes = c.size();
+  return L;
+}
+
+// Stage B on A ~= Q B (Sec. 3): B^T = Q_B R_B, SVD of R_B^T by one-sided
+// Jacobi, U = Q Uhat, V = Q_B J, sign convention; l = rank columns.
+template <typename T, typename C>
+rsvd_status adapt_stage_b(rsvd_handle_t h, int m, int n, int l, T* Q, int ldq, T* Bt, int ldbt, const AdaptLayout& L,
+                          T* U, int ldu, double* D, T* V, int ldv, cudaStream_t s) {
+  const int sms = h->sms;
+  run_orth<T, C>(n, l, Bt, ldbt, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  cudaError_t e = launch_jacobi<C>(l, L.Rb, (C*)L.Wt, (C*)L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<C>(l, l, L.sigma, (const C*)L.Wt, (const C*)L.Jt, D, (C*)L.Wsel, (C*)L.Jsel, s);
+  launch_gemm_simt<T>(false, n, l, l, Bt, ldbt, (const T*)L.Jsel, l, V, ldv, nullptr, sms, s);
+  launch_sign_fix<T, C>(n, l, l, V, ldv, (C*)L.Wsel, L.part, s);
+  launch_gemm_simt<T>(false, m, l, l, Q, ldq, (const T*)L.Wsel, l, U, ldu, nullptr, sms, s);
+  return check_launch(h, "rsvd_adaptive_tol stage B");
+}
+
+template <typename T, typename C>
+rsvd_status adaptive_impl(rsvd_handle_t h, int m, int n, const T* A, int lda, const rsvd_params* p, T* U, int ldu,
+                          double* D, T* V, int ldv, int* rank_out, double* err_out, const AdaptLayout& L,
+                          cudaStream_t s) {
+  const AdaptParams a = adapt_params(m, n, p);
+  T *Q = nullptr, *Bt = nullptr;
+  cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
+  run_adaptive<T, C>(m, n, A, lda, p->tol, a.R, a.b, p->seed, L.abufs, L.orthws, L.st, h->sms, s, &Q, &Bt);
+  rsvd_status st = check_launch(h, "rsvd_adaptive_tol");
+  if (st != RSVD_OK) return st;
+  // one synchronization: the rank sizes Stage B
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+  DevStatus hs;
+  e = cudaMemcpy(&hs, L.st, sizeof(DevStatus), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "status read: %s", cudaGetErrorString(e));
+  const int rank = hs.rank;
+  if (rank > 0) {
+    st = adapt_stage_b<T, C>(h, m, n, rank, Q, a.R, Bt, a.R, L, U, ldu, D, V, ldv, s);
+    if (st != RSVD_OK) return st;
+  }
+  if (rank < a.R) {  // zero the unused trailing triplets
+    cudaMemsetAsync(D + rank, 0, (size_t)(a.R - rank) * sizeof(double), s);
+    cudaMemset2DAsync(U + rank, (size_t)ldu * sizeof(T), 0, (size_t)(a.R - rank) * sizeof(T), m, s);
+    cudaMemset2DAsync(V + rank, (size_t)ldv * sizeof(T), 0, (size_t)(a.R - rank) * sizeof(T), n, s);
+  }
+  const double err = hs.fro2_a > 0.0 ? sqrt(hs.fro2_res > 0.0 ? hs.fro2_res / hs.fro2_a : 0.0) : 0.0;
+  if (rank_out) cudaMemcpyAsync(rank_out, &L.st->rank, sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (err_out) cudaMemcpyAsync(err_out, &err, sizeof(double), cudaMemcpyHostToDevice, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+  int code = 0;
+  cudaMemcpy(&code, &L.st->code, sizeof(int), cudaMemcpyDeviceToHost);
+  if (code != 0) return fail(h, (rsvd_status)code, "device reported status %d (rank %d)", code, rank);
+  return check_launch(h, "rsvd_adaptive_tol");
+}
+
 rsvd_status finish_sync(rsvd_handle_t h, const rsvd_params* p, DevStatus* st, cudaStream_t s) {
   if (!(p->flags & RSVD_FLAG_SYNC)) return RSVD_OK;
   cudaError_t e = cudaStreamSynchronize(s);
@@ -395,6 +516,12 @@ rsvd_status rsvd_last_error_detail(rsvd_handle_t handle, char* buf, size_t len) 
 
 rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_params* params, size_t* bytes) {
   if (!handle || !params || !bytes) return RSVD_E_INVALID;
+  if (params->tol > 0.0) {
+    rsvd_status st = validate_adaptive(handle, m, n, (const void*)1, n, params);
+    if (st != RSVD_OK) return st;
+    *bytes = adapt_layout(nullptr, m, n, params, handle->sms).bytes;
+    return RSVD_OK;
+  }
   int kk = 0;
   rsvd_status st = validate_fixed(handle, m, n, (const void*)1, n, params, (const void*)1, 1 << 30,
                                   (const void*)1, (const void*)1, 1 << 30, &kk);
@@ -445,9 +572,22 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
 rsvd_status rsvd_adaptive_tol(rsvd_handle_t handle, int m, int n, const void* A, int lda, const rsvd_params* params,
                               void* U, int ldu, double* D, void* V, int ldv, int* rank_out, double* err_out,
                               void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
-  (void)m; (void)n; (void)A; (void)lda; (void)params; (void)U; (void)ldu; (void)D; (void)V; (void)ldv;
-  (void)rank_out; (void)err_out; (void)workspace; (void)ws_bytes; (void)stream;
-  return fail(handle, RSVD_E_UNSUPPORTED, "rsvd_adaptive_tol is not built yet");
+  rsvd_status st = validate_adaptive(handle, m, n, A, lda, params);
+  if (st != RSVD_OK) return st;
+  const AdaptParams a = adapt_params(m, n, params);
+  if (ldu < a.R || ldv < a.R) return fail(handle, RSVD_E_INVALID, "ldu/ldv smaller than max_rank %d", a.R);
+  if (!U || !D || !V) return fail(handle, RSVD_E_INVALID, "NULL output pointer");
+  const AdaptLayout need = adapt_layout(nullptr, m, n, params, handle->sms);
+  if (!workspace || ws_bytes < need.bytes)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need.bytes);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  const AdaptLayout L = adapt_layout(workspace, m, n, params, handle->sms);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (params->prec == RSVD_F64)
+    return adaptive_impl<double, double>(handle, m, n, (const double*)A, lda, params, (double*)U, ldu, D, (double*)V,
+                                         ldv, rank_out, err_out, L, s);
+  return adaptive_impl<float, float>(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv,
+                                     rank_out, err_out, L, s);
 }
 
 rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status, rsvd_stream_t stream) {

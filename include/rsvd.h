@@ -137,6 +137,36 @@ rsvd_status rsvd_adaptive_tol(rsvd_handle_t handle, int m, int n, const void* A,
                               int ldv, int* rank_out, double* err_out, void* workspace,
                               size_t ws_bytes, rsvd_stream_t stream);
 
+/* Batched tolerance-driven randomized SVD: `count` independent binary32
+ * problems, each solved exactly as rsvd_adaptive_tol solves it (Sec. 12.3,
+ * Fig. greedy_blocked, then Stage B of Sec. 3), all in ONE persistent kernel
+ * launch: every CTA of the grid (one per SM) takes the next problem, largest
+ * m n first, from a device-side queue.  The call enqueues one memset and two
+ * kernels and never synchronizes (unless RSVD_FLAG_SYNC), so it can be
+ * captured into a CUDA graph.
+ *   count  : number of problems, 0 <= count <= 65536 (0 enqueues nothing).
+ *   m, n, lda : DEVICE int arrays [count]; 1 <= m, n <= 1024, lda >= n.
+ *   A      : DEVICE array [count] of device pointers to float m x n (row-major).
+ *   U, V   : DEVICE arrays [count] of device pointers to float outputs of
+ *            m x R and n x R, row-major with leading dimension exactly R.
+ *   D      : DEVICE array [count] of device pointers to R doubles.
+ *   rank_out, status_out : DEVICE int arrays [count] (may be NULL).
+ *   err_out: DEVICE double array [count], ||A - Q B||_Fro / ||A||_Fro (may be NULL).
+ * params: prec must be RSVD_F32, q must be 0, tol in (0, 1), block b in
+ * [1, 16] (0 -> 16), max_rank R in [1, 64] (0 -> 64); problem p caps its rank
+ * at min(R, m_p, n_p) and draws its Gaussian blocks from the Philox stream
+ * keyed by params->seed + p.  Entries of D, U, V beyond the rank are zero.
+ * Per-problem failures (sizes out of range, NULL pointers: RSVD_E_INVALID;
+ * breakdown, non-finite values, rank cap reached) go to status_out[p] and the
+ * first of them to the workspace status word. */
+rsvd_status rsvd_batched_workspace_size(rsvd_handle_t handle, int count, const rsvd_params* params,
+                                        size_t* bytes);
+rsvd_status rsvd_batched(rsvd_handle_t handle, int count, const int* m, const int* n,
+                         const void* const* A, const int* lda, const rsvd_params* params,
+                         void* const* U, double* const* D, void* const* V, int* rank_out,
+                         double* err_out, int* status_out, void* workspace, size_t ws_bytes,
+                         rsvd_stream_t stream);
+
 /* Reads the device status word of the last solve that used `workspace`
  * (synchronizes `stream` first).  *status receives an rsvd_status value. */
 rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status,

@@ -48,7 +48,7 @@ EXPORTED = [
     "rsvd_query_status", "rsvd_last_error_detail", "rsvd_philox_words", "rsvd_gaussian",
     "rsvd_sketch_workspace_size", "rsvd_sketch", "rsvd_orth_workspace_size", "rsvd_orth",
     "rsvd_project_workspace_size", "rsvd_project", "rsvd_kernel_launches", "rsvd_profile", "rsvd_profile_read",
-    "rsvd_sketch_noalloc",
+    "rsvd_sketch_noalloc", "rsvd_batched_workspace_size", "rsvd_batched",
 ]
 
 
@@ -100,6 +100,8 @@ def load():
         "rsvd_profile": [vp, i],
         "rsvd_profile_read": [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
         "rsvd_sketch_noalloc": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp],
+        "rsvd_batched_workspace_size": [vp, i, P, ctypes.POINTER(sz)],
+        "rsvd_batched": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -167,6 +169,18 @@ def rsvd_adaptive_tol(h, m, n, A, lda, params, U, ldu, D, V, ldv, rank_out, err_
     return load().rsvd_adaptive_tol(h, m, n, _ptr(A), lda, ctypes.byref(params), _ptr(U), ldu, _ptr(D), _ptr(V),
                                     ldv, _ptr(rank_out), _ptr(err_out), _ptr(ws),
                                     ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_batched_workspace_size(h, count, params):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_batched_workspace_size(h, count, ctypes.byref(params), ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_batched(h, count, m, n, A, lda, params, U, D, V, rank_out, err_out, status_out, ws, stream=None):
+    return load().rsvd_batched(h, count, _ptr(m), _ptr(n), _ptr(A), _ptr(lda), ctypes.byref(params), _ptr(U),
+                               _ptr(D), _ptr(V), _ptr(rank_out), _ptr(err_out), _ptr(status_out), _ptr(ws),
+                               ws.numel() if ws is not None else 0, _stream(stream))
 
 
 def rsvd_query_status(h, ws, stream=None):
@@ -300,6 +314,82 @@ def adaptive_tol(A, tol, block=16, max_rank=0, seed=0, prec=RSVD_F32):
     if code not in (RSVD_OK, RSVD_E_NOT_CONVERGED):
         raise RsvdError(code, last_error(h))
     return U, D, V, int(rank.item()), float(err.item()), code
+
+
+class BatchPlan:
+    """Device-resident arguments and outputs of one rsvd_batched call.
+
+    The count problems' matrices live in one float32 buffer ``A`` (block p at
+    an offset that is a multiple of 4 elements, row-major with lda = n); the
+    outputs in ``U`` (m x R blocks), ``V`` (n x R blocks) and ``D`` (count x R
+    doubles).  The device arrays of sizes and pointers are built once, so a
+    plan can be run many times and captured into a CUDA graph."""
+
+    def __init__(self, shapes, R=64, device="cuda"):
+        import torch
+        self.count, self.R, self.shapes = len(shapes), int(R), [(int(a), int(b)) for a, b in shapes]
+        up4 = lambda x: (x + 3) // 4 * 4
+        self.a_off, self.u_off, self.v_off = [], [], []
+        ta = tu = tv = 0
+        for m, n in self.shapes:
+            self.a_off.append(ta)
+            self.u_off.append(tu)
+            self.v_off.append(tv)
+            ta, tu, tv = ta + up4(m * n), tu + up4(m * R), tv + up4(n * R)
+        f32 = torch.float32
+        self.A = torch.zeros(max(ta, 4), dtype=f32, device=device)
+        self.U = torch.empty(max(tu, 4), dtype=f32, device=device)
+        self.V = torch.empty(max(tv, 4), dtype=f32, device=device)
+        self.D = torch.empty(max(self.count * R, 1), dtype=torch.float64, device=device)
+        i32, i64 = torch.int32, torch.int64
+        self.m = torch.tensor([s[0] for s in self.shapes] or [0], dtype=i32, device=device)
+        self.n = torch.tensor([s[1] for s in self.shapes] or [0], dtype=i32, device=device)
+        self.lda = self.n.clone()
+        base = lambda t, offs, es: torch.tensor([t.data_ptr() + es * o for o in offs] or [0], dtype=i64,
+                                                device=device)
+        self.a_ptr = base(self.A, self.a_off, 4)
+        self.u_ptr = base(self.U, self.u_off, 4)
+        self.v_ptr = base(self.V, self.v_off, 4)
+        self.d_ptr = base(self.D, [p * R for p in range(self.count)], 8)
+        self.rank = torch.zeros(max(self.count, 1), dtype=i32, device=device)
+        self.err = torch.zeros(max(self.count, 1), dtype=torch.float64, device=device)
+        self.status = torch.zeros(max(self.count, 1), dtype=i32, device=device)
+        self.ws = None
+
+    def block(self, p):
+        m, n = self.shapes[p]
+        return self.A[self.a_off[p]:self.a_off[p] + m * n].view(m, n)
+
+    def result(self, p):
+        """(U, D, V) views of problem p: m x R, R, n x R."""
+        m, n = self.shapes[p]
+        R = self.R
+        return (self.U[self.u_off[p]:self.u_off[p] + m * R].view(m, R), self.D[p * R:(p + 1) * R],
+                self.V[self.v_off[p]:self.v_off[p] + n * R].view(n, R))
+
+
+def batched_run(plan, tol, block=16, seed=0, flags=0, stream=None):
+    """Enqueue rsvd_batched for a BatchPlan; returns the call's status (with
+    RSVD_FLAG_SYNC in flags, the first device-side failure)."""
+    h = handle(plan.A.device.index)
+    prm = make_params(0, 0, 0, seed, RSVD_F32, flags, tol=tol, block=block, max_rank=plan.R)
+    if plan.ws is None:
+        plan.ws = _empty_ws(rsvd_batched_workspace_size(h, plan.count, prm), plan.A.device)
+    return rsvd_batched(h, plan.count, plan.m, plan.n, plan.a_ptr, plan.lda, prm, plan.u_ptr, plan.d_ptr,
+                        plan.v_ptr, plan.rank, plan.err, plan.status, plan.ws, stream)
+
+
+def batched(blocks, tol, block=16, max_rank=64, seed=0):
+    """Solve a list of float32 CUDA matrices by rsvd_batched.  Returns
+    (plan, code): plan.result(p), plan.rank, plan.err and plan.status hold
+    the per-problem outputs."""
+    plan = BatchPlan([tuple(b.shape) for b in blocks], R=max_rank, device=blocks[0].device if blocks else "cuda")
+    for p, b in enumerate(blocks):
+        plan.block(p).copy_(b)
+    code = batched_run(plan, tol, block=block, seed=seed, flags=RSVD_FLAG_SYNC)
+    if code not in (RSVD_OK, RSVD_E_NOT_CONVERGED, RSVD_E_INVALID, RSVD_E_BREAKDOWN, RSVD_E_NONFINITE):
+        raise RsvdError(code, last_error(handle(plan.A.device.index)))
+    return plan, code
 
 
 def gaussian(n, l, seed, stream_id=0, col0=0, dtype=None, device="cuda"):

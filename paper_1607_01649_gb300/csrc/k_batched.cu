@@ -1,0 +1,953 @@
+// Batched tolerance-driven randomized SVD: many independent binary32 problems
+// (1 <= m, n <= 1024) in ONE persistent launch.  Each CTA takes problems from a
+// queue ordered largest-first (an atomic counter; nothing waits on another
+// CTA) and runs, for each, the blocked greedy range finder of Sec. 12.3 (Fig.
+// greedy_blocked, with the projection and the double deflation of the
+// single-problem path) and then Stage B of Sec. 3, on its own SM:
+//
+//   A_j = A;  loop while ||A_j||_F > tol ||A||_F and rank < R:
+//     G = randn(n, b) (Philox stream 1, columns b t ..; key = seed + problem)
+//     Y = A_j G;  Y -= Q (Q^T Y);  Q_new = CholeskyQR2(Y)
+//     C1 = Q_new^T A_j;  A_j -= Q_new C1;  C2 = Q_new^T A_j;  A_j -= Q_new C2
+//     B_new = C1 + C2;  Q = [Q Q_new];  B = [B; B_new]
+//   Stage B: B^T = Q_B R_B (CholeskyQR2), one-sided Jacobi on R_B^T,
+//            U = Q Uhat, V = Q_B J, sign convention (largest |v_i| entry > 0).
+//
+// The passes over A_j are fused so that each step reads A_j three times and
+// writes it twice:
+//   pass C   C1 = Q_new^T A_j                         (column-owned threads)
+//   pass U1  A_j -= Q_new C1, C2 = Q_new^T A_j        (column-owned threads)
+//   pass U2  A_j -= Q_new C2, ||A_j||_F^2, Y = A_j G  (row-owned warps)
+// where the Y of pass U2 is the next step's sample, formed before the
+// stopping test (and unused after the last step).  The first step reads A
+// itself and writes the working copy.  Arithmetic is binary32, with binary64
+// norms and binary64 folds of 64-term binary32 partial sums in the reductions
+// over rows; the only waits are CTA barriers.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rsvd {
+
+namespace {
+
+constexpr int BT = 256;      // threads per CTA
+constexpr int BW = BT / 32;  // warps per CTA
+constexpr int BB = 16;       // largest block width b (row stride of Y, G, C)
+constexpr int RMAX = 64;     // rank cap
+constexpr int NMAX = 1024;   // largest m, n
+constexpr int CHUNK = 64;    // binary32 partial-sum length before a binary64 fold
+
+// dynamic shared memory, in floats
+constexpr int SQ_OFF = 0;                   // Y / Q_new, [i][16]   (NMAX x 16)
+constexpr int SG_OFF = NMAX * BB;           // G, [j][16]; partials (NMAX x 16)
+constexpr int SC_OFF = 2 * NMAX * BB;       // C1 / C2, [j][16]     (NMAX x 16)
+constexpr int SP_OFF = 3 * NMAX * BB;       // Q^T Y, [k][16]       (RMAX x 16)
+constexpr int SS_OFF = SP_OFF + RMAX * BB;  // Gram (16 x 16 binary64), L, U of the LU, dinv
+constexpr int SMEM_FLOATS = SS_OFF + 2 * BB * BB + 2 * BB * BB + 2 * BB;
+constexpr size_t SMEM_BYTES = (size_t)SMEM_FLOATS * sizeof(float);
+
+// per-CTA working slot in the workspace, in floats
+constexpr size_t SLOT_FLOATS = (size_t)NMAX * NMAX    // A_j, row stride n
+                               + (size_t)RMAX * NMAX  // Q^T, [k][i]
+                               + (size_t)NMAX * RMAX; // B^T, [j][k]
+
+struct Prob {
+  int m, n, lda;
+  const float* A;
+  float* U;
+  double* D;
+  float* V;
+};
+
+__device__ __forceinline__ double block_sum_f64(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < BW; ++w) s += red[w];  // the same order in every thread
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ void lds16(const float* p, float (&v)[BB]) {
+#pragma unroll
+  for (int c = 0; c < BB; c += 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p + c);
+    v[c] = t.x;
+    v[c + 1] = t.y;
+    v[c + 2] = t.z;
+    v[c + 3] = t.w;
+  }
+}
+
+// ------------------------------------------------------------ Gaussians --
+// G[j][c] for c < bb: column col0 + c of Philox stream 1 under key (k0, k1);
+// element 4 g + t of a column is Box-Muller output t of counter (g, col, 1, 0).
+// Columns bb .. 15 are zero.
+__device__ void gen_gauss(int n, int bb, int col0, uint32_t k0, uint32_t k1, float* sG) {
+  const int groups = (n + 3) >> 2;
+  for (int e = threadIdx.x; e < groups * BB; e += BT) {
+    const int g = e / BB, c = e % BB;
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c < bb) {
+      const Philox4 w = philox4x32_10((uint32_t)g, (uint32_t)(col0 + c), 1u, 0u, k0, k1);
+      box_muller_f32(w.x[0], w.x[1], z[0], z[1]);
+      box_muller_f32(w.x[2], w.x[3], z[2], z[3]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (4 * g + t < n) sG[(4 * g + t) * BB + c] = z[t];
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------- warp reduce-scatter --
+// Sums v[0..63] over the 32 lanes of a warp; afterwards lane l holds the
+// totals of indices scatter_index64(l) and scatter_index64(l) + 1 in v[0] and
+// v[1].  At partner offset o the lane keeps the upper half of its values if
+// (lane & o) is set, else the lower half, and adds the partner's copy of it.
+__device__ __forceinline__ void warp_reduce_scatter64(float (&v)[64]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int o = 16 >> s;
+    const int half = 32 >> s;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = up ? v[k] : v[k + half];
+      const float keep = up ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+// Lane bits 16, 8, 4, 2, 1 chose index bits 32, 16, 8, 4, 2.
+__device__ __forceinline__ int scatter_index64(int lane) {
+  return ((lane >> 4) & 1) * 32 + ((lane >> 3) & 1) * 16 + ((lane >> 2) & 1) * 8 + ((lane >> 1) & 1) * 4 +
+         (lane & 1) * 2;
+}
+
+// ------------------------------------------------------- row-owned pass --
+// Warp w takes row groups of 4 rows, lanes take columns lane, lane + 32, ...
+// For every element:
+//   a = src(i, j) [- sum_c q(i, c) C(c, j)]        (UPD; q = sQ rows, C = sC)
+//   dst(i, j) = a                                  (UPD)
+//   norm += a^2
+//   y(i, c) += a G(j, c)                           (AG)
+// y overwrites the rows of sQ the warp owns, after their q has been read.
+// Returns ||a||_F^2 (binary64; the same value in every thread).
+template <bool UPD, bool AG>
+__device__ double pass_rows(int m, int n, const float* src, int lds, float* dst, float* sQ, const float* sC,
+                            const float* sG, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double norm = 0.0;
+  for (int i0 = 4 * warp; i0 < m; i0 += 4 * BW) {
+    const int rows = min(4, m - i0);
+    float q[4][BB];
+    if (UPD) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) lds16(sQ + min(i0 + r, m - 1) * BB, q[r]);
+    }
+    float y[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) y[k] = 0.f;
+    float nrm = 0.f;
+    const float* s0 = src + (size_t)i0 * lds;
+    float* d0 = UPD ? dst + (size_t)i0 * n : nullptr;
+    for (int j = lane; j < n; j += 32) {
+      float a[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = r < rows ? s0[(size_t)r * lds + j] : 0.f;
+      if (UPD) {
+        float cj[BB];
+        lds16(sC + j * BB, cj);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (r < rows) {
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < BB; ++c) s = fmaf(q[r][c], cj[c], s);
+            a[r] -= s;
+            d0[(size_t)r * n + j] = a[r];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) nrm = fmaf(a[r], a[r], nrm);
+      if (AG) {
+        float g[BB];
+        lds16(sG + j * BB, g);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < BB; ++c) y[r * BB + c] = fmaf(a[r], g[c], y[r * BB + c]);
+      }
+    }
+    norm += (double)nrm;
+    if (AG) {
+      warp_reduce_scatter64(y);
+      const int idx = scatter_index64(lane);  // idx and idx + 1 lie in one row
+      const int r = idx / BB, c = idx % BB;
+      __syncwarp();
+      if (r < rows) {
+        sQ[(i0 + r) * BB + c] = y[0];
+        sQ[(i0 + r) * BB + c + 1] = y[1];
+      }
+    }
+  }
+  return block_sum_f64(norm, red);
+}
+
+// ---------------------------------------------------- column-owned passes --
+// The CTA is split into `groups` row groups of `ncol` threads (ncol = 32, 64,
+// 128 or 256: the smallest power-of-two multiple of 32 covering n, at most
+// 256); thread tj of group g owns column j0 + tj and rows g, g + groups, ...
+struct ColSplit {
+  int ncol, groups;
+};
+__device__ __forceinline__ ColSplit col_split(int n) {
+  int ncol = 32;
+  while (ncol < n && ncol < BT) ncol <<= 1;
+  return ColSplit{ncol, BT / ncol};
+}
+
+// UPD = false (pass C):  sC[j][c] = sum_i Q_new(i, c) src(i, j)
+// UPD = true  (pass U1): with C1 = sC on entry,
+//     dst(i, j) = src(i, j) - sum_c Q_new(i, c) C1(c, j),
+//     sC[j][c]  = sum_i Q_new(i, c) dst(i, j)                  (C2)
+//     Bt[j][k0 + c] = C1(c, j) + C2(c, j)   for c < bb
+// Row-group partial sums meet in `part` (binary64, in the sG region).
+template <bool UPD>
+__device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, const float* sQ, float* sC,
+                          double* part, float* Bt, int k0, int bb) {
+  const ColSplit cs = col_split(n);
+  const int g = threadIdx.x / cs.ncol, tj = threadIdx.x % cs.ncol;
+  for (int j0 = 0; j0 < n; j0 += cs.ncol) {
+    const int j = j0 + tj;
+    const bool live = j < n;
+    float c1[BB];
+    if (UPD) {
+#pragma unroll
+      for (int c = 0; c < BB; ++c) c1[c] = live ? sC[j * BB + c] : 0.f;
+    }
+    double acc64[BB];
+    float acc[BB];
+#pragma unroll
+    for (int c = 0; c < BB; ++c) {
+      acc64[c] = 0.0;
+      acc[c] = 0.f;
+    }
+    if (live) {
+      int cnt = 0;
+      for (int i = g; i < m; i += cs.groups) {
+        float a = src[(size_t)i * lds + j];
+        float qi[BB];
+        lds16(sQ + i * BB, qi);
+        if (UPD) {
+          float s = 0.f;
+#pragma unroll
+          for (int c = 0; c < BB; ++c) s = fmaf(qi[c], c1[c], s);
+          a -= s;
+          dst[(size_t)i * n + j] = a;
+        }
+#pragma unroll
+        for (int c = 0; c < BB; ++c) acc[c] = fmaf(qi[c], a, acc[c]);
+        if (++cnt == CHUNK) {
+#pragma unroll
+          for (int c = 0; c < BB; ++c) {
+            acc64[c] += (double)acc[c];
+            acc[c] = 0.f;
+          }
+          cnt = 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < BB; ++c) acc64[c] += (double)acc[c];
+    if (cs.groups > 1) {  // then ncol >= n and this loop runs once
+      __syncthreads();    // the sG region is free for the partials
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < BB; ++c) part[((size_t)g * cs.ncol + tj) * BB + c] = acc64[c];
+      }
+      __syncthreads();
+      if (g == 0 && live) {
+#pragma unroll
+        for (int c = 0; c < BB; ++c) {
+          double s = 0.0;
+          for (int h = 0; h < cs.groups; ++h) s += part[((size_t)h * cs.ncol + tj) * BB + c];
+          acc64[c] = s;
+        }
+      }
+    }
+    if (g == 0 && live) {
+#pragma unroll
+      for (int c = 0; c < BB; ++c) sC[j * BB + c] = (float)acc64[c];
+      if (UPD) {
+#pragma unroll
+        for (int c = 0; c < BB; ++c)
+          if (c < bb) Bt[(size_t)j * RMAX + k0 + c] = (float)((double)c1[c] + acc64[c]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------- small algebra --
+// Gram of the rows x l block Y (row stride ldy >= 16, l <= 16, columns l..15
+// zero) into g64 (l x l, binary64).  Warp w sums rows w, w + 8, ...; lane
+// holds the pairs (lane / 2, 8 (lane % 2) + 0..7); binary32 partials of 64
+// rows are folded into binary64.
+__device__ void gram16(int rows, int l, const float* Y, int ldy, double* g64, double* wpart) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c1 = lane >> 1, cb = (lane & 1) * 8;
+  double acc64[8];
+  float acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    acc64[k] = 0.0;
+    acc[k] = 0.f;
+  }
+  int cnt = 0;
+  for (int i = warp; i < rows; i += BW) {
+    const float a = Y[i * ldy + c1];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = fmaf(a, Y[i * ldy + cb + k], acc[k]);
+    if (++cnt == CHUNK) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        acc64[k] += (double)acc[k];
+        acc[k] = 0.f;
+      }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) wpart[(warp * BB + c1) * BB + cb + k] = acc64[k] + (double)acc[k];
+  __syncthreads();
+  for (int e = threadIdx.x; e < l * l; e += BT) {
+    const int i = e / l, j = e % l;
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < BW; ++w) s += wpart[(w * BB + i) * BB + j];
+    g64[e] = s;
+  }
+  __syncthreads();
+}
+
+// Gram of a rows x l block (l <= 64) in global memory with row stride ldy:
+// one thread per upper-triangle entry, binary32 partials of 64 rows.
+__device__ void gram_wide(int rows, int l, const float* Y, int ldy, double* g64) {
+  const int nent = l * (l + 1) / 2;
+  for (int e = threadIdx.x; e < nent; e += BT) {
+    int i = 0, rem = e;
+    while (rem >= l - i) {
+      rem -= l - i;
+      ++i;
+    }
+    const int j = i + rem;
+    double acc = 0.0;
+    for (int r0 = 0; r0 < rows; r0 += CHUNK) {
+      float part = 0.f;
+      const int r1 = min(rows, r0 + CHUNK);
+      for (int r = r0; r < r1; ++r) part = fmaf(Y[(size_t)r * ldy + i], Y[(size_t)r * ldy + j], part);
+      acc += (double)part;
+    }
+    g64[i * l + j] = acc;
+    g64[j * l + i] = acc;
+  }
+  __syncthreads();
+}
+
+// Cholesky of the unit-diagonal scaling D G D (D = diag(G_ii^-1/2)) by ONE
+// warp (no CTA barriers): the binary32 lower factor goes to L (l x l,
+// row-major, l <= 64) and D to dinv.  On a non-positive pivot the
+// factorization restarts with a diagonal shift (shifted CholeskyQR, Fukaya et
+// al. 2020), growing 32x per retry.  Returns false (in lane 0's view and
+// every other lane's) if every shift failed; the caller's CTA barrier
+// publishes L and dinv.
+__device__ bool chol_warp(int l, const double* g64, float* L, float* dinv) {
+  const int lane = threadIdx.x & 31;
+  const float u = 5.9604644775390625e-08f;
+  float shift = 0.f;
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    for (int e = lane; e < l * l; e += 32) {
+      const int i = e / l, j = e % l;
+      const double gii = g64[i * l + i], gjj = g64[j * l + j];
+      const float di = gii > 0.0 ? (float)(1.0 / sqrt(gii)) : 0.f;
+      const float dj = gjj > 0.0 ? (float)(1.0 / sqrt(gjj)) : 0.f;
+      float v = (float)g64[e] * di * dj;
+      if (i == j) v = (gii > 0.0 ? 1.f : 0.f) + shift;
+      L[e] = (i >= j) ? v : 0.f;
+      if (i == j) dinv[i] = di;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < l; ++k) {
+      const float akk = L[k * l + k];  // the same value in every lane
+      if (!(akk > 64.f * u) || !isfinite(akk)) {
+        ok = false;
+        break;
+      }
+      const float rp = 1.f / sqrtf(akk);
+      for (int i = k + 1 + lane; i < l; i += 32) L[i * l + k] *= rp;
+      __syncwarp();
+      if (lane == 0) L[k * l + k] = akk * rp;
+      const int nr = l - k - 1;
+      for (int e = lane; e < nr * nr; e += 32) {
+        const int i = k + 1 + e / nr, j = k + 1 + e % nr;
+        if (j <= i) L[i * l + j] = fmaf(-L[i * l + k], L[j * l + k], L[i * l + j]);
+      }
+      __syncwarp();
+    }
+    if (ok) return true;
+    shift = shift == 0.f ? 64.f * 11.f * (float)l * u : shift * 32.f;
+  }
+  return false;
+}
+
+// In place Y <- Y D L^-T (rows x l, row stride ldy): a thread per row.
+__device__ void apply_rows(int rows, int l, float* Y, int ldy, const float* L, const float* dinv) {
+  for (int r = threadIdx.x; r < rows; r += BT) {
+    float* y = Y + (size_t)r * ldy;
+    for (int c = 0; c < l; ++c) {
+      float s = y[c] * dinv[c];
+      for (int k = 0; k < c; ++k) s = fmaf(-y[k], L[c * l + k], s);
+      y[c] = s / L[c * l + c];
+    }
+  }
+  __syncthreads();
+}
+
+// LU factorization with partial pivoting of the rows x l block Y (row stride
+// ldy, l <= 64), in place and without moving rows: afterwards Y holds L (row
+// p_k carries the unit pivot of column k and zeros to its right) and U (l x
+// l, row-major, upper) the other factor, Y_in = L U.  A column with no nonzero
+// candidate pivot takes the lowest unused row as its unit column of L and a
+// zero diagonal in U.  Two CTA barriers per column.
+__device__ void lu_rows(int rows, int l, float* Y, int ldy, float* U, unsigned char* used, float* rv, int* ri) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < rows; i += BT) used[i] = 0;
+  __syncthreads();
+  for (int k = 0; k < l; ++k) {
+    // pivot: the largest |Y(i, k)| over unused rows (lowest row on ties)
+    float bv = -1.f;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < rows; i += BT) {
+      if (used[i]) continue;
+      const float a = fabsf(Y[(size_t)i * ldy + k]);
+      if (a > bv) {  // rows visited in increasing order: ties keep the lower row
+        bv = a;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      rv[warp] = bv;
+      ri[warp] = bi;
+    }
+    __syncthreads();
+    float pv = -1.f;
+    int p = 0x7fffffff;
+#pragma unroll
+    for (int w = 0; w < BW; ++w) {
+      if (rv[w] > pv || (rv[w] == pv && ri[w] < p)) {
+        pv = rv[w];
+        p = ri[w];
+      }
+    }
+    // p < rows always: rows >= l and only k < l rows are used
+    const float* yp = Y + (size_t)p * ldy;
+    const float piv = yp[k];
+    for (int j = threadIdx.x; j < l; j += BT) U[k * l + j] = j >= k ? yp[j] : 0.f;
+    const float rpiv = piv != 0.f ? 1.f / piv : 0.f;
+    if (threadIdx.x == 0) used[p] = 1;  // read again only after the next barrier
+    for (int i = threadIdx.x; i < rows; i += BT) {
+      if (used[i] || i == p) continue;
+      float* yi = Y + (size_t)i * ldy;
+      const float lik = yi[k] * rpiv;
+      yi[k] = lik;
+      for (int j = k + 1; j < l; ++j) yi[j] = fmaf(-lik, yp[j], yi[j]);
+    }
+    __syncthreads();
+    // row p becomes the unit pivot row of L: it is used, so no later column of
+    // this factorization reads it; the final barrier orders it before any use
+    for (int j = k + threadIdx.x; j < l; j += BT) Y[(size_t)p * ldy + j] = j == k ? 1.f : 0.f;
+  }
+  __syncthreads();
+}
+
+// Gram of Y (binary32 partials folded into binary64) and its warp Cholesky
+// into L, dinv; false (in every thread) if the Cholesky failed.
+template <bool GLOBAL>
+__device__ bool chol_factor(int rows, int l, const float* Y, int ldy, double* g64, double* wpart, float* L,
+                            float* dinv, int* s_flag) {
+  if (GLOBAL) gram_wide(rows, l, Y, ldy, g64);
+  else gram16(rows, l, Y, ldy, g64, wpart);
+  if (threadIdx.x < 32) {
+    const bool ok = chol_warp(l, g64, L, dinv);
+    if (threadIdx.x == 0) *s_flag = ok ? 0 : 1;
+  }
+  __syncthreads();
+  const int f = *s_flag;
+  __syncthreads();
+  return f == 0;
+}
+
+// Thin QR of the rows x l block Y in place by LU-Cholesky QR (Terao, Ozaki,
+// Ogita 2020): Y = L U by lu_rows, then CholeskyQR2 of the well-conditioned
+// L (binary32 Gram folded into binary64, warp Cholesky, triangular solve), so
+// that Y_in = Q R with R = R2 R1 U.  Holds for any kappa(Y) below the binary32
+// limit, where CholeskyQR2 of Y itself would lose orthogonality.  R
+// (optional, l x l row-major upper) needs Rt and Ra as scratch.  Returns false
+// if the Cholesky failed after every shift.
+template <bool GLOBAL>
+__device__ bool lu_cholqr2(int rows, int l, float* Y, int ldy, double* g64, double* wpart, float* L, float* dinv,
+                           float* Ulu, float* R, float* Rt, unsigned char* used, float* rv, int* ri, int* s_flag) {
+  lu_rows(rows, l, Y, ldy, Ulu, used, rv, ri);
+  if (R) {
+    for (int e = threadIdx.x; e < l * l; e += BT) R[e] = Ulu[e];
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    if (!chol_factor<GLOBAL>(rows, l, Y, ldy, g64, wpart, L, dinv, s_flag)) return false;
+    if (R) {
+      // R <- (L^T D^-1) R, both upper, in place: a thread per column; going
+      // top-down, row i reads only rows k >= i of its column, still the old ones
+      for (int e = threadIdx.x; e < l * l; e += BT) {
+        const int i = e / l, j = e % l;
+        Rt[e] = (i <= j && dinv[j] > 0.f) ? L[j * l + i] / dinv[j] : 0.f;
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < l; j += BT) {
+        for (int i = 0; i < l; ++i) {
+          float s = 0.f;
+          for (int k = i; k <= j; ++k) s = fmaf(Rt[i * l + k], R[k * l + j], s);
+          R[i * l + j] = i <= j ? s : 0.f;
+        }
+      }
+    }
+    apply_rows(rows, l, Y, ldy, L, dinv);
+  }
+  return true;
+}
+
+// Y -= Q (Q^T Y) for the rows x 16 block Y in shared memory (row stride 16)
+// and the rank columns of Q stored transposed (Qt[k][i], row stride NMAX);
+// P (rank x 16) is scratch.  A warp per k forms P, a thread per row applies it.
+__device__ void project_out(int rows, int rank, const float* Qt, float* Y, float* P) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < rank; k += BW) {
+    float acc[BB];
+#pragma unroll
+    for (int c = 0; c < BB; ++c) acc[c] = 0.f;
+    for (int i = lane; i < rows; i += 32) {
+      const float qv = Qt[(size_t)k * NMAX + i];
+      float yi[BB];
+      lds16(Y + i * BB, yi);
+#pragma unroll
+      for (int c = 0; c < BB; ++c) acc[c] = fmaf(qv, yi[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < BB; ++c) {
+      float v = acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) P[k * BB + c] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows; i += BT) {
+    float acc[BB];
+#pragma unroll
+    for (int c = 0; c < BB; ++c) acc[c] = 0.f;
+    for (int k = 0; k < rank; ++k) {
+      const float qv = Qt[(size_t)k * NMAX + i];
+      float pk[BB];
+      lds16(P + k * BB, pk);
+#pragma unroll
+      for (int c = 0; c < BB; ++c) acc[c] = fmaf(qv, pk[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < BB; ++c) Y[i * BB + c] -= acc[c];
+  }
+  __syncthreads();
+}
+
+// One-sided Jacobi on the columns of X (l x l, column c at X + c l),
+// accumulating the rotations in J (same layout, identity on entry).  Round-
+// robin pair order, one warp per pair, at most 30 sweeps.
+__device__ void jacobi_cols(int l, float* X, float* J, int* s_cnt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = (l & 1) ? l + 1 : l;
+  const float tol = 4.f * (float)l * 5.9604644775390625e-08f;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (threadIdx.x == 0) *s_cnt = 0;
+    __syncthreads();
+    for (int step = 0; step < P - 1; ++step) {
+      for (int pr = warp; pr < P / 2; pr += BW) {
+        const int ia = pr == 0 ? 0 : 1 + (pr - 1 + step) % (P - 1);
+        const int qq = P - 1 - pr;
+        const int ib = 1 + (qq - 1 + step) % (P - 1);
+        if (ia >= l || ib >= l) continue;
+        float* xa = X + ia * l;
+        float* xb = X + ib * l;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < l; i += 32) {
+          const float a = xa[i], b = xb[i];
+          al = fmaf(a, a, al);
+          be = fmaf(b, b, be);
+          ga = fmaf(a, b, ga);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+          const float cs = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+          float* ja = J + ia * l;
+          float* jb = J + ib * l;
+          for (int i = lane; i < l; i += 32) {
+            const float a = xa[i], b = xb[i];
+            xa[i] = cs * a - sn * b;
+            xb[i] = sn * a + cs * b;
+            const float p = ja[i], w = jb[i];
+            ja[i] = cs * p - sn * w;
+            jb[i] = sn * p + cs * w;
+          }
+          if (lane == 0) atomicAdd(s_cnt, 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int cnt = *s_cnt;
+    __syncthreads();
+    if (cnt == 0) break;
+  }
+}
+
+// ------------------------------------------------------------- a problem --
+// CTA-shared scalars and small arrays (static shared memory)
+struct Work {
+  double* red;          // BW binary64 partial sums
+  float* rv;            // BW pivot magnitudes
+  int* ri;              // BW pivot rows
+  int* flag;            // one int
+  unsigned char* used;  // NMAX row flags of the LU
+};
+
+__device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R, int b, float* base, float* sm,
+                          const Work& W, int* rank_out, double* err_out, int* status_out, DevStatus* st) {
+  double* red = W.red;
+  const int m = P.m, n = P.n, tid = threadIdx.x;
+  float* Aj = base;
+  float* Qt = Aj + (size_t)NMAX * NMAX;
+  float* Bt = Qt + (size_t)RMAX * NMAX;
+  float* sQ = sm + SQ_OFF;
+  float* sG = sm + SG_OFF;
+  float* sC = sm + SC_OFF;
+  float* sP = sm + SP_OFF;
+  double* g16 = reinterpret_cast<double*>(sm + SS_OFF);  // 16 x 16 binary64
+  float* sL = sm + SS_OFF + 2 * BB * BB;
+  float* sU = sL + BB * BB;
+  float* sDinv = sU + BB * BB;
+  double* wpart = reinterpret_cast<double*>(sG);  // 8 x 16 x 16 binary64 Gram partials
+  const int rmax = min(R, min(m, n));
+  const uint64_t key = seed + (uint64_t)p;
+  const uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
+  int status = RSVD_OK;
+
+  // first pass: Y = A G_0 and ||A||_F^2
+  int bb = min(b, rmax);
+  gen_gauss(n, bb, 0, k0, k1, sG);
+  const double a2 = pass_rows<false, true>(m, n, P.A, P.lda, nullptr, sQ, sC, sG, red);
+  const double eps2 = tol * tol * a2;
+  double r2 = a2;
+  const float* src = P.A;
+  int lds = P.lda;
+  int rank = 0, t = 0;
+  while (!(r2 <= eps2) && rank < rmax) {
+    if (!isfinite(r2)) {
+      status = RSVD_E_NONFINITE;
+      break;
+    }
+    bb = min(b, rmax - rank);
+    if (rank > 0) project_out(m, rank, Qt, sQ, sP);
+    // Q_new = CholeskyQR2(Y)
+    if (!lu_cholqr2<false>(m, bb, sQ, BB, g16, wpart, sL, sDinv, sU, nullptr, nullptr, W.used, W.rv, W.ri,
+                           W.flag)) {
+      status = RSVD_E_BREAKDOWN;
+      break;
+    }
+    if (rank > 0) {
+      // Q_new = qr(Y R^-1) amplifies what round-off left of span(Q) in Y by up
+      // to kappa(Y): project once more and renormalize (block Gram-Schmidt,
+      // twice), so that Q^T Q_new stays at the binary32 round-off level
+      for (int e = tid; e < m * BB; e += BT)
+        if (e % BB >= bb) sQ[e] = 0.f;
+      __syncthreads();
+      project_out(m, rank, Qt, sQ, sP);
+      if (!chol_factor<false>(m, bb, sQ, BB, g16, wpart, sL, sDinv, W.flag)) {
+        status = RSVD_E_BREAKDOWN;
+        break;
+      }
+      apply_rows(m, bb, sQ, BB, sL, sDinv);
+    }
+    for (int e = tid; e < m * BB; e += BT) {
+      const int i = e / BB, c = e % BB;
+      if (c >= bb) sQ[e] = 0.f;
+      else Qt[(size_t)(rank + c) * NMAX + i] = sQ[e];
+    }
+    __syncthreads();
+    pass_cols<false>(m, n, src, lds, nullptr, sQ, sC, reinterpret_cast<double*>(sG), Bt, rank, bb);
+    pass_cols<true>(m, n, src, lds, Aj, sQ, sC, reinterpret_cast<double*>(sG), Bt, rank, bb);
+    src = Aj;
+    lds = n;
+    const int bnext = min(b, rmax - rank - bb);
+    if (bnext > 0) {
+      gen_gauss(n, bnext, (t + 1) * b, k0, k1, sG);
+      r2 = pass_rows<true, true>(m, n, Aj, n, Aj, sQ, sC, sG, red);
+    } else {
+      r2 = pass_rows<true, false>(m, n, Aj, n, Aj, sQ, sC, sG, red);
+    }
+    rank += bb;
+    ++t;
+  }
+  if (status == RSVD_OK && !isfinite(r2)) status = RSVD_E_NONFINITE;
+  if (status == RSVD_OK && !(r2 <= eps2)) status = RSVD_E_NOT_CONVERGED;
+  __syncthreads();
+
+  // Stage B on A ~= Q B with l = rank
+  const int l = rank;
+  const bool have = l > 0 && status != RSVD_E_BREAKDOWN && status != RSVD_E_NONFINITE;
+  bool ok = true;
+  if (have) {
+    double* g64 = reinterpret_cast<double*>(sG);     // l x l binary64
+    float* Xc = sG + 2 * RMAX * RMAX;                // l x l, column c at Xc + c l
+    float* Jm = Xc + RMAX * RMAX;                    // l x l
+    float* L = sC;                                   // l x l
+    float* Rb = L + RMAX * RMAX;                     // R_B
+    float* Rt = Rb + RMAX * RMAX;                    // scratch
+    float* Ulu = Rt + RMAX * RMAX;                   // U of the LU
+    float* dv = sP;                                  // l
+    float* sig = dv + RMAX;                          // l
+    int* perm = reinterpret_cast<int*>(sig + RMAX);  // l
+    ok = lu_cholqr2<true>(n, l, Bt, RMAX, g64, nullptr, L, dv, Ulu, Rb, Rt, W.used, W.rv, W.ri, W.flag);
+    if (ok) {
+      for (int e = tid; e < l * l; e += BT) {  // X = R_B^T: column c is row c of R_B
+        const int c = e / l, r = e % l;
+        Xc[e] = Rb[c * l + r];
+        Jm[e] = c == r ? 1.f : 0.f;
+      }
+      __syncthreads();
+      jacobi_cols(l, Xc, Jm, W.flag);
+      for (int c = tid; c < l; c += BT) {
+        float s = 0.f;
+        for (int r = 0; r < l; ++r) s = fmaf(Xc[c * l + r], Xc[c * l + r], s);
+        sig[c] = sqrtf(s);
+      }
+      __syncthreads();
+      for (int c = tid; c < l; c += BT) {  // descending; ties by index
+        int rk = 0;
+        for (int c2 = 0; c2 < l; ++c2) rk += (sig[c2] > sig[c]) || (sig[c2] == sig[c] && c2 < c);
+        perm[rk] = c;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * l; e += BT) {  // V = Q_B J
+        const int j = e / l, k = e % l, sc = perm[k];
+        float s = 0.f;
+        for (int c = 0; c < l; ++c) s = fmaf(Bt[(size_t)j * RMAX + c], Jm[sc * l + c], s);
+        P.V[(size_t)j * R + k] = s;
+      }
+      for (int e = tid; e < m * l; e += BT) {  // U = Q X / sigma
+        const int i = e / l, k = e % l, sc = perm[k];
+        const float inv = sig[sc] > 0.f ? 1.f / sig[sc] : 0.f;
+        float s = 0.f;
+        for (int c = 0; c < l; ++c) s = fmaf(Qt[(size_t)c * NMAX + i], Xc[sc * l + c], s);
+        P.U[(size_t)i * R + k] = s * inv;
+      }
+      for (int k = tid; k < l; k += BT) P.D[k] = (double)sig[perm[k]];
+      __syncthreads();
+      // sign convention: the largest |V(:, k)| entry (lowest row on ties) is positive
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int k = warp; k < l; k += BW) {
+        float best = -1.f;
+        int bi = 0x7fffffff;
+        for (int j = lane; j < n; j += 32) {
+          const float a = fabsf(P.V[(size_t)j * R + k]);
+          if (a > best) {
+            best = a;
+            bi = j;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        const bool flip = bi < n && P.V[(size_t)bi * R + k] < 0.f;
+        __syncwarp();
+        if (flip) {
+          for (int j = lane; j < n; j += 32) P.V[(size_t)j * R + k] = -P.V[(size_t)j * R + k];
+          for (int i = lane; i < m; i += 32) P.U[(size_t)i * R + k] = -P.U[(size_t)i * R + k];
+        }
+      }
+    } else {
+      status = RSVD_E_BREAKDOWN;
+    }
+  }
+  __syncthreads();
+  // zero the triplets past the rank (all of them when nothing was factored)
+  const int lz = (have && ok) ? l : 0;
+  for (int k = lz + tid; k < R; k += BT) P.D[k] = 0.0;
+  if (lz < R) {
+    const int w = R - lz;
+    for (int e = tid; e < m * w; e += BT) P.U[(size_t)(e / w) * R + lz + e % w] = 0.f;
+    for (int e = tid; e < n * w; e += BT) P.V[(size_t)(e / w) * R + lz + e % w] = 0.f;
+  }
+  if (tid == 0) {
+    if (rank_out) rank_out[p] = lz;
+    if (err_out) err_out[p] = a2 > 0.0 ? sqrt(fmax(r2, 0.0) / a2) : 0.0;
+    if (status_out) status_out[p] = status;
+    if (status != RSVD_OK) set_status(st, status);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(BT, 1)
+    batched_kernel(int count, const int* __restrict__ order, const int* __restrict__ pm, const int* __restrict__ pn,
+                   const int* __restrict__ plda, const float* const* __restrict__ pA, float* const* __restrict__ pU,
+                   double* const* __restrict__ pD, float* const* __restrict__ pV, int R, int b, uint64_t seed,
+                   double tol, int* counter, float* slots, int* rank_out, double* err_out, int* status_out,
+                   DevStatus* st) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double red[BW];
+  __shared__ float rv[BW];
+  __shared__ int ri[BW];
+  __shared__ int s_idx, s_flag;
+  __shared__ unsigned char used[NMAX];
+  const Work W{red, rv, ri, &s_flag, used};
+  float* base = slots + (size_t)blockIdx.x * SLOT_FLOATS;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= count) break;
+    const int p = order[idx];
+    Prob P;
+    P.m = pm[p];
+    P.n = pn[p];
+    P.lda = plda[p];
+    P.A = pA[p];
+    P.U = pU[p];
+    P.D = pD[p];
+    P.V = pV[p];
+    const bool valid = P.m >= 1 && P.n >= 1 && P.m <= NMAX && P.n <= NMAX && P.lda >= P.n && P.A && P.U && P.D &&
+                       P.V;
+    if (!valid) {
+      if (threadIdx.x == 0) {
+        if (rank_out) rank_out[p] = 0;
+        if (err_out) err_out[p] = 0.0;
+        if (status_out) status_out[p] = RSVD_E_INVALID;
+        set_status(st, RSVD_E_INVALID);
+      }
+      continue;
+    }
+    solve_one(P, p, seed, tol, R, b, base, sm, W, rank_out, err_out, status_out, st);
+  }
+}
+
+// order[r] = the problem of rank r in descending m n (ties: lower index
+// first); problems with invalid sizes sort last.
+__device__ __forceinline__ long long size_key(const int* pm, const int* pn, int q) {
+  const int m = pm[q], n = pn[q];
+  return (m >= 1 && n >= 1 && m <= NMAX && n <= NMAX) ? (long long)m * n : 0;
+}
+
+__global__ void batched_order_kernel(int count, const int* __restrict__ pm, const int* __restrict__ pn,
+                                     int* __restrict__ order) {
+  __shared__ long long keys[BT];
+  const int p = blockIdx.x * BT + threadIdx.x;
+  const long long kp = p < count ? size_key(pm, pn, p) : -1;
+  int rk = 0;
+  for (int t0 = 0; t0 < count; t0 += BT) {
+    __syncthreads();
+    const int q = t0 + threadIdx.x;
+    keys[threadIdx.x] = q < count ? size_key(pm, pn, q) : -1;
+    __syncthreads();
+    const int lim = min(BT, count - t0);
+    for (int u = 0; u < lim; ++u) {
+      const long long k = keys[u];
+      rk += (k > kp) || (k == kp && t0 + u < p);
+    }
+  }
+  if (p < count) order[rk] = p;
+}
+
+}  // namespace
+
+int batched_max_rank() { return RMAX; }
+int batched_max_dim() { return NMAX; }
+int batched_max_block() { return BB; }
+
+size_t batched_workspace_bytes(int count, int ctas) {
+  Carver c(nullptr);
+  c.take<DevStatus>(1);
+  c.take<int>(1);              // queue counter
+  c.take<int>((size_t)count);  // order
+  c.take<float>(SLOT_FLOATS * (size_t)ctas);
+  return c.size();
+}
+
+cudaError_t launch_batched(int count, const int* m, const int* n, const int* lda, const float* const* A,
+                           float* const* U, double* const* D, float* const* V, int R, int b, uint64_t seed,
+                           double tol, int* rank_out, double* err_out, int* status_out, void* ws, int ctas,
+                           cudaStream_t s) {
+  Carver c(ws);
+  DevStatus* st = c.take<DevStatus>(1);
+  int* counter = c.take<int>(1);
+  int* order = c.take<int>((size_t)count);
+  float* slots = c.take<float>(SLOT_FLOATS * (size_t)ctas);
+  cudaError_t e = cudaMemsetAsync(st, 0, 512, s);  // the status block and the counter (two 256-byte slices)
+  if (e != cudaSuccess) return e;
+  batched_order_kernel<<<(count + BT - 1) / BT, BT, 0, s>>>(count, m, n, order);
+  note_launch();
+  // the shared-memory opt-in is set once per device, outside any later graph capture
+  static std::atomic<unsigned long long> smem_set{0};
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(smem_set.load() & bit)) {
+    e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    smem_set.fetch_or(bit);
+  }
+  const int grid = count < ctas ? count : ctas;
+  batched_kernel<<<grid, BT, SMEM_BYTES, s>>>(count, order, m, n, lda, A, U, D, V, R, b, seed, tol, counter, slots,
+                                              rank_out, err_out, status_out, st);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rsvd

@@ -63,4 +63,14 @@ template <typename T, typename C>
 void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, uint64_t seed, void* ws, void* orthws,
                   DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout);
 
+// k_batched.cu
+int batched_max_rank();
+int batched_max_dim();
+int batched_max_block();
+size_t batched_workspace_bytes(int count, int ctas);
+cudaError_t launch_batched(int count, const int* m, const int* n, const int* lda, const float* const* A,
+                           float* const* U, double* const* D, float* const* V, int R, int b, uint64_t seed,
+                           double tol, int* rank_out, double* err_out, int* status_out, void* ws, int ctas,
+                           cudaStream_t s);
+
 }  // namespace rsvd

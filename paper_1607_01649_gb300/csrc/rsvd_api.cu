@@ -590,6 +590,59 @@ rsvd_status rsvd_adaptive_tol(rsvd_handle_t handle, int m, int n, const void* A,
                                      rank_out, err_out, L, s);
 }
 
+namespace {
+
+constexpr int BATCHED_MAX_COUNT = 65536;
+
+rsvd_status validate_batched(rsvd_handle_t h, int count, const rsvd_params* p, int* R, int* b) {
+  if (!h) return RSVD_E_INVALID;
+  if (!p) return fail(h, RSVD_E_INVALID, "params is NULL");
+  if (count < 0 || count > BATCHED_MAX_COUNT)
+    return fail(h, RSVD_E_INVALID, "count %d outside [0, %d]", count, BATCHED_MAX_COUNT);
+  if (p->prec != RSVD_F32) return fail(h, RSVD_E_UNSUPPORTED, "rsvd_batched supports RSVD_F32");
+  if (p->q != 0) return fail(h, RSVD_E_UNSUPPORTED, "rsvd_batched has no power steps (q must be 0)");
+  if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  *b = p->block > 0 ? p->block : batched_max_block();
+  if (*b < 1 || *b > batched_max_block())
+    return fail(h, RSVD_E_INVALID, "block must lie in [1, %d]", batched_max_block());
+  *R = p->max_rank > 0 ? p->max_rank : batched_max_rank();
+  if (*R < 1 || *R > batched_max_rank())
+    return fail(h, RSVD_E_INVALID, "max_rank must lie in [1, %d]", batched_max_rank());
+  return RSVD_OK;
+}
+
+}  // namespace
+
+rsvd_status rsvd_batched_workspace_size(rsvd_handle_t handle, int count, const rsvd_params* params, size_t* bytes) {
+  int R = 0, b = 0;
+  if (!bytes) return RSVD_E_INVALID;
+  rsvd_status st = validate_batched(handle, count, params, &R, &b);
+  if (st != RSVD_OK) return st;
+  *bytes = batched_workspace_bytes(count, handle->sms);
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_batched(rsvd_handle_t handle, int count, const int* m, const int* n, const void* const* A,
+                         const int* lda, const rsvd_params* params, void* const* U, double* const* D, void* const* V,
+                         int* rank_out, double* err_out, int* status_out, void* workspace, size_t ws_bytes,
+                         rsvd_stream_t stream) {
+  int R = 0, b = 0;
+  rsvd_status st = validate_batched(handle, count, params, &R, &b);
+  if (st != RSVD_OK) return st;
+  if (count == 0) return RSVD_OK;
+  if (!m || !n || !A || !lda || !U || !D || !V) return fail(handle, RSVD_E_INVALID, "NULL array argument");
+  const size_t need = batched_workspace_bytes(count, handle->sms);
+  if (!workspace || ws_bytes < need)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e =
+      launch_batched(count, m, n, lda, (const float* const*)A, (float* const*)U, D, (float* const*)V, R, b,
+                     params->seed, params->tol, rank_out, err_out, status_out, workspace, handle->sms, s);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_batched launch: %s", cudaGetErrorString(e));
+  return finish_sync(handle, params, (DevStatus*)workspace, s);
+}
+
 rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status, rsvd_stream_t stream) {
   if (!handle || !workspace || !status) return RSVD_E_INVALID;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

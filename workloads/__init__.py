@@ -163,16 +163,37 @@ def block_seed(seed, b):
     return z ^ (z >> 31)
 
 
-def kernel_block(b, seed=4001, lo=64, hi=1024, dtype=np.float32):
-    """Block b of the batched workload: A_ij = 1 / |x_i - y_j| with x_i ~ U([0,1]^3)
-    and y_j ~ U([0,1]^3) + (3, 0, 0); m, n ~ U{lo..hi}."""
+def kernel_block_points(b, seed=4001, lo=64, hi=1024):
+    """Point clouds of block b: x_i ~ U([0,1]^3) (m points) and
+    y_j ~ U([0,1]^3) + (3, 0, 0) (n points), m, n ~ U{lo..hi}."""
     rng = np.random.default_rng(block_seed(seed, b))
     m = int(rng.integers(lo, hi + 1))
     n = int(rng.integers(lo, hi + 1))
     x = rng.random((m, 3))
     y = rng.random((n, 3)) + np.array([3.0, 0.0, 0.0])
-    d = np.sqrt(((x[:, None, :] - y[None, :, :]) ** 2).sum(axis=2))
-    return (1.0 / d).astype(dtype)
+    return x, y
+
+
+def kernel_block(b, seed=4001, lo=64, hi=1024, dtype=np.float32):
+    """Block b of the batched workload: A_ij = 1 / |x_i - y_j| (binary64, then
+    rounded to dtype) for the point clouds of kernel_block_points."""
+    x, y = kernel_block_points(b, seed, lo, hi)
+    d = x[:, None, :] - y[None, :, :]
+    r = np.sqrt((d[:, :, 0] * d[:, :, 0] + d[:, :, 1] * d[:, :, 1]) + d[:, :, 2] * d[:, :, 2])
+    return (1.0 / r).astype(dtype)
+
+
+def kernel_block_torch(b, out, seed=4001, lo=64, hi=1024):
+    """kernel_block(b) formed on out's device into the float32 tensor `out`
+    (m x n), with the same binary64 operations in the same order."""
+    torch = _torch()
+    x, y = kernel_block_points(b, seed, lo, hi)
+    xt = torch.from_numpy(x).to(out.device)
+    yt = torch.from_numpy(y).to(out.device)
+    d = xt[:, None, :] - yt[None, :, :]
+    r = torch.sqrt((d[:, :, 0] * d[:, :, 0] + d[:, :, 1] * d[:, :, 1]) + d[:, :, 2] * d[:, :, 2])
+    out.copy_((1.0 / r).to(torch.float32))
+    return out
 
 
 def kernel_blocks(count=4096, seed=4001, lo=64, hi=1024, dtype=np.float32):

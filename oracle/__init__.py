@@ -16,6 +16,13 @@ Parity status per function:
   eps-rank from a full SVD, span equivalence with the block method).
 * certificate, spectral_residual: pinned (eq. (infomm), Lemma
   thm:aposteriori statistically, direct 2-norm on small cases).
+* controller (probe features, MLP forward / loss / gradient, Adam step,
+  decision rule, labels from the adaptive ranks, residual estimate): pinned
+  (sigma(Q G) = sigma(G) through eigvalsh, scale invariance, hand-built
+  networks, uniform-logit loss, central finite differences, the closed-form
+  first Adam step, brute-force label and eps-rank checks, eq. (infomm) and
+  Lemma thm:aposteriori over seeds).  What the trained network predicts has
+  no pin: it is judged by the gain it brings, not by parity.
 """
 from .philox import (philox4x32_10, gaussian, omega_words, box_muller, seed_key,
                      STREAM_SKETCH, STREAM_ADAPTIVE, STREAM_CERTIFY, STREAM_ADAPTIVE2, STREAM_NORM)
@@ -23,3 +30,4 @@ from .rsvd import orth, sign_normalize, stage_b, rsvd_basic, rsvd_power, rsvd_po
 from .norms import fro_residual, spectral_residual, certificate, theorem_bounds
 from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_finder,
                        adaptive_range_finder)
+from . import controller

@@ -18,7 +18,9 @@ Workload families (sizes are parameters; the defaults are the full sizes):
                          column-centred, 1,048,576 x 4096, float32.
 * ``kernel_blocks``      4096 blocks 1/|x_i - y_j| between point clouds in unit
                          cubes whose centres are 3 apart, m, n ~ U{64..1024}.
-* ``spectrum``           the decay laws used by the controller stream.
+* ``controller_matrix``  the learned-controller stream: square n x n, n
+                         log-uniform, spectra exp(-j/r), j^-alpha or a step,
+                         with permuted, signed DCT-II factors.
 
 Numpy generators (``numpy.random.default_rng(seed)``) are used for anything the
 CPU oracle must reproduce; the full-size float32 matrices are synthesized with
@@ -206,3 +208,97 @@ def kernel_block_shapes(count=4096, seed=4001, lo=64, hi=1024):
         rng = np.random.default_rng(block_seed(seed, b))
         out.append((int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1))))
     return out
+
+
+# ------------------------------------------------- controller stream -------
+CONTROLLER_KINDS = ("exp", "poly", "step")
+
+
+def controller_case(seed, lo=512, hi=16384):
+    """One matrix of the controller stream: size n log-uniform in [lo, hi]
+    (square), spectrum drawn uniformly among exp(-j/r) (r ~ U{16..256}),
+    j^-alpha (alpha ~ U[0.5, 2]) and a step at rank r ~ U{16..256} followed
+    by 1e-6.  Returns (n, sigma (length n), kind, parameter)."""
+    rng = np.random.default_rng(int(seed))
+    n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+    n = max(lo, min(hi, n))
+    kind = CONTROLLER_KINDS[int(rng.integers(0, 3))]
+    j = np.arange(1, n + 1, dtype=np.float64)
+    if kind == "exp":
+        r = int(rng.integers(16, 257))
+        return n, np.exp(-j / r), kind, float(r)
+    if kind == "poly":
+        alpha = float(rng.uniform(0.5, 2.0))
+        return n, j ** (-alpha), kind, alpha
+    r = int(rng.integers(16, 257))
+    s = np.full(n, 1e-6)
+    s[:min(r, n)] = 1.0
+    return n, s, kind, float(r)
+
+
+def dct_factor_np(rng, n):
+    """Orthonormal n x n factor: the orthonormal DCT-II matrix with its rows
+    randomly permuted and signed (a cheap dense stand-in for a Haar factor;
+    the randomized range finder's error law under a Gaussian test matrix
+    depends only on the singular values)."""
+    k = np.arange(n, dtype=np.float64)[:, None]
+    i = np.arange(n, dtype=np.float64)[None, :]
+    C = np.sqrt(2.0 / n) * np.cos(np.pi * (2.0 * i + 1.0) * k / (2.0 * n))
+    C[0, :] *= 1.0 / np.sqrt(2.0)
+    perm = rng.permutation(n)
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    return C.T[perm, :] * sign[:, None]
+
+
+def controller_matrix_np(seed, lo=512, hi=16384, dtype=np.float32):
+    """Dense A = U diag(sigma) V^T of controller_case(seed), U and V from
+    dct_factor_np, formed in float64 and rounded to dtype."""
+    n, sig, kind, par = controller_case(seed, lo, hi)
+    rng = np.random.default_rng(int(seed) + 7919)
+    U = dct_factor_np(rng, n)
+    V = dct_factor_np(rng, n)
+    return ((U * sig[None, :]) @ V.T).astype(dtype), (n, kind, par)
+
+
+def controller_matrix(seed, lo=512, hi=16384, device="cuda"):
+    """controller_matrix_np(seed) synthesized on `device` as float32: the
+    same factors, formed with torch in float64 up to n = 4096 and in float32
+    (without TF32) above."""
+    torch = _torch()
+    n, sig, kind, par = controller_case(seed, lo, hi)
+    rng = np.random.default_rng(int(seed) + 7919)
+    perm_u = rng.permutation(n)
+    sign_u = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    perm_v = rng.permutation(n)
+    sign_v = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    k = torch.arange(n, dtype=torch.float64, device=device)[:, None]
+    i = torch.arange(n, dtype=torch.float64, device=device)[None, :]
+    C = math.sqrt(2.0 / n) * torch.cos(math.pi * (2.0 * i + 1.0) * k / (2.0 * n))
+    C[0, :] *= 1.0 / math.sqrt(2.0)
+    Ct = C.T.contiguous()
+    del C
+    U = Ct[torch.from_numpy(perm_u).to(device), :] * torch.from_numpy(sign_u).to(device)[:, None]
+    V = Ct[torch.from_numpy(perm_v).to(device), :] * torch.from_numpy(sign_v).to(device)[:, None]
+    del Ct
+    U.mul_(torch.from_numpy(sig).to(device)[None, :])
+    if n > 4096:
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        try:
+            A = U.to(torch.float32) @ V.to(torch.float32).T
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    else:
+        A = (U @ V.T).to(torch.float32)
+    del U, V
+    return A, (n, kind, par)
+
+
+def mlp_init(seed, d_in=17, hid=128, n_out=20):
+    """Initial controller parameters (He-normal weights, zero biases) as one
+    flat float64 array in the order W1, b1, W2, b2, W3, b3."""
+    rng = np.random.default_rng(int(seed))
+    W1 = rng.standard_normal((hid, d_in)) * math.sqrt(2.0 / d_in)
+    W2 = rng.standard_normal((hid, hid)) * math.sqrt(2.0 / hid)
+    W3 = rng.standard_normal((n_out, hid)) * math.sqrt(1.0 / hid)
+    return np.concatenate([W1.ravel(), np.zeros(hid), W2.ravel(), np.zeros(hid), W3.ravel(), np.zeros(n_out)])

@@ -80,7 +80,7 @@ enum {
   RSVD_FLAG_RETURN_FULL_L = 1, /* return all l = k + p triplets instead of k */
   RSVD_FLAG_SYNC = 2,          /* block until the work ends; return the device status */
   RSVD_FLAG_CERTIFY = 4,       /* reserved: a-posteriori certificate (Sec. 14) */
-  RSVD_FLAG_USE_CONTROLLER = 8 /* reserved: learned (l, q) controller */
+  RSVD_FLAG_USE_CONTROLLER = 8 /* rsvd_adaptive_tol: learned (l, q) controller */
 };
 
 typedef struct {
@@ -126,6 +126,18 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
  * the Frobenius norm of the explicitly updated remainder, Sec. 12.4):
  * blocks of b Gaussian columns (Philox stream 1, block t = columns t*b ..)
  * are drawn until ||A - Q B||_Fro <= tol ||A||_Fro, then Stage B runs on B.
+ * params->q in [0, 8] power steps per block (the power variant in the
+ * caption of Fig. greedy_blocked: Y = (A_j A_j^T)^q A_j G, with orth between
+ * products).
+ * With RSVD_FLAG_USE_CONTROLLER (prec RSVD_F32 or RSVD_MIXED_BF16; m, n >= 16;
+ * parameters attached by rsvd_controller_attach): a 16-column probe and the
+ * network choose (l, q); rsvd_fixed_rank runs with k = l, p = 0 in `prec`;
+ * the residual is estimated with 16 columns of Philox stream 2 (Sec. 14); if
+ * the estimate meets the tolerance the result is truncated to the smallest
+ * rank whose estimated error still meets it, otherwise (and if l < max_rank)
+ * the plain binary32 adaptive range finder (q = 0) recomputes the result.
+ * That path synchronizes the stream twice (to read the choice and the judge's
+ * verdict).
  *   U, V : capacity max_rank columns (ldu, ldv >= max_rank).
  *   rank_out : DEVICE int, receives the rank r (a multiple of b, or max_rank).
  *   err_out  : DEVICE double, receives ||A - Q B||_Fro / ||A||_Fro.
@@ -230,6 +242,75 @@ rsvd_status rsvd_project(rsvd_handle_t handle, int prec, int m, int n, int l, co
 rsvd_status rsvd_kernel_launches(rsvd_handle_t handle, long long* count);
 rsvd_status rsvd_profile(rsvd_handle_t handle, int on);
 rsvd_status rsvd_profile_read(rsvd_handle_t handle, int kind, double* total_ms, long long* launches);
+
+/* ---------------------------------------------------------------------------
+ * Learned (l, q) controller (the paper has no learned component; the probe is
+ * Fig. RSVD of Sec. 4 with l = 16, the labels come from the tolerance-driven
+ * range finder of Sec. 12.3, Fig. greedy_blocked, and the judge is the
+ * a-posteriori estimate of Sec. 13-14, eq. (infomm) and Lemma
+ * thm:aposteriori).
+ *
+ * Network: x (17 floats) -> h1 = relu(W1 x + b1) (128) -> h2 = relu(W2 h1 + b2)
+ * (128) -> z = W3 h2 + b3 (20).  z[0..15] are the logits of l = 16 (c + 1),
+ * c = 0..15; z[16..19] the logits of q = 0..3.  The parameters are one
+ * DEVICE array of RSVD_CTRL_PARAMS floats: W1 (128 x 17, row-major
+ * [out][in]), b1 (128), W2 (128 x 128), b2 (128), W3 (20 x 128), b3 (20).
+ * The caller owns it (the handle only keeps the pointer).
+ * Features x: log10(sigma_i / sigma_1) of the probe Y = A G (G = the first 16
+ * columns of the Omega stream of rsvd_fixed_rank), i = 2..16, clipped below at
+ * -3, then log2(m) / 16 and log2(n) / 16.
+ * ------------------------------------------------------------------------- */
+#define RSVD_CTRL_D_IN 17
+#define RSVD_CTRL_HIDDEN 128
+#define RSVD_CTRL_OUT 20
+#define RSVD_CTRL_PARAMS 21396
+
+/* Probe features of a float m x n matrix A (lda), m, n >= 16:
+ *   feat : DEVICE float[17] (the network input above);
+ *   fro2 : DEVICE double, ||A||_F^2 (may be NULL).
+ * One pass over A (the 16-column sketch and the squares are fused). */
+rsvd_status rsvd_probe_workspace_size(rsvd_handle_t handle, int m, int n, size_t* bytes);
+rsvd_status rsvd_probe_features(rsvd_handle_t handle, int m, int n, const float* A, int lda, uint64_t seed,
+                                float* feat, double* fro2, void* workspace, size_t ws_bytes, rsvd_stream_t stream);
+
+/* Network evaluation and training on the GPU.  X: DEVICE batch x 17 floats;
+ * yl: DEVICE int[batch], l classes in [0, 15]; yq: DEVICE int[batch], q in
+ * [0, 3] (labels outside these ranges are clamped into them); lam >= 0: weight of the penalty on the probability of a too small l.
+ * Loss (mean over the batch):
+ *   -log p_l[yl] - log p_q[yq] + lam * sum_{c < yl} p_l[c],  p = softmax per head.
+ *   rsvd_mlp_forward   : logits (DEVICE batch x 20); needs no workspace.
+ *   rsvd_mlp_grad      : grad (DEVICE RSVD_CTRL_PARAMS floats) of the loss,
+ *                        loss (DEVICE double).
+ *   rsvd_mlp_train_step: one Adam step (Kingma and Ba 2015; beta1 0.9, beta2
+ *                        0.999, eps 1e-8, step >= 1) on theta with moments m1,
+ *                        m2 (DEVICE, RSVD_CTRL_PARAMS floats each, zero before
+ *                        step 1); loss (DEVICE double, may be NULL) receives
+ *                        the loss before the step.
+ * Gradients are summed over CTAs in a fixed order: results are reproducible. */
+rsvd_status rsvd_mlp_workspace_size(rsvd_handle_t handle, int batch, size_t* bytes);
+rsvd_status rsvd_mlp_forward(rsvd_handle_t handle, int batch, const float* X, const float* theta, float* logits,
+                             rsvd_stream_t stream);
+rsvd_status rsvd_mlp_grad(rsvd_handle_t handle, int batch, const float* X, const int* yl, const int* yq, float lam,
+                          const float* theta, float* grad, double* loss, void* workspace, size_t ws_bytes,
+                          rsvd_stream_t stream);
+rsvd_status rsvd_mlp_train_step(rsvd_handle_t handle, int batch, const float* X, const int* yl, const int* yq,
+                                float lam, float* theta, float* m1, float* m2, int step, float lr, double* loss,
+                                void* workspace, size_t ws_bytes, rsvd_stream_t stream);
+
+/* Attaches trained parameters (DEVICE, caller-owned, kept alive by the caller
+ * while attached; NULL detaches) to the handle for rsvd_adaptive_tol with
+ * RSVD_FLAG_USE_CONTROLLER.  quantile in (0, 1]: l is the smallest class whose
+ * cumulative probability reaches it (larger = more conservative); safety in
+ * (0, 1]: a prediction is accepted when the residual estimate is at most
+ * safety * tol * ||A||_F. */
+rsvd_status rsvd_controller_attach(rsvd_handle_t handle, const float* theta, double quantile, double safety);
+
+/* Host-side record of the last controlled solve on this handle:
+ * info[0] = l chosen, info[1] = q chosen, info[2] = accepted by the judge,
+ * info[3] = fell back to the adaptive range finder, info[4] = output rank;
+ * est[0] = Frobenius residual estimate / ||A||_F, est[1] = spectral bound /
+ * ||A||_F (Lemma thm:aposteriori).  info: 5 ints, est: 2 doubles (host). */
+rsvd_status rsvd_controller_last(rsvd_handle_t handle, int* info, double* est);
 
 /* Allocation-free variant of rsvd_sketch for RSVD_MIXED_BF16 (the paper has
  * no counterpart: this is a deployment convenience).  For callers that may

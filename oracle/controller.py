@@ -39,7 +39,7 @@ N_L = 16
 N_Q = 4
 N_OUT = N_L + N_Q
 PROBE = 16
-FEAT_FLOOR = -12.0
+FEAT_FLOOR = -3.0
 Q_CHOICES = (0, 1, 2, 3)
 L_STEP = 16
 
@@ -81,7 +81,9 @@ def probe_singular_values(A, seed):
 
 def features(sig, m, n):
     """Controller input: log10(sigma_i / sigma_1) for i = 2..16, clipped below
-    at -12, then log2(m) / 16 and log2(n) / 16."""
+    at -3, then log2(m) / 16 and log2(n) / 16.  (The floor is a reading: a
+    binary32 probe resolves singular-value ratios only down to about
+    sqrt(u32) ~ 2.4e-4, so ratios below 1e-3 carry no reliable information.)"""
     sig = np.asarray(sig, dtype=np.float64)
     f = np.full(D_IN, FEAT_FLOOR)
     if sig[0] > 0:

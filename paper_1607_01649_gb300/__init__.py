@@ -49,7 +49,14 @@ EXPORTED = [
     "rsvd_sketch_workspace_size", "rsvd_sketch", "rsvd_orth_workspace_size", "rsvd_orth",
     "rsvd_project_workspace_size", "rsvd_project", "rsvd_kernel_launches", "rsvd_profile", "rsvd_profile_read",
     "rsvd_sketch_noalloc", "rsvd_batched_workspace_size", "rsvd_batched",
+    "rsvd_probe_workspace_size", "rsvd_probe_features", "rsvd_mlp_workspace_size", "rsvd_mlp_forward",
+    "rsvd_mlp_grad", "rsvd_mlp_train_step", "rsvd_controller_attach", "rsvd_controller_last",
 ]
+
+CTRL_D_IN = 17
+CTRL_HIDDEN = 128
+CTRL_OUT = 20
+CTRL_PARAMS = 21396
 
 
 class Params(ctypes.Structure):
@@ -102,6 +109,14 @@ def load():
         "rsvd_sketch_noalloc": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp],
         "rsvd_batched_workspace_size": [vp, i, P, ctypes.POINTER(sz)],
         "rsvd_batched": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp],
+        "rsvd_probe_workspace_size": [vp, i, i, ctypes.POINTER(sz)],
+        "rsvd_probe_features": [vp, i, i, vp, i, u64, vp, vp, vp, sz, vp],
+        "rsvd_mlp_workspace_size": [vp, i, ctypes.POINTER(sz)],
+        "rsvd_mlp_forward": [vp, i, vp, vp, vp, vp],
+        "rsvd_mlp_grad": [vp, i, vp, vp, vp, ctypes.c_float, vp, vp, vp, vp, sz, vp],
+        "rsvd_mlp_train_step": [vp, i, vp, vp, vp, ctypes.c_float, vp, vp, vp, i, ctypes.c_float, vp, vp, sz, vp],
+        "rsvd_controller_attach": [vp, vp, ctypes.c_double, ctypes.c_double],
+        "rsvd_controller_last": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -244,6 +259,50 @@ def rsvd_sketch_noalloc(h, trans, m, n, l, A, lda, X, ldx, Y, ldy, stream=None):
     return load().rsvd_sketch_noalloc(h, trans, m, n, l, _ptr(A), lda, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream))
 
 
+def rsvd_probe_workspace_size(h, m, n):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_probe_workspace_size(h, m, n, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_probe_features(h, m, n, A, lda, seed, feat, fro2, ws, stream=None):
+    return load().rsvd_probe_features(h, m, n, _ptr(A), lda, seed, _ptr(feat), _ptr(fro2), _ptr(ws),
+                                      ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_mlp_workspace_size(h, batch):
+    out = ctypes.c_size_t()
+    _check(load().rsvd_mlp_workspace_size(h, batch, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_mlp_forward(h, batch, X, theta, logits, stream=None):
+    return load().rsvd_mlp_forward(h, batch, _ptr(X), _ptr(theta), _ptr(logits), _stream(stream))
+
+
+def rsvd_mlp_grad(h, batch, X, yl, yq, lam, theta, grad, loss, ws, stream=None):
+    return load().rsvd_mlp_grad(h, batch, _ptr(X), _ptr(yl), _ptr(yq), lam, _ptr(theta), _ptr(grad), _ptr(loss),
+                                _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_mlp_train_step(h, batch, X, yl, yq, lam, theta, m1, m2, step, lr, loss, ws, stream=None):
+    return load().rsvd_mlp_train_step(h, batch, _ptr(X), _ptr(yl), _ptr(yq), lam, _ptr(theta), _ptr(m1), _ptr(m2),
+                                      step, lr, _ptr(loss), _ptr(ws), ws.numel() if ws is not None else 0,
+                                      _stream(stream))
+
+
+def rsvd_controller_attach(h, theta, quantile=0.9, safety=0.8):
+    return load().rsvd_controller_attach(h, _ptr(theta), quantile, safety)
+
+
+def rsvd_controller_last(h):
+    info = (ctypes.c_int * 5)()
+    est = (ctypes.c_double * 2)()
+    _check(load().rsvd_controller_last(h, info, est), h)
+    return {"l": info[0], "q": info[1], "accepted": bool(info[2]), "fallback": bool(info[3]), "rank": info[4],
+            "est_rel": est[0], "spec_bound_rel": est[1]}
+
+
 def rsvd_kernel_launches(h):
     out = ctypes.c_longlong()
     _check(load().rsvd_kernel_launches(h, ctypes.byref(out)), h)
@@ -294,14 +353,17 @@ def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws
     return U, D, V
 
 
-def adaptive_tol(A, tol, block=16, max_rank=0, seed=0, prec=RSVD_F32):
-    """Tolerance-driven randomized SVD by rsvd_adaptive_tol.  Returns
-    (U, D, V, rank, err, status): U, V have max_rank columns, the first `rank`
-    valid; status is RSVD_OK or RSVD_E_NOT_CONVERGED (other failures raise)."""
+def adaptive_tol(A, tol, block=16, max_rank=0, seed=0, prec=RSVD_F32, q=0, controller=False):
+    """Tolerance-driven randomized SVD by rsvd_adaptive_tol (q power steps per
+    block; with controller=True the learned controller attached to the
+    device's handle chooses (l, q)).  Returns (U, D, V, rank, err, status):
+    U, V have max_rank columns, the first `rank` valid; status is RSVD_OK or
+    RSVD_E_NOT_CONVERGED (other failures raise)."""
     import torch
     h = handle(A.device.index)
     m, n = A.shape
-    prm = make_params(0, 0, 0, seed, prec, 0, tol=tol, block=block, max_rank=max_rank)
+    flags = RSVD_FLAG_USE_CONTROLLER if controller else 0
+    prm = make_params(0, 0, q, seed, prec, flags, tol=tol, block=block, max_rank=max_rank)
     R = max_rank if max_rank > 0 else min(m, n, 128 if prec == RSVD_F64 else 256)
     dt = _prec_dtype(prec)
     U = torch.empty(m, R, dtype=dt, device=A.device)
@@ -449,3 +511,87 @@ def orth(Y, prec=RSVD_F32, want_r=True):
     if st != RSVD_OK:
         raise RsvdError(st, "orth device status")
     return Q, R
+
+
+# ----------------------------------------------------- learned controller --
+def probe_features(A, seed=0):
+    """(features (17 floats, CUDA tensor), ||A||_F^2) of a float32 CUDA matrix."""
+    import torch
+    h = handle(A.device.index)
+    m, n = A.shape
+    feat = torch.empty(CTRL_D_IN, dtype=torch.float32, device=A.device)
+    fro2 = torch.empty(1, dtype=torch.float64, device=A.device)
+    ws = _empty_ws(rsvd_probe_workspace_size(h, m, n), A.device)
+    _check(rsvd_probe_features(h, m, n, A, A.stride(0), seed, feat, fro2, ws), h)
+    return feat, fro2
+
+
+def mlp_forward(X, theta):
+    import torch
+    h = handle(X.device.index)
+    logits = torch.empty(X.shape[0], CTRL_OUT, dtype=torch.float32, device=X.device)
+    _check(rsvd_mlp_forward(h, X.shape[0], X, theta, logits), h)
+    return logits
+
+
+def mlp_grad(X, yl, yq, lam, theta):
+    import torch
+    h = handle(X.device.index)
+    grad = torch.empty(CTRL_PARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float64, device=X.device)
+    ws = _empty_ws(rsvd_mlp_workspace_size(h, X.shape[0]), X.device)
+    _check(rsvd_mlp_grad(h, X.shape[0], X, yl, yq, lam, theta, grad, loss, ws), h)
+    return grad, loss
+
+
+class Trainer:
+    """Adam training of the controller network on the GPU through
+    rsvd_mlp_train_step.  theta (float32 CUDA tensor of CTRL_PARAMS) is
+    updated in place."""
+
+    def __init__(self, theta, lr=1e-3, lam=0.5):
+        import torch
+        self.theta, self.lr, self.lam = theta, float(lr), float(lam)
+        self.m1 = torch.zeros_like(theta)
+        self.m2 = torch.zeros_like(theta)
+        self.t = 0
+        self.h = handle(theta.device.index)
+        self.ws = None
+        self.loss = torch.zeros(1, dtype=torch.float64, device=theta.device)
+
+    def step(self, X, yl, yq):
+        if self.ws is None or self.ws.numel() < rsvd_mlp_workspace_size(self.h, X.shape[0]):
+            self.ws = _empty_ws(rsvd_mlp_workspace_size(self.h, X.shape[0]), X.device)
+        self.t += 1
+        _check(rsvd_mlp_train_step(self.h, X.shape[0], X, yl, yq, self.lam, self.theta, self.m1, self.m2, self.t,
+                                   self.lr, self.loss, self.ws), self.h)
+        return self.loss
+
+
+L_STEP = 16
+N_L_CLASSES = 16
+
+
+def label_from_ranks(ranks, converged):
+    """Training label (l class, q) from the adaptive ranks l_q, q = 0..3: the q
+    that meets the tolerance with the least sketch work (2q + 2) l_q, ties to
+    the smaller q; (15, 2) when none met it."""
+    best = None
+    for q, (r, ok) in enumerate(zip(ranks, converged)):
+        if ok and (best is None or (2 * q + 2) * r < best[0]):
+            best = ((2 * q + 2) * r, q, r)
+    if best is None:
+        return N_L_CLASSES - 1, 2
+    _, q, r = best
+    return min(max((r + L_STEP - 1) // L_STEP - 1, 0), N_L_CLASSES - 1), q
+
+
+def adaptive_labels(A, tol, seed=0, max_rank=256, block=16):
+    """Ranks l_q of rsvd_adaptive_tol (binary32, power steps q = 0..3) and the
+    label they give."""
+    ranks, conv = [], []
+    for q in range(4):
+        _, _, _, r, _, code = adaptive_tol(A, tol, block=block, max_rank=max_rank, seed=seed, q=q)
+        ranks.append(r)
+        conv.append(code == RSVD_OK)
+    return ranks, conv, label_from_ranks(ranks, conv)

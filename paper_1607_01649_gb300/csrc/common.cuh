@@ -28,6 +28,22 @@ struct DevStatus {
 };
 static_assert(sizeof(DevStatus) <= 256, "status block fits its slot");
 
+// Device-side record of one controller decision (probe, network, judge).
+struct RsvdCtrlBlock {
+  int l_hat, q_hat;       // the network's choice
+  int accepted;           // judge: residual estimate within tolerance
+  int rank;               // judge: truncation rank
+  int jacobi_sweeps;      // probe: sweeps of the 16 x 16 eigen-solve
+  int pad[3];
+  double fro2;            // ||A||_F^2
+  double est2;            // mean_i ||E(:, i)||^2 (Frobenius estimate, squared)
+  double spec_bound;      // 10 sqrt(2/pi) max_i ||E(:, i)||
+  double pad2;
+  double sigma[16];       // probe singular values, descending
+  float feat[RSVD_CTRL_D_IN];
+  float logits[RSVD_CTRL_OUT];
+};
+
 __device__ __forceinline__ void set_status(DevStatus* st, int code) {
   atomicCAS(&st->code, 0, code);
 }

@@ -7,6 +7,8 @@
 // One step t (b = block columns, tb = t * b columns accepted so far):
 //   G_t  = randn(n, b), columns tb .. tb + b - 1 of Philox stream 1
 //   Y    = A_j G_t                        -> written into Q(:, tb : tb + b)
+//   q times (power variant of the figure's caption, orth between products):
+//          Y = orth(Y);  Z = orth(A_j^T Y);  Y = A_j Z
 //   Y   -= Q(:, :tb) (Q(:, :tb)^T Y)      (no-op in exact arithmetic; keeps Q orthonormal)
 //   Q_new = orth(Y)                       (CholeskyQR2, in place)
 //   B_new^T = A_j^T Q_new                 -> Bt(:, tb : tb + b)
@@ -303,8 +305,8 @@ AdaptBufs<T> adapt_carve(void* ws, int m, int n, int R, int b) {
 // factorization A ~= Q B, st->rank the rank, st->fro2_res and st->fro2_a the
 // squared norms.
 template <typename T, typename C>
-void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, uint64_t seed, void* ws, void* orthws,
-                  DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout) {
+void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, int q, uint64_t seed, void* ws,
+                  void* orthws, DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout) {
   AdaptBufs<T> B = adapt_carve<T>(ws, m, n, R, b);
   *Qout = B.Q;
   *Btout = B.Bt;
@@ -322,6 +324,21 @@ void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, u
     launch_gaussian(n, bb, seed, 1u, tb, dt, B.G, b, s);
     adapt_sketch_kernel<T><<<ceil_div(m, 8), 256, 0, s>>>(m, n, bb, B.Aj, B.G, b, Y, R, done);
     note_launch();
+    for (int j = 0; j < q; ++j) {
+      // Y = orth(Y); Z = orth(A_j^T Y) (into the G buffer, binary64 row sums);
+      // Y = A_j Z
+      run_orth<T, C>(m, bb, Y, R, nullptr, nullptr, 0, orthws, st, sms, s, done);
+      const int splits = ceil_div(m, 256) < 64 ? ceil_div(m, 256) : 64;
+      const int rows_per = ceil_div(m, splits);
+      adapt_bt_kernel<T><<<dim3(ceil_div(n, 128), splits), 128, 0, s>>>(m, n, bb, B.Aj, Y, R, rows_per, B.Btp,
+                                                                        done);
+      note_launch();
+      adapt_bt_reduce_kernel<T><<<ceil_div(n * bb, 256), 256, 0, s>>>(n, bb, splits, B.Btp, B.G, b, nullptr, done);
+      note_launch();
+      run_orth<T, C>(n, bb, B.G, b, nullptr, nullptr, 0, orthws, st, sms, s, done);
+      adapt_sketch_kernel<T><<<ceil_div(m, 8), 256, 0, s>>>(m, n, bb, B.Aj, B.G, b, Y, R, done);
+      note_launch();
+    }
     if (tb > 0) {
       const int splits = ceil_div(m, 512) < 64 ? ceil_div(m, 512) : 64;
       const int rows_per = ceil_div(m, splits);
@@ -353,9 +370,9 @@ void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, u
   }
 }
 
-template void run_adaptive<float, float>(int, int, const float*, int, double, int, int, uint64_t, void*, void*,
-                                         DevStatus*, int, cudaStream_t, float**, float**);
-template void run_adaptive<double, double>(int, int, const double*, int, double, int, int, uint64_t, void*, void*,
-                                           DevStatus*, int, cudaStream_t, double**, double**);
+template void run_adaptive<float, float>(int, int, const float*, int, double, int, int, int, uint64_t, void*,
+                                         void*, DevStatus*, int, cudaStream_t, float**, float**);
+template void run_adaptive<double, double>(int, int, const double*, int, double, int, int, int, uint64_t, void*,
+                                           void*, DevStatus*, int, cudaStream_t, double**, double**);
 
 }  // namespace rsvd

@@ -60,8 +60,8 @@ void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat1
 // k_adapt.cu
 size_t adapt_workspace_bytes(int m, int n, int R, int b, int sms, size_t es);
 template <typename T, typename C>
-void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, uint64_t seed, void* ws, void* orthws,
-                  DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout);
+void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, int q, uint64_t seed, void* ws,
+                  void* orthws, DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout);
 
 // k_batched.cu
 int batched_max_rank();
@@ -72,5 +72,21 @@ cudaError_t launch_batched(int count, const int* m, const int* n, const int* lda
                            float* const* U, double* const* D, float* const* V, int R, int b, uint64_t seed,
                            double tol, int* rank_out, double* err_out, int* status_out, void* ws, int ctas,
                            cudaStream_t s);
+
+// k_ctrl.cu
+int thin_splits(int m, int n, int sms);
+int launch_thin_sketch(int m, int n, const float* A, int lda, const float* G, float* Yp, float* Y, double* fro2p,
+                       int sms, cudaStream_t s);
+void launch_ctrl_features(int m, int n, const double* Gram, int nfro, const double* fro2p, RsvdCtrlBlock* blk,
+                          cudaStream_t s);
+void launch_ctrl_decide(RsvdCtrlBlock* blk, float quantile, int lmax, cudaStream_t s);
+size_t mlp_workspace_bytes(int batch);
+// mode -1: logits only (no workspace); 0: gradient into grad; 1: Adam step on th
+cudaError_t launch_mlp(int mode, int batch, const float* X, const int* yl, const int* yq, float lam,
+                       const float* th, float* logits, float* grad, float* m1, float* m2, int t, float lr,
+                       double* loss_out, void* ws, cudaStream_t s);
+int resid_blocks(int m, int sms);
+void launch_judge(int m, int l, const float* Yc, const float* U, int ldu, const double* D, const float* T,
+                  double* part, double tol, double safety, RsvdCtrlBlock* blk, int sms, cudaStream_t s);
 
 }  // namespace rsvd

@@ -18,6 +18,11 @@ struct rsvd_handle_s {
   bool profile;
   std::vector<cudaEvent_t> pool;                     // free events
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[2];
+  // learned controller: caller-owned parameters and the last decision
+  const float* ctrl_theta;
+  double ctrl_quantile, ctrl_safety;
+  int ctrl_info[5];
+  double ctrl_est[2];
 };
 
 namespace rsvd {
@@ -322,6 +327,7 @@ rsvd_status validate_adaptive(rsvd_handle_t h, int m, int n, const void* A, int 
   if (p->prec != RSVD_F64 && p->prec != RSVD_F32)
     return fail(h, RSVD_E_UNSUPPORTED, "rsvd_adaptive_tol supports RSVD_F64 and RSVD_F32");
   if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  if (p->q < 0 || p->q > 8) return fail(h, RSVD_E_INVALID, "q must lie in [0, 8]");
   const AdaptParams a = adapt_params(m, n, p);
   if (a.b < 1 || a.b > 32) return fail(h, RSVD_E_INVALID, "block must lie in [1, 32]");
   const int mn = m < n ? m : n;
@@ -391,7 +397,7 @@ rsvd_status adaptive_impl(rsvd_handle_t h, int m, int n, const T* A, int lda, co
   const AdaptParams a = adapt_params(m, n, p);
   T *Q = nullptr, *Bt = nullptr;
   cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
-  run_adaptive<T, C>(m, n, A, lda, p->tol, a.R, a.b, p->seed, L.abufs, L.orthws, L.st, h->sms, s, &Q, &Bt);
+  run_adaptive<T, C>(m, n, A, lda, p->tol, a.R, a.b, p->q, p->seed, L.abufs, L.orthws, L.st, h->sms, s, &Q, &Bt);
   rsvd_status st = check_launch(h, "rsvd_adaptive_tol");
   if (st != RSVD_OK) return st;
   // one synchronization: the rank sizes Stage B
@@ -432,6 +438,204 @@ rsvd_status finish_sync(rsvd_handle_t h, const rsvd_params* p, DevStatus* st, cu
   return RSVD_OK;
 }
 
+// ------------------------------------------------------- controller path --
+constexpr int CTRL_NC = 16;
+
+struct CtrlLayout {
+  RsvdCtrlBlock* blk;
+  float* G;       // n x 16: probe, then certificate columns
+  float* Yp;      // split partials of the thin sketch
+  float* Y;       // m x 16
+  double* fro2p;  // partial sums of squares
+  double* P;      // Gram partials
+  double* Gram;   // 16 x 16
+  float* T;       // R x 16: V^T G
+  float* Tpart;   // split partials of T
+  double* rpart;  // judge partials
+  void* rest;     // fixed-rank / adaptive workspace
+  size_t bytes;
+};
+
+CtrlLayout ctrl_layout(void* ws, int m, int n, int R, int sms, size_t rest_bytes) {
+  Carver c(ws);
+  CtrlLayout L;
+  L.blk = c.take<RsvdCtrlBlock>(1);
+  L.G = c.take<float>((size_t)n * CTRL_NC);
+  L.Yp = c.take<float>((size_t)thin_splits(m, n, sms) * m * CTRL_NC);
+  L.Y = c.take<float>((size_t)m * CTRL_NC);
+  L.fro2p = c.take<double>((size_t)ceil_div(m, 128) * thin_splits(m, n, sms));
+  L.P = c.take<double>((size_t)gram_splits(m, CTRL_NC, sms) * CTRL_NC * CTRL_NC);
+  L.Gram = c.take<double>(CTRL_NC * CTRL_NC);
+  L.T = c.take<float>((size_t)R * CTRL_NC);
+  L.Tpart = c.take<float>(simt_gemm_workspace(R, CTRL_NC, n, sms, 4) / 4 + 1);
+  L.rpart = c.take<double>((size_t)resid_blocks(m, sms) * CTRL_NC);
+  L.rest = c.take<unsigned char>(rest_bytes);
+  L.bytes = c.size();
+  return L;
+}
+
+// Probe: G = the first 16 columns of the Omega stream; Y = A G and ||A||_F^2
+// in one pass; the 16 x 16 Gram of Y in binary64; features into blk.
+void run_probe(rsvd_handle_t h, int m, int n, const float* A, int lda, uint64_t seed, const CtrlLayout& L,
+               cudaStream_t s) {
+  launch_gaussian(n, CTRL_NC, seed, 0u, 0, RSVD_DT_F32, L.G, CTRL_NC, s);
+  const int nfro = launch_thin_sketch(m, n, A, lda, L.G, L.Yp, L.Y, L.fro2p, h->sms, s);
+  launch_gram<float>(m, CTRL_NC, L.Y, CTRL_NC, L.P, L.Gram, nullptr, h->sms, nullptr, s);
+  launch_ctrl_features(m, n, L.Gram, nfro, L.fro2p, L.blk, s);
+}
+
+struct CtrlSizes {
+  int R, b;
+  size_t rest;
+};
+
+CtrlSizes ctrl_sizes(rsvd_handle_t h, int m, int n, const rsvd_params* p) {
+  CtrlSizes z;
+  const int mn = m < n ? m : n;
+  z.R = p->max_rank > 0 ? p->max_rank : (mn < 256 ? mn : 256);
+  z.b = p->block > 0 ? p->block : 16;
+  size_t fx = p->prec == RSVD_MIXED_BF16 ? mixed_layout(nullptr, m, n, z.R, z.R, h->sms).bytes
+                                         : fixed_layout(nullptr, m, n, z.R, z.R, RSVD_F32, h->sms).bytes;
+  rsvd_params ap = *p;
+  ap.prec = RSVD_F32;
+  ap.q = 0;
+  ap.max_rank = z.R;
+  ap.block = z.b;
+  const size_t ad = adapt_layout(nullptr, m, n, &ap, h->sms).bytes;
+  z.rest = fx > ad ? fx : ad;
+  return z;
+}
+
+rsvd_status validate_controlled(rsvd_handle_t h, int m, int n, const void* A, int lda, const rsvd_params* p,
+                                bool need_theta = true) {
+  if (!h) return RSVD_E_INVALID;
+  if (!p) return fail(h, RSVD_E_INVALID, "params is NULL");
+  if (p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16)
+    return fail(h, RSVD_E_UNSUPPORTED, "the controller runs RSVD_F32 or RSVD_MIXED_BF16");
+  if (m < CTRL_NC || n < CTRL_NC) return fail(h, RSVD_E_INVALID, "the controller needs m, n >= 16");
+  if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  const int mn = m < n ? m : n;
+  const int R = p->max_rank > 0 ? p->max_rank : (mn < 256 ? mn : 256);
+  if (R < 1 || R > mn || R > 256) return fail(h, RSVD_E_INVALID, "max_rank must lie in [1, min(m, n, 256)]");
+  const int b = p->block > 0 ? p->block : 16;
+  if (b < 1 || b > 32) return fail(h, RSVD_E_INVALID, "block must lie in [1, 32]");
+  if (lda < n) return fail(h, RSVD_E_INVALID, "lda %d < n %d", lda, n);
+  if (!A) return fail(h, RSVD_E_INVALID, "NULL A");
+  if (need_theta && !h->ctrl_theta)
+    return fail(h, RSVD_E_INVALID, "no controller parameters attached (rsvd_controller_attach)");
+  if (p->prec == RSVD_MIXED_BF16 && ((uintptr_t)A & 15) != 0)
+    return fail(h, RSVD_E_INVALID, "A must be 16-byte aligned");
+  return RSVD_OK;
+}
+
+void zero_tail(int m, int n, int r, int R, float* U, int ldu, double* D, float* V, int ldv, cudaStream_t s) {
+  if (r >= R) return;
+  cudaMemsetAsync(D + r, 0, (size_t)(R - r) * sizeof(double), s);
+  cudaMemset2DAsync(U + r, (size_t)ldu * sizeof(float), 0, (size_t)(R - r) * sizeof(float), m, s);
+  cudaMemset2DAsync(V + r, (size_t)ldv * sizeof(float), 0, (size_t)(R - r) * sizeof(float), n, s);
+}
+
+// Probe -> network -> (l, q) -> rsvd_fixed_rank -> residual estimate ->
+// accept and truncate, or fall back to the adaptive range finder.
+rsvd_status controlled_impl(rsvd_handle_t h, int m, int n, const float* A, int lda, const rsvd_params* p, float* U,
+                            int ldu, double* D, float* V, int ldv, int* rank_out, double* err_out, void* ws,
+                            cudaStream_t s) {
+  const CtrlSizes z = ctrl_sizes(h, m, n, p);
+  const CtrlLayout L = ctrl_layout(ws, m, n, z.R, h->sms, z.rest);
+  const int mn = m < n ? m : n;
+  const int lmax = z.R < mn ? z.R : mn;
+  cudaMemsetAsync(L.blk, 0, sizeof(RsvdCtrlBlock), s);
+  run_probe(h, m, n, A, lda, p->seed, L, s);
+  cudaError_t e = launch_mlp(-1, 1, L.blk->feat, nullptr, nullptr, 0.f, h->ctrl_theta, L.blk->logits, nullptr,
+                             nullptr, nullptr, 0, 0.f, nullptr, nullptr, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "controller network: %s", cudaGetErrorString(e));
+  launch_ctrl_decide(L.blk, (float)h->ctrl_quantile, lmax, s);
+  rsvd_status st = check_launch(h, "controller probe");
+  if (st != RSVD_OK) return st;
+  RsvdCtrlBlock hb;
+  e = cudaMemcpyAsync(&hb, L.blk, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "controller read: %s", cudaGetErrorString(e));
+  const int l = hb.l_hat < 1 ? 1 : (hb.l_hat > lmax ? lmax : hb.l_hat);
+  const int q = hb.q_hat;
+  // the fixed-rank solve with the chosen (l, q), all l triplets returned
+  rsvd_params fp = *p;
+  fp.k = l;
+  fp.p = 0;
+  fp.q = q;
+  fp.flags = RSVD_FLAG_RETURN_FULL_L;
+  DevStatus* fst;
+  if (p->prec == RSVD_MIXED_BF16) {
+    const MixedLayout M = mixed_layout(L.rest, m, n, l, l, h->sms);
+    fst = M.st;
+    cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
+    st = fixed_rank_mixed(h, m, n, A, lda, &fp, U, ldu, D, V, ldv, M, s);
+  } else {
+    const FixedLayout F = fixed_layout(L.rest, m, n, l, l, RSVD_F32, h->sms);
+    fst = F.st;
+    cudaMemsetAsync(F.st, 0, sizeof(DevStatus), s);
+    st = fixed_rank_simt<float, float>(h, m, n, A, lda, &fp, U, ldu, D, V, ldv, F, s);
+  }
+  if (st != RSVD_OK) return st;
+  // judge: E = A Gc - U (D (V^T Gc)), Gc = 16 columns of Philox stream 2
+  launch_gaussian(n, CTRL_NC, p->seed, 2u, 0, RSVD_DT_F32, L.G, CTRL_NC, s);
+  launch_thin_sketch(m, n, A, lda, L.G, L.Yp, L.Y, nullptr, h->sms, s);
+  launch_gemm_simt<float>(true, l, CTRL_NC, n, V, ldv, L.G, CTRL_NC, L.T, CTRL_NC, L.Tpart, h->sms, s);
+  launch_judge(m, l, L.Y, U, ldu, D, L.T, L.rpart, p->tol, h->ctrl_safety, L.blk, h->sms, s);
+  st = check_launch(h, "controller judge");
+  if (st != RSVD_OK) return st;
+  int fcode = 0;
+  e = cudaMemcpyAsync(&hb, L.blk, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&fcode, &fst->code, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "judge read: %s", cudaGetErrorString(e));
+  const double fro = sqrt(hb.fro2 > 0.0 ? hb.fro2 : 0.0);
+  h->ctrl_info[0] = l;
+  h->ctrl_info[1] = q;
+  h->ctrl_info[2] = (hb.accepted && fcode == 0) ? 1 : 0;
+  h->ctrl_info[3] = 0;
+  h->ctrl_est[0] = fro > 0.0 ? sqrt(hb.est2) / fro : 0.0;
+  h->ctrl_est[1] = fro > 0.0 ? hb.spec_bound / fro : 0.0;
+  if (hb.accepted && fcode == 0) {
+    const int r = hb.rank;
+    zero_tail(m, n, r, z.R, U, ldu, D, V, ldv, s);
+    const double err = h->ctrl_est[0];
+    if (rank_out) cudaMemcpyAsync(rank_out, &r, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (err_out) cudaMemcpyAsync(err_out, &err, sizeof(double), cudaMemcpyHostToDevice, s);
+    h->ctrl_info[4] = r;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+    return check_launch(h, "rsvd_adaptive_tol (controller)");
+  }
+  if (l < z.R) {
+    // fall back: the blocked adaptive range finder in binary32, q = 0
+    rsvd_params ap = *p;
+    ap.prec = RSVD_F32;
+    ap.q = 0;
+    ap.max_rank = z.R;
+    ap.block = z.b;
+    ap.flags = 0;
+    const AdaptLayout AL = adapt_layout(L.rest, m, n, &ap, h->sms);
+    h->ctrl_info[3] = 1;
+    st = adaptive_impl<float, float>(h, m, n, A, lda, &ap, U, ldu, D, V, ldv, rank_out, err_out, AL, s);
+    int r = 0;
+    cudaMemcpy(&r, &AL.st->rank, sizeof(int), cudaMemcpyDeviceToHost);
+    h->ctrl_info[4] = r;
+    return st;
+  }
+  // the largest rank allowed already misses the tolerance
+  zero_tail(m, n, l, z.R, U, ldu, D, V, ldv, s);
+  const double err = h->ctrl_est[0];
+  if (rank_out) cudaMemcpyAsync(rank_out, &l, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (err_out) cudaMemcpyAsync(err_out, &err, sizeof(double), cudaMemcpyHostToDevice, s);
+  h->ctrl_info[4] = l;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+  if (fcode != 0) return fail(h, (rsvd_status)fcode, "fixed-rank solve reported status %d", fcode);
+  return fail(h, RSVD_E_NOT_CONVERGED, "estimated residual %.3e above tol %.3e at the largest rank %d", err, p->tol,
+              l);
+}
+
 }  // namespace
 
 // Accessors for translation units that only see the opaque handle.
@@ -456,6 +660,9 @@ rsvd_status rsvd_create(rsvd_handle_t* handle, int device) {
   h->device = device;
   h->err[0] = 0;
   h->profile = false;
+  h->ctrl_theta = nullptr;
+  h->ctrl_quantile = 0.9;
+  h->ctrl_safety = 0.8;
   if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete h;
     return RSVD_E_CUDA;
@@ -516,6 +723,13 @@ rsvd_status rsvd_last_error_detail(rsvd_handle_t handle, char* buf, size_t len) 
 
 rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_params* params, size_t* bytes) {
   if (!handle || !params || !bytes) return RSVD_E_INVALID;
+  if (params->tol > 0.0 && (params->flags & RSVD_FLAG_USE_CONTROLLER)) {
+    rsvd_status st = validate_controlled(handle, m, n, (const void*)16, n, params, false);
+    if (st != RSVD_OK) return st;
+    const CtrlSizes z = ctrl_sizes(handle, m, n, params);
+    *bytes = ctrl_layout(nullptr, m, n, z.R, handle->sms, z.rest).bytes;
+    return RSVD_OK;
+  }
   if (params->tol > 0.0) {
     rsvd_status st = validate_adaptive(handle, m, n, (const void*)1, n, params);
     if (st != RSVD_OK) return st;
@@ -572,6 +786,19 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
 rsvd_status rsvd_adaptive_tol(rsvd_handle_t handle, int m, int n, const void* A, int lda, const rsvd_params* params,
                               void* U, int ldu, double* D, void* V, int ldv, int* rank_out, double* err_out,
                               void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
+  if (params && (params->flags & RSVD_FLAG_USE_CONTROLLER)) {
+    rsvd_status st = validate_controlled(handle, m, n, A, lda, params);
+    if (st != RSVD_OK) return st;
+    const CtrlSizes z = ctrl_sizes(handle, m, n, params);
+    if (ldu < z.R || ldv < z.R) return fail(handle, RSVD_E_INVALID, "ldu/ldv smaller than max_rank %d", z.R);
+    if (!U || !D || !V) return fail(handle, RSVD_E_INVALID, "NULL output pointer");
+    const size_t need = ctrl_layout(nullptr, m, n, z.R, handle->sms, z.rest).bytes;
+    if (!workspace || ws_bytes < need)
+      return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+    if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+    return controlled_impl(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, rank_out,
+                           err_out, workspace, (cudaStream_t)stream);
+  }
   rsvd_status st = validate_adaptive(handle, m, n, A, lda, params);
   if (st != RSVD_OK) return st;
   const AdaptParams a = adapt_params(m, n, params);
@@ -602,6 +829,7 @@ rsvd_status validate_batched(rsvd_handle_t h, int count, const rsvd_params* p, i
   if (p->prec != RSVD_F32) return fail(h, RSVD_E_UNSUPPORTED, "rsvd_batched supports RSVD_F32");
   if (p->q != 0) return fail(h, RSVD_E_UNSUPPORTED, "rsvd_batched has no power steps (q must be 0)");
   if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  if (p->q < 0 || p->q > 8) return fail(h, RSVD_E_INVALID, "q must lie in [0, 8]");
   *b = p->block > 0 ? p->block : batched_max_block();
   if (*b < 1 || *b > batched_max_block())
     return fail(h, RSVD_E_INVALID, "block must lie in [1, %d]", batched_max_block());
@@ -810,6 +1038,108 @@ rsvd_status rsvd_orth(rsvd_handle_t handle, int prec, int rows, int l, void* Y, 
   else
     run_orth<float, float>(rows, l, (float*)Y, ldy, R, nullptr, 0, ows, dst, handle->sms, s);
   return check_launch(handle, "rsvd_orth");
+}
+
+rsvd_status rsvd_probe_workspace_size(rsvd_handle_t handle, int m, int n, size_t* bytes) {
+  if (!handle || !bytes) return RSVD_E_INVALID;
+  if (m < 16 || n < 16) return fail(handle, RSVD_E_INVALID, "the probe needs m, n >= 16");
+  *bytes = ctrl_layout(nullptr, m, n, 16, handle->sms, 0).bytes;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_probe_features(rsvd_handle_t handle, int m, int n, const float* A, int lda, uint64_t seed,
+                                float* feat, double* fro2, void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
+  size_t need = 0;
+  rsvd_status st = rsvd_probe_workspace_size(handle, m, n, &need);
+  if (st != RSVD_OK) return st;
+  if (lda < n) return fail(handle, RSVD_E_INVALID, "lda %d < n %d", lda, n);
+  if (!A || !feat) return fail(handle, RSVD_E_INVALID, "NULL pointer");
+  if (!workspace || ws_bytes < need)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const CtrlLayout L = ctrl_layout(workspace, m, n, 16, handle->sms, 0);
+  cudaMemsetAsync(L.blk, 0, sizeof(RsvdCtrlBlock), s);
+  run_probe(handle, m, n, A, lda, seed, L, s);
+  cudaMemcpyAsync(feat, L.blk->feat, RSVD_CTRL_D_IN * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (fro2) cudaMemcpyAsync(fro2, &L.blk->fro2, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  return check_launch(handle, "rsvd_probe_features");
+}
+
+rsvd_status rsvd_mlp_workspace_size(rsvd_handle_t handle, int batch, size_t* bytes) {
+  if (!handle || !bytes || batch < 0) return RSVD_E_INVALID;
+  *bytes = mlp_workspace_bytes(batch > 0 ? batch : 1);
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_mlp_forward(rsvd_handle_t handle, int batch, const float* X, const float* theta, float* logits,
+                             rsvd_stream_t stream) {
+  if (!handle) return RSVD_E_INVALID;
+  if (batch < 0) return fail(handle, RSVD_E_INVALID, "negative batch");
+  if (batch == 0) return RSVD_OK;
+  if (!X || !theta || !logits) return fail(handle, RSVD_E_INVALID, "NULL pointer");
+  cudaError_t e = launch_mlp(-1, batch, X, nullptr, nullptr, 0.f, theta, logits, nullptr, nullptr, nullptr, 0, 0.f,
+                             nullptr, nullptr, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_mlp_forward: %s", cudaGetErrorString(e));
+  return RSVD_OK;
+}
+
+namespace {
+rsvd_status mlp_common(rsvd_handle_t h, int batch, const float* X, const int* yl, const int* yq, float lam,
+                       const void* theta, void* ws, size_t ws_bytes) {
+  if (!h) return RSVD_E_INVALID;
+  if (batch < 1) return fail(h, RSVD_E_INVALID, "batch must be >= 1");
+  if (!X || !yl || !yq || !theta) return fail(h, RSVD_E_INVALID, "NULL pointer");
+  if (!(lam >= 0.f)) return fail(h, RSVD_E_INVALID, "lam must be >= 0");
+  const size_t need = mlp_workspace_bytes(batch);
+  if (!ws || ws_bytes < need) return fail(h, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)ws & 255) != 0) return fail(h, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  return RSVD_OK;
+}
+}  // namespace
+
+rsvd_status rsvd_mlp_grad(rsvd_handle_t handle, int batch, const float* X, const int* yl, const int* yq, float lam,
+                          const float* theta, float* grad, double* loss, void* workspace, size_t ws_bytes,
+                          rsvd_stream_t stream) {
+  rsvd_status st = mlp_common(handle, batch, X, yl, yq, lam, theta, workspace, ws_bytes);
+  if (st != RSVD_OK) return st;
+  if (!grad) return fail(handle, RSVD_E_INVALID, "NULL grad");
+  cudaError_t e = launch_mlp(0, batch, X, yl, yq, lam, theta, nullptr, grad, nullptr, nullptr, 0, 0.f, loss,
+                             workspace, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_mlp_grad: %s", cudaGetErrorString(e));
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_mlp_train_step(rsvd_handle_t handle, int batch, const float* X, const int* yl, const int* yq,
+                                float lam, float* theta, float* m1, float* m2, int step, float lr, double* loss,
+                                void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
+  rsvd_status st = mlp_common(handle, batch, X, yl, yq, lam, theta, workspace, ws_bytes);
+  if (st != RSVD_OK) return st;
+  if (!m1 || !m2) return fail(handle, RSVD_E_INVALID, "NULL Adam moments");
+  if (step < 1) return fail(handle, RSVD_E_INVALID, "step must be >= 1");
+  if (!(lr > 0.f)) return fail(handle, RSVD_E_INVALID, "lr must be > 0");
+  cudaError_t e = launch_mlp(1, batch, X, yl, yq, lam, theta, nullptr, nullptr, m1, m2, step, lr, loss, workspace,
+                             (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_mlp_train_step: %s", cudaGetErrorString(e));
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_controller_attach(rsvd_handle_t handle, const float* theta, double quantile, double safety) {
+  if (!handle) return RSVD_E_INVALID;
+  if (!(quantile > 0.0 && quantile <= 1.0)) return fail(handle, RSVD_E_INVALID, "quantile must lie in (0, 1]");
+  if (!(safety > 0.0 && safety <= 1.0)) return fail(handle, RSVD_E_INVALID, "safety must lie in (0, 1]");
+  handle->ctrl_theta = theta;
+  handle->ctrl_quantile = quantile;
+  handle->ctrl_safety = safety;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_controller_last(rsvd_handle_t handle, int* info, double* est) {
+  if (!handle || !info || !est) return RSVD_E_INVALID;
+  for (int i = 0; i < 5; ++i) info[i] = handle->ctrl_info[i];
+  est[0] = handle->ctrl_est[0];
+  est[1] = handle->ctrl_est[1];
+  return RSVD_OK;
 }
 
 }  // extern "C"

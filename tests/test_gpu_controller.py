@@ -1,0 +1,271 @@
+"""The learned (l, q) controller on the GPU: the power variant of the adaptive
+range finder that labels it, the probe features, the network's forward pass,
+gradient and Adam step (each against the float64 oracle on the same inputs),
+the controlled solve's three outcomes, and the gain of the trained network
+over the adaptive range finder alone."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import controller as OC
+from workloads import (lowrank_np, exp_spectrum, poly_decay_matrix_np, step_spectrum, controller_matrix,
+                       controller_matrix_np, mlp_init)
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(x, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+    return t if dtype is None else t.to(dtype)
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_adaptive_power_variant_f64_matches_oracle(lib, q):
+    A = lowrank_np(300, 240, exp_spectrum(240, 8.0), seed=5)
+    tol, seed = 1e-6, 17
+    U, D, V, rank, err, code = lib.adaptive_tol(_t(A), tol, block=16, seed=seed, prec=lib.RSVD_F64, q=q)
+    assert code == lib.RSVD_OK
+    ref = oracle.adaptive_blocked(A, tol, b=16, seed=seed, q=q, max_rank=128)
+    assert rank == ref["rank"] and err <= tol
+    np.testing.assert_allclose(D.cpu().numpy()[:rank], ref["D"], rtol=1e-9, atol=1e-13 * ref["D"][0])
+    # power steps need no more rank than the plain scheme
+    assert rank <= oracle.adaptive_blocked(A, tol, b=16, seed=seed, q=0, max_rank=128)["rank"]
+
+
+def test_adaptive_labels_match_oracle(lib):
+    for seed in (101, 102, 103):
+        A, (n, kind, par) = controller_matrix_np(seed, lo=128, hi=320)
+        ranks, conv, label = lib.adaptive_labels(_t(A), 1e-4, seed=seed, max_rank=min(n, 256))
+        r_ref, c_ref = OC.adaptive_ranks(A.astype(np.float64), 1e-4, seed=seed, R=min(n, 256))
+        for q in range(4):
+            # binary32 vs binary64 stopping decisions agree unless the remainder sits at the threshold
+            assert abs(ranks[q] - r_ref[q]) <= 16, (kind, par, ranks, r_ref)
+        if ranks == r_ref and conv == c_ref:
+            assert label == OC.label_from_ranks(r_ref, c_ref)
+
+
+@pytest.mark.parametrize("case", ["stream0", "stream1", "stream2", "poly_rect", "rank5"])
+def test_probe_features_parity(lib, case):
+    if case.startswith("stream"):
+        A, _ = controller_matrix_np(200 + int(case[-1]), lo=256, hi=1024)
+    elif case == "poly_rect":
+        A = poly_decay_matrix_np(3001, 707, seed=9, alpha=0.8)  # ragged rows and columns
+    else:
+        A = lowrank_np(500, 333, np.geomspace(1, 0.1, 5), seed=4).astype(np.float32)
+    seed = 23
+    feat, fro2 = lib.probe_features(_t(A), seed=seed)
+    ref = OC.probe_features(A.astype(np.float64), seed)
+    f = feat.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(f, ref, atol=0.02)
+    np.testing.assert_allclose(f[15:], ref[15:], rtol=1e-6)
+    np.testing.assert_allclose(float(fro2.item()), float(np.sum(A.astype(np.float64) ** 2)), rtol=1e-6)
+    if case == "rank5":
+        assert np.all(f[4:15] == -3.0)
+
+
+def _theta32(seed, noise=0.05):
+    th = mlp_init(seed) + noise * np.random.default_rng(seed + 1).standard_normal(OC.n_params())
+    th[-OC.N_OUT:] += 0.1 * np.random.default_rng(seed + 2).standard_normal(OC.N_OUT)
+    return th.astype(np.float32)
+
+
+def _batch(N, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, OC.D_IN)).astype(np.float32)
+    return X, rng.integers(0, 16, N).astype(np.int32), rng.integers(0, 4, N).astype(np.int32)
+
+
+@pytest.mark.parametrize("N", [1, 77, 300])
+def test_mlp_forward_parity(lib, N):
+    th = _theta32(1)
+    X, _, _ = _batch(N, 2)
+    Z = lib.mlp_forward(_t(X), _t(th)).cpu().numpy()
+    Zr, _, _ = OC.forward(th.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_allclose(Z, Zr, rtol=1e-5, atol=1e-5 * np.abs(Zr).max())
+
+
+@pytest.mark.parametrize("N,lam", [(5, 0.0), (77, 0.5), (300, 2.0)])
+def test_mlp_gradient_parity(lib, N, lam):
+    th = _theta32(3)
+    X, yl, yq = _batch(N, 4)
+    g, loss = lib.mlp_grad(_t(X), _t(yl), _t(yq), lam, _t(th))
+    lr, gr = OC.loss_and_grad(th.astype(np.float64), X.astype(np.float64), yl, yq, lam)
+    g = g.cpu().numpy().astype(np.float64)
+    assert float(loss.item()) == pytest.approx(lr, rel=1e-5)
+    np.testing.assert_allclose(g, gr, rtol=0, atol=2e-5 * np.abs(gr).max())
+
+
+def test_adam_steps_parity(lib):
+    import torch
+    th = _theta32(5)
+    X, yl, yq = _batch(130, 6)
+    tr = lib.Trainer(_t(th).clone(), lr=1e-3, lam=0.5)
+    ref = th.astype(np.float64)
+    m1 = np.zeros_like(ref)
+    m2 = np.zeros_like(ref)
+    Xt, ylt, yqt = _t(X), _t(yl), _t(yq)
+    for t in range(1, 4):
+        loss = float(tr.step(Xt, ylt, yqt).item())
+        lref, g = OC.loss_and_grad(ref, X.astype(np.float64), yl, yq, 0.5)
+        assert loss == pytest.approx(lref, rel=1e-4)
+        ref, m1, m2 = OC.adam_step(ref, g, m1, m2, t, 1e-3)
+    torch.cuda.synchronize()
+    got = tr.theta.cpu().numpy().astype(np.float64)
+    d = np.abs(got - ref)
+    # Adam's early steps are about lr * sign(g): where |g| is at the rounding level
+    # the sign may differ, which moves a parameter by at most 3 lr in 3 steps
+    assert d.max() <= 3e-3 + 1e-6
+    _, g0 = OC.loss_and_grad(th.astype(np.float64), X.astype(np.float64), yl, yq, 0.5)
+    big = np.abs(g0) > 1e-3 * np.abs(g0).max()
+    assert np.percentile(d[big], 99) <= 2e-5
+
+
+def _fixed_theta(cls, q):
+    """A network that always answers (l = 16 (cls + 1), q): zero weights and
+    large output biases."""
+    th = np.zeros(OC.n_params(), dtype=np.float32)
+    b3 = th[-OC.N_OUT:]
+    b3[:OC.N_L] = -30.0
+    b3[cls] = 30.0
+    b3[OC.N_L:] = -30.0
+    b3[OC.N_L + q] = 30.0
+    return th
+
+
+def _true_rel_residual(A, U, D, V, r):
+    import torch
+    A64 = A.double()
+    R = A64 - (U[:, :r].double() * D[:r][None, :]) @ V[:, :r].double().T
+    return float(torch.linalg.norm(R) / torch.linalg.norm(A64))
+
+
+def test_controlled_solve_accept_fallback_and_cap(lib):
+    import torch
+    h = lib.handle()
+    A64 = lowrank_np(700, 500, step_spectrum(500, 24), seed=8)
+    A = _t(A64.astype(np.float32))
+    tol, seed = 1e-4, 3
+    # (a) l = 32, q = 1 meets the tolerance: accepted, truncated, equal to the oracle's rank-32 solve
+    th = _t(_fixed_theta(1, 1))
+    lib.rsvd_controller_attach(h, th, 0.9, 0.8)
+    U, D, V, rank, err, code = lib.adaptive_tol(A, tol, seed=seed, max_rank=64, controller=True)
+    info = lib.rsvd_controller_last(h)
+    assert code == lib.RSVD_OK and info["l"] == 32 and info["q"] == 1 and info["accepted"] and not info["fallback"]
+    assert 24 <= rank <= 32 and info["rank"] == rank
+    ref = oracle.rsvd_power(A64.astype(np.float32).astype(np.float64), 32, 0, 1, seed, full=True)
+    np.testing.assert_allclose(D.cpu().numpy()[:24], ref["D"][:24], rtol=1e-5)
+    assert np.all(D.cpu().numpy()[rank:] == 0)
+    assert _true_rel_residual(A, U, D, V, rank) <= tol
+    assert err == pytest.approx(info["est_rel"]) and err <= 0.8 * tol
+    # (b) l = 16 is too small: the judge rejects it and the adaptive finder recomputes
+    th16 = _t(_fixed_theta(0, 0))
+    lib.rsvd_controller_attach(h, th16, 0.9, 0.8)
+    U, D, V, rank, err, code = lib.adaptive_tol(A, tol, seed=seed, max_rank=64, controller=True)
+    info = lib.rsvd_controller_last(h)
+    assert code == lib.RSVD_OK and info["l"] == 16 and not info["accepted"] and info["fallback"]
+    ref = oracle.adaptive_blocked(A64.astype(np.float32).astype(np.float64), tol, b=16, seed=seed, max_rank=64)
+    assert rank == ref["rank"] and _true_rel_residual(A, U, D, V, rank) <= tol
+    # (c) a slowly decaying spectrum misses the tolerance at the largest allowed rank
+    P = _t(poly_decay_matrix_np(400, 300, seed=2, alpha=0.6))
+    lib.rsvd_controller_attach(h, _t(_fixed_theta(15, 2)), 0.9, 0.8)
+    U, D, V, rank, err, code = lib.adaptive_tol(P, tol, seed=seed, max_rank=48, controller=True)
+    info = lib.rsvd_controller_last(h)
+    assert code == lib.RSVD_E_NOT_CONVERGED and info["l"] == 48 and not info["fallback"] and rank == 48
+    assert err > tol
+    # mixed precision: bf16 sketches find the dominant subspace of bf16(A), about
+    # 2^-9 ||A|| away from A's, so they serve looser tolerances: at 1e-4 the judge
+    # rejects them (and the binary32 fallback takes over), at 3e-3 it accepts
+    lib.rsvd_controller_attach(h, th, 0.9, 0.8)
+    U, D, V, rank, err, code = lib.adaptive_tol(A, tol, seed=seed, max_rank=64, controller=True,
+                                                prec=lib.RSVD_MIXED_BF16)
+    info = lib.rsvd_controller_last(h)
+    assert code == lib.RSVD_OK and not info["accepted"] and info["fallback"]
+    assert 2e-4 < info["est_rel"] < 3e-3 and _true_rel_residual(A, U, D, V, rank) <= tol
+    U, D, V, rank, err, code = lib.adaptive_tol(A, 3e-3, seed=seed, max_rank=64, controller=True,
+                                                prec=lib.RSVD_MIXED_BF16)
+    info = lib.rsvd_controller_last(h)
+    assert code == lib.RSVD_OK and info["accepted"] and not info["fallback"] and rank == 24
+    assert _true_rel_residual(A, U, D, V, rank) <= 3e-3
+    lib.rsvd_controller_attach(h, None, 0.9, 0.8)
+    with pytest.raises(lib.RsvdError):
+        lib.adaptive_tol(A, tol, seed=seed, max_rank=64, controller=True)
+
+
+def _stream(seeds, lo, hi):
+    out = []
+    for s in seeds:
+        A, (n, kind, par) = controller_matrix(s, lo=lo, hi=hi, device="cuda")
+        out.append((s, A, kind, par))
+    return out
+
+
+def test_controller_gain_over_adaptive(lib):
+    """Train the network on the GPU from the adaptive finder's own labels, then
+    compare on a held-out stream: (i) controller + judge + fallback, (ii) the
+    adaptive range finder alone, (iii) fixed conservative l = min(n, 256),
+    q = 2; and the untrained network in (i)'s place."""
+    import torch
+    # sizes where the passes over A, not the fixed per-solve work, set the cost
+    lo, hi, tol = 1024, 4096, 1e-4
+    train = _stream(range(50000, 50160), lo, hi)
+    X, yl, yq = [], [], []
+    for s, A, kind, par in train:
+        f, _ = lib.probe_features(A, seed=s)
+        X.append(f)
+        _, _, (c, q) = lib.adaptive_labels(A, tol, seed=s, max_rank=min(A.shape[0], 256))
+        yl.append(c)
+        yq.append(q)
+    X = torch.stack(X)
+    yl = torch.tensor(yl, dtype=torch.int32, device="cuda")
+    yq = torch.tensor(yq, dtype=torch.int32, device="cuda")
+    theta0 = _t(mlp_init(7).astype(np.float32))
+    tr = lib.Trainer(theta0.clone(), lr=2e-3, lam=1.0)
+    first = float(tr.step(X, yl, yq).item())
+    for _ in range(2500):
+        tr.step(X, yl, yq)
+    last = float(tr.step(X, yl, yq).item())
+    assert last < 0.5 * first, (first, last)
+    del train
+    torch.cuda.empty_cache()
+
+    evals = _stream(range(60000, 60040), lo, hi)
+    h = lib.handle()
+
+    def run(method, theta=None):
+        t_total, met, fallbacks = 0.0, 0, 0
+        for s, A, kind, par in evals:
+            n = A.shape[0]
+            R = min(n, 256)
+            if theta is not None:
+                lib.rsvd_controller_attach(h, theta, 0.9, 0.8)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if method == "adaptive":
+                U, D, V, r, err, code = lib.adaptive_tol(A, tol, seed=s, max_rank=R)
+            elif method == "controller":
+                U, D, V, r, err, code = lib.adaptive_tol(A, tol, seed=s, max_rank=R, controller=True)
+            else:
+                U, D, V = lib.fixed_rank(A, R, 0, 2, seed=s, full=True, sync=True)
+                r = R
+            torch.cuda.synchronize()
+            t_total += time.perf_counter() - t0
+            if method == "controller":
+                fallbacks += lib.rsvd_controller_last(h)["fallback"]
+            met += _true_rel_residual(A, U, D, V, r) <= tol
+        return len(evals) / t_total, met / len(evals), fallbacks
+
+    run("adaptive")  # warm-up of every kernel
+    ada = run("adaptive")
+    ctl = run("controller", tr.theta)
+    fix = run("fixed")
+    raw = run("controller", theta0)
+    print("\ncontroller gain (%d held-out matrices, n in [%d, %d], tol %.0e):" % (len(evals), lo, hi, tol))
+    for name, (sps, frac, fb) in (("adaptive only", ada), ("controller (trained)", ctl),
+                                  ("controller (untrained)", raw), ("fixed l=256 q=2", fix)):
+        print("  %-24s %8.1f solves/s  %.3f meet tol  %d fallbacks" % (name, sps, frac, fb))
+    assert ctl[0] > 1.5 * ada[0]
+    assert ctl[1] >= ada[1] - 0.05
+    assert ctl[2] < raw[2] or ctl[0] > raw[0]

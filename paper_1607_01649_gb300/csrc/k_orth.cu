@@ -6,8 +6,8 @@
 //   1. G = Y^T Y                    (gram_partial + gram_reduce; binary64 sums)
 //   2. G = D Gt D, Gt = Lt Lt^T      (chol: unit-diagonal scaling in binary64,
 //                                     Cholesky of Gt (+ s I when needed))
-//   3. Y <- Y D^-1 Lt^-T             (apply: one warp per row, forward
-//                                     substitution against Lt^T)
+//   3. Y <- Y D^-1 Lt^-T             (apply: blocked triangular solve,
+//                                     64-row stripes)
 // so Y = Q R with R = Lt^T D upper triangular, diag(R) > 0.
 //
 // Binary64 on this part runs at 1/58 of binary32 (measured 1.20 TFLOP/s vs
@@ -105,6 +105,120 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Binary32 partial Gram, same contract as gram_partial_kernel: 128 threads,
+// thread (ty, tx) owns rows ty * 8 .. + 7 and columns tx * 4 .. + 3 of the
+// tile (4 shared-memory vector loads per 32 FMAs); the next 32-row chunk is
+// loaded into registers while the current one is multiplied.
+constexpr int G32_THREADS = 128;
+
+__device__ __forceinline__ void gram_load_chunk(const float* __restrict__ Y, int ldy, int r0, int r_end, int c0,
+                                                int l, bool vec, float4 (&reg)[4]) {
+  // 32 rows x 64 columns = 512 float4, four per thread
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + G32_THREADS * u;
+    const int rr = e / 16, c4 = e % 16;
+    const int gr = r0 + rr, gc = c0 + 4 * c4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gr < r_end) {
+      const float* src = Y + (size_t)gr * ldy + gc;
+      if (vec) {
+        if (gc < l) v = *reinterpret_cast<const float4*>(src);
+      } else {
+        if (gc < l) v.x = src[0];
+        if (gc + 1 < l) v.y = src[1];
+        if (gc + 2 < l) v.z = src[2];
+        if (gc + 3 < l) v.w = src[3];
+      }
+    }
+    reg[u] = v;
+  }
+}
+
+__device__ __forceinline__ void gram_store_chunk(float (*S)[GT], const float4 (&reg)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + G32_THREADS * u;
+    *reinterpret_cast<float4*>(&S[e / 16][4 * (e % 16)]) = reg[u];
+  }
+}
+
+__global__ void __launch_bounds__(G32_THREADS)
+    gram_partial_f32_kernel(int rows, int l, const float* __restrict__ Y, int ldy, double* __restrict__ P,
+                            int rows_per_split, const int* gate, const int* skip) {
+  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
+  __shared__ __align__(16) float Yi[GCH][GT];
+  __shared__ __align__(16) float Yj[GCH][GT];
+  const int nb = ceil_div(l, GT);
+  int t = blockIdx.x, bi = 0;
+  while (t >= nb - bi) {
+    t -= nb - bi;
+    ++bi;
+  }
+  const int bj = bi + t;
+  const bool diag = bi == bj;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int r_beg = blockIdx.y * rows_per_split;
+  const int r_end = min(rows, r_beg + rows_per_split);
+  const bool vec = (l % 4) == 0 && (ldy % 4) == 0 && (((uintptr_t)Y) & 15) == 0;
+  float part[8][4];
+  double acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      part[a][b] = 0.f;
+      acc[a][b] = 0.0;
+    }
+  float4 ri[4], rj[4];
+  gram_load_chunk(Y, ldy, r_beg, r_end, bi * GT, l, vec, ri);
+  if (!diag) gram_load_chunk(Y, ldy, r_beg, r_end, bj * GT, l, vec, rj);
+  int chunk = 0;
+  for (int r0 = r_beg; r0 < r_end; r0 += GCH, ++chunk) {
+    __syncthreads();  // previous chunk's reads are done
+    gram_store_chunk(Yi, ri);
+    if (!diag) gram_store_chunk(Yj, rj);
+    __syncthreads();
+    if (r0 + GCH < r_end) {  // prefetch the next chunk
+      gram_load_chunk(Y, ldy, r0 + GCH, r_end, bi * GT, l, vec, ri);
+      if (!diag) gram_load_chunk(Y, ldy, r0 + GCH, r_end, bj * GT, l, vec, rj);
+    }
+    const float(*Sj)[GT] = diag ? Yi : Yj;
+#pragma unroll 4
+    for (int rr = 0; rr < GCH; ++rr) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Yi[rr][8 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Yi[rr][8 * ty + 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Sj[rr][4 * tx]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) part[u][v] = fmaf(a[u], b[v], part[u][v]);
+    }
+    if ((chunk % GFOLD) == GFOLD - 1 || r0 + GCH >= r_end) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          acc[u][v] += (double)part[u][v];
+          part[u][v] = 0.f;
+        }
+    }
+  }
+  double* out = P + (size_t)blockIdx.y * l * l;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int i = bi * GT + 8 * ty + u;
+    if (i >= l) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = bj * GT + 4 * tx + v;
+      if (j < l) out[(size_t)i * l + j] = acc[u][v];
+    }
+  }
+}
+
 // G[i][j] = sum over splits (fixed order) of the upper-triangular partials;
 // Gf receives G rounded to binary32 (the Cholesky kernel's input on the
 // binary32 path; converting here spreads the binary64 conversions over the GPU).
@@ -129,7 +243,7 @@ __global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__
 int gram_splits(int rows, int l, int sms) {
   const int nb = ceil_div(l, GT);
   const int tiles = nb * (nb + 1) / 2;
-  int s = ceil_div(2 * sms, tiles);
+  int s = ceil_div(3 * sms, tiles);
   const int smax = ceil_div(rows, 4 * GCH);
   if (s > smax) s = smax;
   if (s < 1) s = 1;
@@ -145,16 +259,17 @@ void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, flo
   const int splits = gram_splits(rows, l, sms);
   const int rps = ceil_div(ceil_div(rows, splits), GCH) * GCH;
   const int used = ceil_div(rows, rps);
-  gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate, skip);
+  if (sizeof(T) == 4)
+    gram_partial_f32_kernel<<<dim3(tiles, used), G32_THREADS, 0, s>>>(rows, l, (const float*)Y, ldy, P, rps, gate,
+                                                                      skip);
+  else
+    gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate, skip);
   note_launch();
   gram_reduce_kernel<<<ceil_div(l * l, 256), 256, 0, s>>>(l, used, P, G, Gf, gate, skip);
   note_launch();
 }
 
 // -------------------------------------------------------------- Cholesky --
-// Packed column-major lower triangle: column j holds rows j..l-1.
-__device__ __forceinline__ int pk(int l, int i, int j) { return j * l - (j * (j - 1)) / 2 + (i - j); }
-
 template <typename C>
 struct Eps;
 template <>
@@ -166,40 +281,50 @@ struct Eps<double> {
   static constexpr double u = 1.1102230246251565e-16;  // 2^-53
 };
 
-// Single CTA of 1024 threads.  In: G (l x l binary64) and Gf (G rounded to
-// binary32, used on the binary32 path).  Out:
+// Single CTA.  In: G (l x l binary64) and Gf (G rounded to binary32, used on
+// the binary32 path).  Out:
 //   Ub   : l x l row-major, type C: the upper triangular factor Lt^T whose
-//          32 x 32 diagonal blocks are replaced by their inverses; with
-//          dinv it defines Q = (Y D^-1) Lt^-T (blocked triangular solve)
+//          32 x 32 diagonal blocks are replaced by their inverses; with dinv
+//          it defines Q = (Y D^-1) Lt^-T (blocked triangular solve, apply_kernel)
 //   dinv : 1 / d_i, d_i = sqrt(G_ii)
 //   R    : optional l x l row-major binary64, R = Lt^T D (zeros below the diagonal)
 // where G = D Gt D and Gt = Lt Lt^T.  Pivots below tau (unit-diagonal scale)
 // restart the factorization on Gt + s I, s = s0, 32 s0, ...; four failures
 // give RSVD_E_BREAKDOWN.
 //
-// Factorization: blocked right-looking on 32-column panels.  For each panel:
-//   (b) the 32 x 32 diagonal block is factored by warp 0, lane i holding row i
-//       in registers (pivot columns broadcast by shuffles);
-//   (c) the rows below are solved against it, one thread per row;
-//   (d) the trailing lower triangle is updated, A22 -= L21 L21^T, by all
-//       threads in 4 x 4 register tiles.
-// Finally the diagonal blocks are inverted, one warp per block.
+// Storage: the lower triangle of 32 x 32 blocks, block (bi, bj), bj <= bi, at
+// index bi (bi + 1) / 2 + bj, each block 32 rows of CP = 33 entries (the pad
+// keeps column reads free of bank conflicts).  l is padded to 32 NB with an
+// identity block, which decouples the pad from the rest.
+//
+// Right-looking over block columns k, with one block of lookahead:
+//   (1) L_ik = A_ik L_kk^-T, i > k, forward substitution, one thread per row;
+//   (2) A_i,k+1 -= L_ik L_k+1,k^T, i > k (the next block column);
+//   (3) warp 0 factors A_k+1,k+1, warp 1 inverts L_kk (for Ub), and the other
+//       warps apply the rest of the trailing update, A_ij -= L_ik L_jk^T,
+//       k + 1 < j <= i.
+// A warp updates a 32 x 32 block with each lane holding a 4 x 8 tile.
+constexpr int CBK = 32;             // block size
+constexpr int CP = 33;              // padded row stride within a block
+constexpr int CBS = CBK * CP;       // stored entries per block
 
-// Warp-level Cholesky of a w x w block held as rows (lane i: row[0..31] =
+__device__ __forceinline__ int lblk(int bi, int bj) { return bi * (bi + 1) / 2 + bj; }
+
+// Warp-level Cholesky of a 32 x 32 block held as rows (lane i: row[0..31] =
 // A(i, 0..31), lower part valid).  On return row[] holds row i of L.  Returns
 // false (warp-uniformly) on a pivot below tau.
 template <typename C>
-__device__ __forceinline__ bool warp_chol32(C (&row)[32], int w, C tau) {
+__device__ __forceinline__ bool warp_chol32(C (&row)[32], C tau) {
   const int lane = threadIdx.x % 32;
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
-    if (q < w && ok) {  // warp-uniform; no break, so q stays a compile-time index
+    if (ok) {  // warp-uniform; no break, so q stays a compile-time index
       const C akk = __shfl_sync(0xffffffffu, row[q], q);
       if (!(akk > tau) || !isfinite(akk)) {
         ok = false;
       } else {
-        const C piv = sqrt(akk), rp = C(1) / piv;
+        const C rp = rsqrt(akk), piv = akk * rp;
         const C liq = (lane == q) ? piv : (lane > q ? row[q] * rp : C(0));
         row[q] = liq;
         // row i -= l(i, q) * l(j, q) for q < j <= i
@@ -214,31 +339,100 @@ __device__ __forceinline__ bool warp_chol32(C (&row)[32], int w, C tau) {
   return ok;
 }
 
-// Warp-level inverse of the lower triangular w x w diagonal block at
-// (c0, c0) of the packed factor.  Lane i ends with x[] = row i of L^-1.
-// x doubles as the accumulator: lanes i > k add L(i, k) X(k, :) at step k,
-// when lane k turns its accumulator into its final row.
+// Warp-level inverse of the lower triangular L held as rows (lane i: row[]
+// = row i of L): lane i ends with x[] = row i of L^-1.  x doubles as the
+// accumulator: lanes i > t add L(i, t) X(t, :) at step t, when lane t turns
+// its accumulator into its final row.
 template <typename C>
-__device__ __forceinline__ void warp_trinv32(const C* a, const int* cb, int c0, int w, C (&x)[32]) {
+__device__ __forceinline__ void warp_trinv32(const C (&row)[32], C (&x)[32]) {
   const int lane = threadIdx.x % 32;
-  const int i = c0 + lane;
 #pragma unroll
   for (int c = 0; c < 32; ++c) x[c] = C(0);
-  const C rd = (lane < w) ? C(1) / a[cb[i] + i] : C(0);
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k >= w) continue;  // warp-uniform; keeps k a compile-time index
-    if (lane == k) {
+  for (int t = 0; t < 32; ++t) {
+    if (lane == t) {
+      const C rd = C(1) / row[t];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) x[c] = ((c == k ? C(1) : C(0)) - x[c]) * rd;
+      for (int c = 0; c < 32; ++c) x[c] = ((c == t ? C(1) : C(0)) - x[c]) * rd;
     }
-    const C lik = (lane > k && lane < w) ? a[cb[c0 + k] + i] : C(0);
+    const C lit = lane > t ? row[t] : C(0);
 #pragma unroll
-    for (int c = 0; c <= k; ++c) {
-      const C xkc = __shfl_sync(0xffffffffu, x[c], k);
-      if (lane > k) x[c] = fma(lik, xkc, x[c]);
+    for (int c = 0; c <= t; ++c) {
+      const C xtc = __shfl_sync(0xffffffffu, x[c], t);
+      if (lane > t) x[c] = fma(lit, xtc, x[c]);
     }
   }
+}
+
+// One warp: Cb = A B^T (sub == false, in place allowed: Cb may be Ab) or
+// Cb -= A B^T (sub == true), 32 x 32 blocks with row stride CP.  Lane (lr, lc)
+// holds rows 4 lr .. + 3, columns 8 lc .. + 7.
+template <typename C>
+__device__ __forceinline__ void warp_blk_nt(C* Cb, const C* Ab, const C* Bb, bool sub) {
+  const int lane = threadIdx.x % 32, lr = lane >> 2, lc = lane & 3;
+  C acc[4][8];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
+#pragma unroll 4
+  for (int t = 0; t < 32; ++t) {
+    C a[4], b[8];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) a[x] = Ab[(4 * lr + x) * CP + t];
+#pragma unroll
+    for (int y = 0; y < 8; ++y) b[y] = Bb[(8 * lc + y) * CP + t];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      C* p = Cb + (4 * lr + x) * CP + 8 * lc + y;
+      *p = sub ? *p - acc[x][y] : acc[x][y];
+    }
+  __syncwarp();
+}
+
+// One warp: Cholesky of diagonal block k in place, and 1 / L(q, q) into
+// rdg[32 k + q].  On a pivot failure sets *fail.
+template <typename C>
+__device__ __forceinline__ void diag_potrf(C* Ls, C* rdg, int k, C tau, int* fail) {
+  const int lane = threadIdx.x % 32;
+  C* A = Ls + (size_t)lblk(k, k) * CBS + lane * CP;
+  C row[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) row[j] = (j <= lane) ? A[j] : C(0);
+  const bool ok = warp_chol32<C>(row, tau);
+  if (!ok) {
+    if (lane == 0) *fail = 1;
+    return;
+  }
+  C dii = C(1);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    A[j] = (j <= lane) ? row[j] : C(0);
+    if (j == lane) dii = row[j];
+  }
+  rdg[CBK * k + lane] = C(1) / dii;
+}
+
+// One warp: X_kk = L_kk^-1 into Xs[k] (rows of L from shared memory).
+template <typename C>
+__device__ __forceinline__ void diag_trinv(const C* Ls, C* Xs, int k) {
+  const int lane = threadIdx.x % 32;
+  const C* A = Ls + (size_t)lblk(k, k) * CBS + lane * CP;
+  C row[32], x[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) row[j] = (j <= lane) ? A[j] : C(0);
+  warp_trinv32<C>(row, x);
+  C* X = Xs + (size_t)k * CBS + lane * CP;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) X[j] = (j <= lane) ? x[j] : C(0);
 }
 
 template <typename C, int NT>
@@ -247,26 +441,34 @@ __global__ void __launch_bounds__(NT)
                 C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate,
                 const int* skip) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
-  extern __shared__ unsigned char smem_raw[];
-  C* a = reinterpret_cast<C*>(smem_raw);  // packed lower, l(l+1)/2
-  double* d = reinterpret_cast<double*>(smem_raw + (((size_t)l * (l + 1) / 2 * sizeof(C) + 15) & ~15));
-  C* rdiag = reinterpret_cast<C*>(d + l);
-  C* rdc = rdiag + l;
-  int* cb = reinterpret_cast<int*>(rdc + l);  // pk(i, j) = cb[j] + i
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NB = (l + CBK - 1) / CBK;
+  const int nblk = NB * (NB + 1) / 2;
+  C* Ls = reinterpret_cast<C*>(smem_raw);  // nblk blocks
+  C* Xs = Ls + (size_t)nblk * CBS;         // NB diagonal inverses
+  double* d = reinterpret_cast<double*>(Xs + (size_t)NB * CBS);
+  C* rdc = reinterpret_cast<C*>(d + l);
+  C* rdg = rdc + l;  // 1 / L(i, i), 32 NB entries
   __shared__ int s_fail;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid / 32, lane = tid % 32;
+  __shared__ unsigned char s_bi[64], s_bj[64];
+  const int tid = threadIdx.x;
+  const int warp = tid / 32, nw = NT / 32;
   const double u = Eps<C>::u;
   const C ctau = (C)(1024.0 * u);
   const double s0 = 16384.0 * u;
 
   bool bad = false;
-  for (int i = tid; i < l; i += nt) {
+  for (int i = tid; i < l; i += NT) {
     const double gii = G[(size_t)i * l + i];
     if (!isfinite(gii)) bad = true;
     d[i] = gii > 0.0 ? sqrt(gii) : 1.0;
     rdc[i] = (C)(1.0 / d[i]);
-    cb[i] = i * l - (i * (i - 1)) / 2 - i;
+  }
+  if (tid < nblk) {
+    int bi = 0;
+    while ((bi + 1) * (bi + 2) / 2 <= tid) ++bi;
+    s_bi[tid] = (unsigned char)bi;
+    s_bj[tid] = (unsigned char)(tid - bi * (bi + 1) / 2);
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -280,107 +482,99 @@ __global__ void __launch_bounds__(NT)
   C shift = C(0);
   int attempt = 0;
   for (;;) {
-    // unit-diagonal scaling Gt = D^-1 G D^-1 in the working precision (a
-    // binary64 divide per entry would cost more than the factorization)
-    for (int j = warp; j < l; j += nt / 32) {
-      const int base = cb[j];
-      const C rj = rdc[j];
-      for (int i = j + lane; i < l; i += 32) {
-        C v = (sizeof(C) == 4 ? (C)Gf[(size_t)i * l + j] : (C)G[(size_t)i * l + j]) * rdc[i] * rj;
-        if (i == j) v += shift;
-        if (!isfinite(v)) v = C(0);
-        a[base + i] = v;
+    // unit-diagonal scaling Gt = D^-1 G D^-1 (+ shift) in the working
+    // precision, read row by row (G is symmetric), eight independent loads
+    // in flight per thread (a load-then-store loop would wait out the memory
+    // latency once per element)
+    for (int e0 = tid; e0 < nblk * CBK * CBK; e0 += 8 * NT) {
+      C v[8];
+#pragma unroll
+      for (int uu = 0; uu < 8; ++uu) {
+        const int e = e0 + uu * NT;
+        v[uu] = C(0);
+        if (e < nblk * CBK * CBK) {
+          const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+          const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
+          if (i < l && j < l) v[uu] = sizeof(C) == 4 ? (C)Gf[(size_t)i * l + j] : (C)G[(size_t)i * l + j];
+        }
+      }
+#pragma unroll
+      for (int uu = 0; uu < 8; ++uu) {
+        const int e = e0 + uu * NT;
+        if (e < nblk * CBK * CBK) {
+          const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+          const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
+          C w;
+          if (i < l && j < l) {
+            w = v[uu] * rdc[i] * rdc[j];
+            if (i == j) w += shift;
+            if (!isfinite(w)) w = C(0);
+          } else {
+            w = (i == j) ? C(1) : C(0);
+          }
+          Ls[(size_t)b * CBS + r * CP + c] = w;
+        }
       }
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
-    for (int c0 = 0; c0 < l; c0 += 32) {
-      const int w = min(32, l - c0);
-      // (b) diagonal block
-      if (warp == 0) {
-        C row[32];
-        const int i = c0 + lane;
+    if (warp == 0) diag_potrf<C>(Ls, rdg, 0, ctau, &s_fail);
+    __syncthreads();
+    if (s_fail == 0) {
+      for (int k = 0; k < NB; ++k) {
+        // (1) L_ik = A_ik L_kk^-T by forward substitution, one thread per row
+        {
+          const C* Lkk = Ls + (size_t)lblk(k, k) * CBS;
+          for (int rr = tid; rr < (NB - 1 - k) * CBK; rr += NT) {
+            const int i = k + 1 + rr / CBK, r = rr % CBK;
+            C* a = Ls + (size_t)lblk(i, k) * CBS + r * CP;
+            C x[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) row[j] = (lane < w && j < w && j <= lane) ? a[cb[c0 + j] + i] : C(0);
-        const bool ok = warp_chol32<C>(row, w, ctau);
-        if (!ok) {
-          if (lane == 0) s_fail = 1;
-        } else if (lane < w) {
+            for (int q = 0; q < 32; ++q) x[q] = a[q];
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j <= lane) a[cb[c0 + j] + i] = row[j];
-          C dii = C(1);
+            for (int q = 0; q < 32; ++q) {
+              x[q] *= rdg[CBK * k + q];
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (j == lane) dii = row[j];
-          rdiag[i] = C(1) / dii;
-        }
-      }
-      __syncthreads();
-      if (s_fail) break;
-      // (c) rows below: x L11^T = a(i, c0 : c0 + w), thread per row
-      for (int i = c0 + w + tid; i < l; i += nt) {
-        C x[32];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) x[q] = q < w ? a[cb[c0 + q] + i] : C(0);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          if (q < w) {
-            x[q] *= rdiag[c0 + q];
-            const int bq = cb[c0 + q];
-#pragma unroll
-            for (int r2 = q + 1; r2 < 32; ++r2)
-              if (r2 < w) x[r2] = fma(-x[q], a[bq + c0 + r2], x[r2]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (q < w) a[cb[c0 + q] + i] = x[q];
-      }
-      __syncthreads();
-      // (d) trailing update A22 -= L21 L21^T over the lower triangle, 4 x 4 tiles
-      const int t0 = c0 + w;
-      const int n2 = l - t0;
-      if (n2 > 0) {
-        const int nq = (n2 + 3) / 4;             // row/column quads
-        const int ntiles = nq * (nq + 1) / 2;    // lower-triangular tiles
-        for (int tI = tid; tI < ntiles; tI += nt) {
-          // tile index -> (rq, cq) with cq <= rq
-          int rq = (int)((sqrtf(8.0f * tI + 1.0f) - 1.0f) * 0.5f);
-          while ((rq + 1) * (rq + 2) / 2 <= tI) ++rq;
-          while (rq * (rq + 1) / 2 > tI) --rq;
-          const int cq = tI - rq * (rq + 1) / 2;
-          const int i0 = t0 + 4 * rq, j0 = t0 + 4 * cq;
-          C acc[4][4];
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = C(0);
-          for (int k = c0; k < c0 + w; ++k) {
-            const int base = cb[k];
-            C av[4], bv[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) av[x] = (i0 + x < l) ? a[base + i0 + x] : C(0);
-#pragma unroll
-            for (int y = 0; y < 4; ++y) bv[y] = (j0 + y < l) ? a[base + j0 + y] : C(0);
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-              for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
-          }
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) {
-              const int ii = i0 + x, jj = j0 + y;
-              if (ii < l && jj < l && ii >= jj) a[cb[jj] + ii] -= acc[x][y];
+              for (int r2 = q + 1; r2 < 32; ++r2) x[r2] = fma(-x[q], Lkk[r2 * CP + q], x[r2]);
             }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) a[q] = x[q];
+          }
         }
         __syncthreads();
+        if (k + 1 >= NB) break;
+        // (2) the next block column
+        for (int i = k + 1 + warp; i < NB; i += nw)
+          warp_blk_nt<C>(Ls + (size_t)lblk(i, k + 1) * CBS, Ls + (size_t)lblk(i, k) * CBS,
+                         Ls + (size_t)lblk(k + 1, k) * CBS, true);
+        __syncthreads();
+        // (3) factor the next diagonal block || invert this one || the rest
+        // of the trailing update
+        if (warp == 0) {
+          diag_potrf<C>(Ls, rdg, k + 1, ctau, &s_fail);
+        } else if (warp == 1) {
+          diag_trinv<C>(Ls, Xs, k);
+        } else {
+          const int nt = NB - k - 2;  // block columns k + 2 .. NB - 1
+          const int tasks = nt * (nt + 1) / 2;
+          for (int tk = warp - 2; tk < tasks; tk += nw - 2) {
+            int ii = 0;
+            while ((ii + 1) * (ii + 2) / 2 <= tk) ++ii;
+            const int i = k + 2 + ii, j = k + 2 + (tk - ii * (ii + 1) / 2);
+            warp_blk_nt<C>(Ls + (size_t)lblk(i, j) * CBS, Ls + (size_t)lblk(i, k) * CBS,
+                           Ls + (size_t)lblk(j, k) * CBS, true);
+          }
+        }
+        __syncthreads();
+        if (s_fail) break;
       }
     }
     __syncthreads();
-    if (s_fail == 0) break;
+    if (s_fail == 0) {
+      if (warp == 0) diag_trinv<C>(Ls, Xs, NB - 1);
+      __syncthreads();
+      break;
+    }
     ++attempt;
     if (attempt > 4) {
       if (tid == 0) set_status(st, RSVD_E_BREAKDOWN);
@@ -396,35 +590,28 @@ __global__ void __launch_bounds__(NT)
       st->shifted = 1;
     if (shift > C(0)) atomicAdd(&st->shift_count, 1);
   }
-  // outputs, row i of Ub / R by warp, columns by lane: Lt^T[i][j] = L(j, i), j >= i
-  for (int i = warp; i < l; i += nt / 32) {
-    const int bi = i >> 5;
-    for (int j = lane; j < l; j += 32) {
-      const C v = (j >= i) ? a[cb[i] + j] : C(0);
-      if (R) R[(size_t)i * l + j] = (double)(v * (C)d[j]);
-      if (bi != (j >> 5)) Ub[(size_t)i * l + j] = v;
+  // outputs: Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a
+  // diagonal block (i <= j), 0 below;  R(i, j) = L(j, i) d_j for i <= j
+  for (int e = tid; e < l * l; e += NT) {
+    const int i = e / l, j = e % l;
+    const int bi = i / CBK, bj = j / CBK;
+    C v = C(0);
+    double rv = 0.0;
+    if (i <= j) {
+      const C lji = Ls[(size_t)lblk(bj, bi) * CBS + (j % CBK) * CP + (i % CBK)];
+      v = (bi == bj) ? Xs[(size_t)bj * CBS + (j % CBK) * CP + (i % CBK)] : lji;
+      rv = (double)lji * d[j];
     }
+    Ub[e] = v;
+    if (R) R[e] = rv;
   }
-  // diagonal blocks of Ub: (L(bb, bb)^-1)^T, one warp per block
-  const int nb = (l + 31) / 32;
-  for (int bb = warp; bb < nb; bb += nt / 32) {
-    const int c0 = 32 * bb, w = min(32, l - c0);
-    const int i = c0 + lane;
-    C x[32];
-    warp_trinv32<C>(a, cb, c0, w, x);
-    // x = row `lane` of L^-1; Ub(c0 + c, c0 + lane) = L^-1(lane, c), i.e. column lane of the transposed inverse
-    if (lane < w) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < w) Ub[(size_t)(c0 + c) * l + c0 + lane] = x[c];
-    }
-  }
-  for (int i = tid; i < l; i += nt) dinv[i] = rdc[i];
+  for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
 }
 
 size_t chol_smem_bytes(int l, size_t csize) {
-  return (((size_t)l * (l + 1) / 2 * csize + 15) & ~(size_t)15) + (size_t)l * sizeof(double) +
-         (size_t)2 * l * csize + (size_t)l * sizeof(int);
+  const int NB = (l + CBK - 1) / CBK;
+  const size_t blocks = (size_t)NB * (NB + 1) / 2 + NB;
+  return blocks * CBS * csize + (size_t)l * sizeof(double) + (size_t)l * csize + (size_t)CBK * NB * csize;
 }
 
 // ----------------------------------------------------------------- apply --
@@ -437,6 +624,60 @@ size_t chol_smem_bytes(int l, size_t csize) {
 //   acc_c += q_b Ub(b, c) for later blocks c (each thread owns a 8 x 8 tile:
 //            rows ty + 8 x, columns tx + 32 y)
 // Optionally writes a bf16 copy of Q.
+constexpr int AP_ROWS = 64;
+
+// dst[r * dld + c] = src[r * sld + c] for r < nrows, c < ncols (rows r >= nr
+// read as zero), by the whole CTA with eight independent loads in flight per
+// thread (16-byte loads when every row is 16-byte aligned).
+template <typename T, typename C>
+__device__ __forceinline__ void stage_rows(C* dst, int dld, const T* src, int sld, int nrows, int nr, int ncols) {
+  const bool vec = sizeof(T) == 4 && sizeof(C) == 4 && (sld % 4) == 0 && (dld % 4) == 0 && (ncols % 4) == 0 &&
+                   (((uintptr_t)src | (uintptr_t)dst) & 15) == 0;
+  const int nt = blockDim.x;
+  if (vec) {
+    const int cv = ncols / 4, total = nrows * cv;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * nt) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nt;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < total) {
+          const int r = e / cv, c = e % cv;
+          if (r < nr) v[u] = *reinterpret_cast<const float4*>(src + (size_t)r * sld + 4 * c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * nt;
+        if (e < total) {
+          const int r = e / cv, c = e % cv;
+          *reinterpret_cast<float4*>(dst + (size_t)r * dld + 4 * c) = v[u];
+        }
+      }
+    }
+    return;
+  }
+  const int total = nrows * ncols;
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * nt) {
+    C v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt;
+      v[u] = C(0);
+      if (e < total) {
+        const int r = e / ncols, c = e % ncols;
+        if (r < nr) v[u] = (C)src[(size_t)r * sld + c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * nt;
+      if (e < total) dst[(size_t)(e / ncols) * dld + e % ncols] = v[u];
+    }
+  }
+}
+
 template <typename T, typename C>
 __global__ void __launch_bounds__(256)
     apply_kernel(int rows, int l, T* __restrict__ Y, int ldy, const C* __restrict__ Ub, const C* __restrict__ dinv,
@@ -448,10 +689,10 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
   const int r0 = blockIdx.x * 64;
   const int nr = min(64, rows - r0);
-  // stage the stripe (row by row, no index division), scaled by dinv
-  for (int r = 0; r < 64; ++r)
-    for (int c = tid; c < l; c += 256)
-      ys[(size_t)r * l + c] = (r < nr) ? (C)Y[(size_t)(r0 + r) * ldy + c] * dinv[c] : C(0);
+  // stage the stripe, then scale it by dinv
+  stage_rows<T, C>(ys, l, Y + (size_t)r0 * ldy, ldy, AP_ROWS, nr, l);
+  __syncthreads();
+  for (int e = tid; e < AP_ROWS * l; e += 256) ys[e] *= dinv[e % l];
   C acc[8][8];
 #pragma unroll
   for (int x = 0; x < 8; ++x)
@@ -465,9 +706,8 @@ __global__ void __launch_bounds__(256)
     if (b < nb) {
       const int k0 = 32 * b, kw = min(32, l - k0);
       __syncthreads();  // previous block's reads of rs / ys are done
-      for (int kk = ty; kk < 32; kk += 8)
-        for (int c = tx; c < l; c += 32)
-          rs[(size_t)kk * l + c] = (kk < kw && c >= k0) ? Ub[(size_t)(k0 + kk) * l + c] : C(0);
+      // rows k0 .. k0 + kw of Ub, columns from k0 on (Ub is zero to the left)
+      stage_rows<C, C>(rs + k0, l, Ub + (size_t)k0 * l + k0, l, 32, kw, l - k0);
       // r_b into ys (thread's column k0 + tx, rows ty + 8 x)
       const int cb_ = k0 + tx;
       if (tx < kw) {
@@ -532,8 +772,9 @@ void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __
 template <typename C>
 void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
                  const int* gate, cudaStream_t s, const int* skip) {
-  // binary32: 1024 threads; binary64 (l <= 128): 256 threads with room for registers
-  constexpr int NT = sizeof(C) == 4 ? 1024 : 256;
+  // binary32: 512 threads (128 registers each: the diagonal-block warp keeps a
+  // row of L and a row of its inverse in registers); binary64 (l <= 128): 256
+  constexpr int NT = sizeof(C) == 4 ? 512 : 256;
   const size_t smem = chol_smem_bytes(l, sizeof(C));
   auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -45,18 +45,59 @@ __device__ __forceinline__ int rr_where(int x, int r, int P) {
   return 1 + v;
 }
 
-// Rx, Jx: buffers of w columns, each column l contiguous values.
+// 16-byte vectors of the working type.
+template <typename C>
+struct JVec;
+template <>
+struct JVec<float> {
+  using T = float4;
+  static constexpr int W = 4;
+  static __device__ __forceinline__ float dot(const float4& a, const float4& b, float s) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+  }
+  static __device__ __forceinline__ void rot(float4& a, float4& b, float c, float s) {
+    const float4 x = a, y = b;
+    a = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
+    b = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
+  }
+};
+template <>
+struct JVec<double> {
+  using T = double2;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ double dot(const double2& a, const double2& b, double s) {
+    return fma(a.y, b.y, fma(a.x, b.x, s));
+  }
+  static __device__ __forceinline__ void rot(double2& a, double2& b, double c, double s) {
+    const double2 x = a, y = b;
+    a = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+    b = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
+  }
+};
+
+// Padded column length: a multiple of 32 lanes x one 16-byte vector.  A
+// column occupies lp + W entries; entry lp holds its squared norm.
+__host__ __device__ inline int jac_lp(int l, int vw) { return (l + 32 * vw - 1) / (32 * vw) * (32 * vw); }
+
+// Buffers: four slots (two current blocks, two being received), each w
+// columns of X then w columns of J.  The squared column norms are carried
+// with the columns and updated by the rotation formulas (Rutishauser:
+// alpha' = alpha - t gamma, beta' = beta + t gamma); they are recomputed at
+// the start of every sweep.
 template <typename C>
 __global__ void __launch_bounds__(512)
     jacobi_cluster_kernel(int l, int w, const double* __restrict__ Rb, C* __restrict__ Wt,
                           C* __restrict__ Jt, double* __restrict__ sigma, DevStatus* st, int max_sweeps) {
+  using V = typename JVec<C>::T;
+  constexpr int VW = JVec<C>::W;
   cg::cluster_group cluster = cg::this_cluster();
   const int NC = (int)cluster.num_blocks();
   const int me = (int)cluster.block_rank();
   const int P = 2 * NC;
-  extern __shared__ unsigned char smem_raw[];
+  const int lp = jac_lp(l, VW), cs = lp + VW, nv = lp / (32 * VW);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  const size_t blk = (size_t)2 * w * l;  // X then J, w columns each
+  const size_t blk = (size_t)2 * w * cs;  // X then J, w columns each
   __shared__ int s_rot;
   __shared__ int s_total;
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
@@ -66,17 +107,28 @@ __global__ void __launch_bounds__(512)
   // round 0: CTA me holds players rr_pos(me, 0), rr_pos(P-1-me, 0)
   auto load_block = [&](C* dst, int bid) {
     C* X = dst;
-    C* J = dst + (size_t)w * l;
-    for (int e = tid; e < w * l; e += blockDim.x) {
-      const int cc = e / l, r = e % l;
-      const int col = bid * w + cc;
-      C xv = C(0), jv = C(0);
-      if (col < l) {
-        xv = (C)Rb[(size_t)col * l + r];  // column col of M = row col of R_B
-        jv = (r == col) ? C(1) : C(0);
+    C* J = dst + (size_t)w * cs;
+    const int total = w * cs;
+    for (int e0 = tid; e0 < total; e0 += 8 * blockDim.x) {
+      C v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = C(0);
+        if (e < total) {
+          const int cc = e / cs, r = e % cs, col = bid * w + cc;
+          if (col < l && r < l) v[u] = (C)Rb[(size_t)col * l + r];  // column col of M = row col of R_B
+        }
       }
-      X[e] = xv;
-      J[e] = jv;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) {
+          const int cc = e / cs, r = e % cs, col = bid * w + cc;
+          X[e] = v[u];
+          J[e] = (col < l && r == col) ? C(1) : C(0);
+        }
+      }
     }
   };
   load_block(buf + 0 * blk, rr_pos(me, 0, P));
@@ -88,6 +140,18 @@ __global__ void __launch_bounds__(512)
   bool converged = false;
   for (; sweep < max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
+    {  // fresh squared norms of the 2w columns this CTA holds
+      const int par = (sweep * (P - 1)) & 1;
+      for (int cc = warp; cc < 2 * w; cc += nwarps) {
+        C* x = buf + (size_t)(2 * par + cc / w) * blk + (size_t)(cc % w) * cs;
+        const V* xv = reinterpret_cast<const V*>(x);
+        C a = C(0);
+        for (int v = 0; v < nv; ++v) a = JVec<C>::dot(xv[v * 32 + lane], xv[v * 32 + lane], a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) x[lp] = a;
+      }
+    }
     __syncthreads();
     for (int r = 0; r < P - 1; ++r) {
       const int par = (sweep * (P - 1) + r) & 1;
@@ -110,26 +174,19 @@ __global__ void __launch_bounds__(512)
             ia = pr;
             ib = w + (pr + step) % w;
           }
-          C* xa = (ia < w ? top : bot) + (size_t)(ia % w) * l;
-          C* xb = (ib < w ? top : bot) + (size_t)(ib % w) * l;
-          C* ja = xa + (size_t)w * l;
-          C* jb = xb + (size_t)w * l;
-          C al = C(0), be = C(0), ga = C(0);
-          for (int i = lane; i < l; i += 32) {
-            const C a = xa[i], b = xb[i];
-            al = fma(a, a, al);
-            be = fma(b, b, be);
-            ga = fma(a, b, ga);
-          }
-          // xor butterflies leave the identical sums in every lane (each level
-          // adds the same two operands, only swapped), so the rotation
-          // decision below is warp-uniform without a broadcast
+          C* xa = (ia < w ? top : bot) + (size_t)(ia % w) * cs;
+          C* xb = (ib < w ? top : bot) + (size_t)(ib % w) * cs;
+          V* va = reinterpret_cast<V*>(xa);
+          V* vb = reinterpret_cast<V*>(xb);
+          V* ja = reinterpret_cast<V*>(xa + (size_t)w * cs);
+          V* jb = reinterpret_cast<V*>(xb + (size_t)w * cs);
+          C ga = C(0);
+          for (int v = 0; v < nv; ++v) ga = JVec<C>::dot(va[v * 32 + lane], vb[v * 32 + lane], ga);
+          // xor butterflies leave the identical sum in every lane, so the
+          // rotation decision below is warp-uniform without a broadcast
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            ga += __shfl_xor_sync(0xffffffffu, ga, o);
-          }
+          for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          const C al = xa[lp], be = xb[lp];
           if (al > C(0) && be > C(0) && fabs(ga) > (C)tol * sqrt(al * be)) {
             // Rutishauser's formulas: zeta = (beta - alpha) / (2 gamma),
             // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
@@ -138,15 +195,22 @@ __global__ void __launch_bounds__(512)
             const C t = (az > C(1e15) ? C(0.5) / az : C(1) / (az + sqrt(C(1) + zeta * zeta))) *
                         (zeta >= C(0) ? C(1) : C(-1));
             const C c = C(1) / sqrt(C(1) + t * t), s = c * t;
-            for (int i = lane; i < l; i += 32) {
-              const C a = xa[i], b = xb[i];
-              xa[i] = c * a - s * b;
-              xb[i] = s * a + c * b;
-              const C p = ja[i], q = jb[i];
-              ja[i] = c * p - s * q;
-              jb[i] = s * p + c * q;
+            for (int v = 0; v < nv; ++v) {
+              V a = va[v * 32 + lane], b = vb[v * 32 + lane];
+              JVec<C>::rot(a, b, c, s);
+              va[v * 32 + lane] = a;
+              vb[v * 32 + lane] = b;
+              V p = ja[v * 32 + lane], q = jb[v * 32 + lane];
+              JVec<C>::rot(p, q, c, s);
+              ja[v * 32 + lane] = p;
+              jb[v * 32 + lane] = q;
             }
-            if (lane == 0) atomicAdd(&s_rot, 1);
+            __syncwarp();
+            if (lane == 0) {
+              xa[lp] = al - t * ga;
+              xb[lp] = be + t * ga;
+              atomicAdd(&s_rot, 1);
+            }
           }
         }
         __syncthreads();
@@ -211,12 +275,12 @@ __global__ void __launch_bounds__(512)
   for (int half = 0; half < 2; ++half) {
     const int player = rr_pos(half == 0 ? me : P - 1 - me, (sweep * (P - 1)) % (P - 1), P);
     const C* X = buf + (size_t)(2 * par + half) * blk;
-    const C* J = X + (size_t)w * l;
+    const C* J = X + (size_t)w * cs;
     for (int cc = warp; cc < w; cc += nwarps) {
       const int col = player * w + cc;
       if (col >= l) continue;
-      const C* x = X + (size_t)cc * l;
-      const C* jv = J + (size_t)cc * l;
+      const C* x = X + (size_t)cc * cs;
+      const C* jv = J + (size_t)cc * cs;
       double ss = 0.0;
       C part = C(0);
       for (int i = lane; i < l; i += 32) part = fma(x[i], x[i], part);
@@ -244,7 +308,8 @@ int jacobi_cluster_size(int l) {
 size_t jacobi_smem_bytes(int l, size_t csize) {
   const int nc = jacobi_cluster_size(l);
   const int w = (l + 2 * nc - 1) / (2 * nc);
-  return (size_t)4 * 2 * w * l * csize;
+  const int vw = (int)(16 / csize);
+  return (size_t)4 * 2 * w * (jac_lp(l, vw) + vw) * csize;
 }
 
 template <typename C>

@@ -23,6 +23,10 @@ Parity status per function:
   first Adam step, brute-force label and eps-rank checks, eq. (infomm) and
   Lemma thm:aposteriori over seeds).  What the trained network predicts has
   no pin: it is judged by the gain it brings, not by parity.
+* fp8 (e4m3 values, rounding, row/column scaling, the scaled sketch
+  products): pinned (the value set and all 256 codes from the format's
+  definition, round trip, ties to even at every midpoint, saturation, brute
+  force over 8000 values, exact products on representable operands).
 """
 from .philox import (philox4x32_10, gaussian, omega_words, box_muller, seed_key,
                      STREAM_SKETCH, STREAM_ADAPTIVE, STREAM_CERTIFY, STREAM_ADAPTIVE2, STREAM_NORM)
@@ -31,3 +35,4 @@ from .norms import fro_residual, spectral_residual, certificate, theorem_bounds
 from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_finder,
                        adaptive_range_finder)
 from . import controller
+from . import fp8

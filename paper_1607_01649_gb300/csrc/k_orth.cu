@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(NT)
   __shared__ int s_fail;
   __shared__ unsigned char s_bi[64], s_bj[64];
   const int tid = threadIdx.x;
-  const int warp = tid / 32, nw = NT / 32;
+  const int warp = tid / 32, lane = tid % 32, nw = NT / 32;
   const double u = Eps<C>::u;
   const C ctau = (C)(1024.0 * u);
   const double s0 = 16384.0 * u;
@@ -483,37 +483,36 @@ __global__ void __launch_bounds__(NT)
   int attempt = 0;
   for (;;) {
     // unit-diagonal scaling Gt = D^-1 G D^-1 (+ shift) in the working
-    // precision, read row by row (G is symmetric), eight independent loads
-    // in flight per thread (a load-then-store loop would wait out the memory
-    // latency once per element)
-    for (int e0 = tid; e0 < nblk * CBK * CBK; e0 += 8 * NT) {
-      C v[8];
-#pragma unroll
-      for (int uu = 0; uu < 8; ++uu) {
-        const int e = e0 + uu * NT;
-        v[uu] = C(0);
-        if (e < nblk * CBK * CBK) {
-          const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
-          const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
-          if (i < l && j < l) v[uu] = sizeof(C) == 4 ? (C)Gf[(size_t)i * l + j] : (C)G[(size_t)i * l + j];
-        }
+    // precision: asynchronous copies of G (row by row; G is symmetric) into
+    // the blocks, then the scaling in place
+    for (int e = tid; e < nblk * CBK * CBK; e += NT) {
+      const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+      const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
+      C* dst = Ls + (size_t)b * CBS + r * CP + c;
+      if (i < l && j < l) {
+        if (sizeof(C) == 4)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                       "l"(Gf + (size_t)i * l + j)
+                       : "memory");
+        else
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                       "l"(G + (size_t)i * l + j)
+                       : "memory");
+      } else {
+        *dst = (i == j) ? C(1) : C(0);
       }
-#pragma unroll
-      for (int uu = 0; uu < 8; ++uu) {
-        const int e = e0 + uu * NT;
-        if (e < nblk * CBK * CBK) {
-          const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
-          const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
-          C w;
-          if (i < l && j < l) {
-            w = v[uu] * rdc[i] * rdc[j];
-            if (i == j) w += shift;
-            if (!isfinite(w)) w = C(0);
-          } else {
-            w = (i == j) ? C(1) : C(0);
-          }
-          Ls[(size_t)b * CBS + r * CP + c] = w;
-        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    for (int e = tid; e < nblk * CBK * CBK; e += NT) {
+      const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+      const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
+      if (i < l && j < l) {
+        C* p = Ls + (size_t)b * CBS + r * CP + c;
+        C w = *p * rdc[i] * rdc[j];
+        if (i == j) w += shift;
+        if (!isfinite(w)) w = C(0);
+        *p = w;
       }
     }
     if (tid == 0) s_fail = 0;
@@ -592,18 +591,20 @@ __global__ void __launch_bounds__(NT)
   }
   // outputs: Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a
   // diagonal block (i <= j), 0 below;  R(i, j) = L(j, i) d_j for i <= j
-  for (int e = tid; e < l * l; e += NT) {
-    const int i = e / l, j = e % l;
-    const int bi = i / CBK, bj = j / CBK;
-    C v = C(0);
-    double rv = 0.0;
-    if (i <= j) {
-      const C lji = Ls[(size_t)lblk(bj, bi) * CBS + (j % CBK) * CP + (i % CBK)];
-      v = (bi == bj) ? Xs[(size_t)bj * CBS + (j % CBK) * CP + (i % CBK)] : lji;
-      rv = (double)lji * d[j];
+  for (int i = warp; i < l; i += nw) {
+    const int bi = i >> 5, ii = i & 31;
+    for (int j = lane; j < l; j += 32) {
+      const int bj = j >> 5, jj = j & 31;
+      C v = C(0);
+      double rv = 0.0;
+      if (i <= j) {
+        const C lji = Ls[(size_t)lblk(bj, bi) * CBS + jj * CP + ii];
+        v = (bi == bj) ? Xs[(size_t)bj * CBS + jj * CP + ii] : lji;
+        rv = (double)lji * d[j];
+      }
+      Ub[(size_t)i * l + j] = v;
+      if (R) R[(size_t)i * l + j] = rv;
     }
-    Ub[e] = v;
-    if (R) R[e] = rv;
   }
   for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
 }

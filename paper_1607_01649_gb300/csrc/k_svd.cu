@@ -75,6 +75,32 @@ struct JVec<double> {
   }
 };
 
+// Rotation of the pair with squared norms al, be and inner product ga
+// (Rutishauser): zeta = (be - al) / (2 ga), t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2).  binary32: the angle needs no
+// correctly rounded division or square root (any angle near it still gives an
+// orthogonal rotation; the sweep's convergence test measures what is left),
+// so the hardware reciprocal square root and fast division are used.
+template <typename C>
+__device__ __forceinline__ void jac_rotation(C al, C be, C ga, C& t, C& c);
+template <>
+__device__ __forceinline__ void jac_rotation<float>(float al, float be, float ga, float& t, float& c) {
+  const float zeta = __fdividef(be - al, 2.0f * ga);
+  const float az = fabsf(zeta);
+  const float q = 1.0f + zeta * zeta;
+  const float tt = az > 1e15f ? __fdividef(0.5f, az) : __fdividef(1.0f, az + q * rsqrtf(q));
+  t = zeta >= 0.0f ? tt : -tt;
+  c = rsqrtf(1.0f + t * t);
+}
+template <>
+__device__ __forceinline__ void jac_rotation<double>(double al, double be, double ga, double& t, double& c) {
+  const double zeta = (be - al) / (2.0 * ga);
+  const double az = fabs(zeta);
+  const double tt = az > 1e15 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + zeta * zeta));
+  t = zeta >= 0.0 ? tt : -tt;
+  c = 1.0 / sqrt(1.0 + t * t);
+}
+
 // Padded column length: a multiple of 32 lanes x one 16-byte vector.  A
 // column occupies lp + W entries; entry lp holds its squared norm.
 __host__ __device__ inline int jac_lp(int l, int vw) { return (l + 32 * vw - 1) / (32 * vw) * (32 * vw); }
@@ -103,6 +129,14 @@ __global__ void __launch_bounds__(512)
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int nwarps = blockDim.x / 32;
   const double tol = 16.0 * sqrt((double)l) * JacobiTol<C>::u;
+  const C tol2 = (C)(tol * tol);
+  // pairs of the full round (circle method on 2w players), step-major
+  __shared__ unsigned char s_pair[64 * 32 * 2];
+  for (int e = tid; e < (2 * w - 1) * w; e += blockDim.x) {
+    const int step = e / w, pr = e % w;
+    s_pair[2 * e] = (unsigned char)rr_pos(pr, step, 2 * w);
+    s_pair[2 * e + 1] = (unsigned char)rr_pos(2 * w - 1 - pr, step, 2 * w);
+  }
 
   // round 0: CTA me holds players rr_pos(me, 0), rr_pos(P-1-me, 0)
   auto load_block = [&](C* dst, int bid) {
@@ -168,14 +202,16 @@ __global__ void __launch_bounds__(512)
         for (int pr = warp; pr < w; pr += nwarps) {
           int ia, ib;
           if (full_round) {
-            ia = rr_pos(pr, step, Q2);
-            ib = rr_pos(Q2 - 1 - pr, step, Q2);
+            ia = s_pair[2 * (step * w + pr)];
+            ib = s_pair[2 * (step * w + pr) + 1];
           } else {
             ia = pr;
-            ib = w + (pr + step) % w;
+            ib = pr + step;
+            if (ib >= w) ib -= w;
+            ib += w;
           }
-          C* xa = (ia < w ? top : bot) + (size_t)(ia % w) * cs;
-          C* xb = (ib < w ? top : bot) + (size_t)(ib % w) * cs;
+          C* xa = (ia < w ? top + (size_t)ia * cs : bot + (size_t)(ia - w) * cs);
+          C* xb = (ib < w ? top + (size_t)ib * cs : bot + (size_t)(ib - w) * cs);
           V* va = reinterpret_cast<V*>(xa);
           V* vb = reinterpret_cast<V*>(xb);
           V* ja = reinterpret_cast<V*>(xa + (size_t)w * cs);
@@ -187,14 +223,12 @@ __global__ void __launch_bounds__(512)
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
           const C al = xa[lp], be = xb[lp];
-          if (al > C(0) && be > C(0) && fabs(ga) > (C)tol * sqrt(al * be)) {
+          if (al > C(0) && be > C(0) && ga * ga > tol2 * al * be) {
             // Rutishauser's formulas: zeta = (beta - alpha) / (2 gamma),
             // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
-            const C zeta = (be - al) / (C(2) * ga);
-            const C az = fabs(zeta);
-            const C t = (az > C(1e15) ? C(0.5) / az : C(1) / (az + sqrt(C(1) + zeta * zeta))) *
-                        (zeta >= C(0) ? C(1) : C(-1));
-            const C c = C(1) / sqrt(C(1) + t * t), s = c * t;
+            C t, c;
+            jac_rotation<C>(al, be, ga, t, c);
+            const C s = c * t;
             for (int v = 0; v < nv; ++v) {
               V a = va[v * 32 + lane], b = vb[v * 32 + lane];
               JVec<C>::rot(a, b, c, s);

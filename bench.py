@@ -1,11 +1,14 @@
 """Benchmark: randomized SVD solves/s on one GB300 (or N replicas).
 
-Workload: the polynomial-decay matrix A = U diag(j^-1.5) V^T, 32768 x 32768
-float32 with Haar U, V (4.29 GB, far larger than the 129 MB L2), rank k = 200
-with p = 56 (l = 256) and q = 2 power steps.  One step = one full
-rsvd_fixed_rank call (every row of the path: Omega, the six tensor-core passes
-over A, CholeskyQR2 after each product, B^T = A^T Q in split bf16, the small
-SVD, the lift to U and V).
+Default workload: the polynomial-decay matrix A = U diag(j^-1.5) V^T, 32768 x
+32768 float32 with Haar U, V (4.29 GB, far larger than the 129 MB L2), rank
+k = 200 with p = 56 (l = 256) and q = 2 power steps, bf16 sketches.  One step
+= one full rsvd_fixed_rank call (every row of the path: Omega, the six
+tensor-core passes over A, CholeskyQR2 after each product, B^T = A^T Q in
+split bf16, the small SVD, the lift to U and V).
+
+``--workload pca``: the 2^20 x 4096 PCA-shaped matrix (rank-64 signal plus
+noise, column-centred), k = 64, p = 64, q = 1, e4m3 sketches.
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own
 matrix (replicas; there is no exchange step), and `value` is the total over
@@ -34,23 +37,49 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "f32"])
-    ap.add_argument("--m", type=int, default=32768)
-    ap.add_argument("--n", type=int, default=32768)
-    ap.add_argument("--k", type=int, default=200)
-    ap.add_argument("--p", type=int, default=56)
-    ap.add_argument("--q", type=int, default=2)
-    ap.add_argument("--seed", type=int, default=2001)
+    ap.add_argument("--workload", default="poly", choices=["poly", "pca"],
+                    help="poly: 32768^2 polynomial decay (bf16); pca: 2^20 x 4096 PCA matrix (e4m3)")
+    ap.add_argument("--prec", default=None, choices=["bf16", "f32", "fp8"])
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--q", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f32", action="store_true")
-    ap.add_argument("--sample", type=int, default=8192, help="CPU oracle sample size (square)")
-    return ap.parse_args()
+    ap.add_argument("--sample", type=int, default=None, help="CPU oracle sample size (rows; square for poly)")
+    a = ap.parse_args()
+    dflt = {"poly": dict(prec="bf16", m=32768, n=32768, k=200, p=56, q=2, seed=2001, sample=8192),
+            "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768)}[a.workload]
+    for key, val in dflt.items():
+        if getattr(a, key) is None:
+            setattr(a, key, val)
+    return a
 
 
 def workload_name(a):
+    if a.workload == "pca":
+        return ("PCA %dx%d fp32, rank-64 signal (sigma 100 -> 1) + N(0, 1e-6) noise, column-centred; "
+                "k=%d p=%d (l=%d) q=%d" % (a.m, a.n, a.k, a.p, a.k + a.p, a.q))
     return "poly-decay %dx%d fp32, sigma_j=j^-1.5, Haar U,V; k=%d p=%d (l=%d) q=%d" % (
         a.m, a.n, a.k, a.p, a.k + a.p, a.q)
+
+
+def make_workload(a, m, n, seed, device):
+    from workloads import poly_decay_matrix, pca_matrix
+    if a.workload == "pca":
+        return pca_matrix(m, n, seed=seed, device=device)
+    return poly_decay_matrix(m, n, seed=seed, device=device)
+
+
+def sample_shape(a):
+    """Shape of the CPU oracle's sample of the workload."""
+    if a.workload == "pca":
+        return min(a.sample, a.m), a.n
+    s = min(a.sample, a.m, a.n)
+    return s, s
 
 
 # ------------------------------------------------------------------ clocks --
@@ -152,11 +181,12 @@ def oracle_sample(a, seconds=12.0, device=None):
     passes are linear in m*n).  Returns (solves_per_s_full_size, detail)."""
     import numpy as np
     import oracle
-    s = min(a.sample, a.m, a.n)
-    A = _make_matrix(s, s, a.seed, device).astype(np.float64) if device is not None else None
+    sm_, sn_ = sample_shape(a)
+    A = _make_matrix(a, sm_, sn_, a.seed, device).astype(np.float64) if device is not None else None
     if A is None:
-        from workloads import poly_decay_matrix_np
-        A = poly_decay_matrix_np(s, s, a.seed).astype(np.float64)
+        from workloads import poly_decay_matrix_np, pca_matrix_np
+        A = (pca_matrix_np(sm_, sn_, a.seed) if a.workload == "pca" else
+             poly_decay_matrix_np(sm_, sn_, a.seed)).astype(np.float64)
     times = []
     t_start = time.perf_counter()
     while True:
@@ -166,16 +196,15 @@ def oracle_sample(a, seconds=12.0, device=None):
         if time.perf_counter() - t_start > seconds or len(times) >= 20:
             break
     t = statistics.median(times)
-    scale = (a.m * a.n) / float(s * s)
+    scale = (a.m * a.n) / float(sm_ * sn_)
     detail = ("float64 oracle rsvd_power on a %dx%d matrix of the same family (k=%d p=%d q=%d), %d solve(s), "
-              "median %.3f s, scaled by m*n ratio %.1f" % (s, s, a.k, a.p, a.q, len(times), t, scale))
+              "median %.3f s, scaled by m*n ratio %.1f" % (sm_, sn_, a.k, a.p, a.q, len(times), t, scale))
     return 1.0 / (t * scale), detail, t, len(times)
 
 
-def _make_matrix(m, n, seed, device):
+def _make_matrix(a, m, n, seed, device):
     import torch
-    from workloads import poly_decay_matrix
-    A = poly_decay_matrix(m, n, seed=seed, device=device)
+    A = make_workload(a, m, n, seed, device)
     out = A.cpu().numpy()
     del A
     torch.cuda.empty_cache()
@@ -195,22 +224,23 @@ def run_reference(a):
         dev = None
     import numpy as np
     import oracle
-    s = min(a.sample, a.m, a.n)
+    sm_, sn_ = sample_shape(a)
     if dev is not None:
-        A = _make_matrix(s, s, a.seed, dev).astype(np.float64)
+        A = _make_matrix(a, sm_, sn_, a.seed, dev).astype(np.float64)
     else:
-        from workloads import poly_decay_matrix_np
-        A = poly_decay_matrix_np(s, s, a.seed).astype(np.float64)
+        from workloads import poly_decay_matrix_np, pca_matrix_np
+        A = (pca_matrix_np(sm_, sn_, a.seed) if a.workload == "pca" else
+             poly_decay_matrix_np(sm_, sn_, a.seed)).astype(np.float64)
     for _ in range(a.warmup):
         oracle.rsvd_power(A, a.k, a.p, a.q, a.seed)
     t0 = time.perf_counter()
     for i in range(a.steps):
         oracle.rsvd_power(A, a.k, a.p, a.q, a.seed + i)
     dt = time.perf_counter() - t0
-    scale = (a.m * a.n) / float(s * s)
+    scale = (a.m * a.n) / float(sm_ * sn_)
     value = a.steps / dt / scale
     sample = ("float64 oracle rsvd_power on a %dx%d matrix of the same family (k=%d p=%d q=%d) per step, "
-              "time scaled by the m*n ratio %.1f" % (s, s, a.k, a.p, a.q, scale))
+              "time scaled by the m*n ratio %.1f" % (sm_, sn_, a.k, a.p, a.q, scale))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * dt / a.steps * scale,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -241,11 +271,10 @@ def run_ours(a):
             dist.barrier()
         torch.cuda.synchronize()
 
-    from workloads import poly_decay_matrix
     m, n, k, p, q = a.m, a.n, a.k, a.p, a.q
     l = k + p
-    prec = rs.RSVD_MIXED_BF16 if a.prec == "bf16" else rs.RSVD_F32
-    A = poly_decay_matrix(m, n, seed=a.seed + rank, device=dev)
+    prec = {"bf16": rs.RSVD_MIXED_BF16, "fp8": rs.RSVD_MIXED_FP8, "f32": rs.RSVD_F32}[a.prec]
+    A = make_workload(a, m, n, a.seed + rank, dev)
     h = rs.handle(local)
     prm = rs.make_params(k, p, q, seed=a.seed, prec=prec, flags=0)
     ws = torch.empty(rs.rsvd_workspace_size(h, m, n, prm), dtype=torch.uint8, device=dev)
@@ -300,20 +329,33 @@ def run_ours(a):
     diag = rs.status_block(ws)
 
     # ---- accuracy of the last solve (not timed): singular values against the
-    # construction sigma_j = j^-1.5, Frobenius residual in float64 blockwise
+    # construction, Frobenius residual in float64 blockwise
     torch.cuda.synchronize()
-    sig_true = torch.arange(1, k + 1, dtype=torch.float64, device=dev).pow(-1.5)
-    d_rel = float(((D - sig_true).abs() / sig_true).max())
-    fro2 = 0.0
-    Ud = (U.double() * D[None, :])
-    for r0 in range(0, m, 4096):
-        R = A[r0:r0 + 4096].double() - Ud[r0:r0 + 4096] @ V.double().T
-        fro2 += float((R * R).sum())
-    fro_a = float(torch.linalg.norm(A.double()))
-    fro_opt = float(torch.arange(k + 1, min(m, n) + 1, dtype=torch.float64).pow(-3.0).sum().sqrt())
-    err = {"max_rel_err_sigma_1..k_vs_construction": d_rel,
-           "fro_residual_rel": (fro2 ** 0.5) / fro_a,
-           "fro_residual_optimal_rel(Eckart-Young)": fro_opt / fro_a}
+
+    def fro_rel(Uo, Do, Vo):
+        f2, a2 = 0.0, 0.0
+        Ud = (Uo.double() * Do[None, :])
+        for r0 in range(0, m, 4096):
+            Ab = A[r0:r0 + 4096].double()
+            R = Ab - Ud[r0:r0 + 4096] @ Vo.double().T
+            f2 += float((R * R).sum())
+            a2 += float((Ab * Ab).sum())
+        return (f2 / a2) ** 0.5, a2 ** 0.5
+
+    res_rel, fro_a = fro_rel(U, D, V)
+    if a.workload == "pca":
+        # the signal's singular values (the noise moves them by about its norm)
+        sig_true = torch.linspace(100.0, 1.0, 64, dtype=torch.float64, device=dev)[:k]
+        nk = min(k, 48)
+        d_rel = float(((D[:nk] - sig_true[:nk]).abs() / sig_true[:nk]).max())
+        err = {"max_rel_err_sigma_1..48_vs_signal": d_rel, "fro_residual_rel": res_rel,
+               "noise_floor_rel": 1e-3 * (m * n) ** 0.5 / fro_a}
+    else:
+        sig_true = torch.arange(1, k + 1, dtype=torch.float64, device=dev).pow(-1.5)
+        d_rel = float(((D - sig_true).abs() / sig_true).max())
+        fro_opt = float(torch.arange(k + 1, min(m, n) + 1, dtype=torch.float64).pow(-3.0).sum().sqrt())
+        err = {"max_rel_err_sigma_1..k_vs_construction": d_rel, "fro_residual_rel": res_rel,
+               "fro_residual_optimal_rel(Eckart-Young)": fro_opt / fro_a}
 
     # ---- roofline of the dominant kernel: the tcgen05 sketch product
     roof = None
@@ -323,14 +365,22 @@ def run_ours(a):
         peak_src = "measured"
     except Exception:
         hbm, peak_src = 6800.0, "fallback"
-    if prec == rs.RSVD_MIXED_BF16 and sk_n > 0:
+    if prec in (rs.RSVD_MIXED_BF16, rs.RSVD_MIXED_FP8) and sk_n > 0:
         per_launch_ms = sk_ms / sk_n
-        # algorithmic bytes of one sketch product: A in bf16 once, X in bf16, Y in fp32
-        alg_bytes = 2.0 * m * n + 2.0 * n * l + 4.0 * m * l
+        # algorithmic bytes of the sketch products of one solve: A once per
+        # product (bf16: 2 bytes, e4m3: 1 byte per entry), the thin operand in the
+        # same type, the fp32 output; q + 1 products A X (m x l out), q products
+        # A^T X (n x l out); averaged per launch
+        eb = 2.0 if prec == rs.RSVD_MIXED_BF16 else 1.0
+        nn_b = eb * m * n + eb * n * l + 4.0 * m * l
+        tn_b = eb * m * n + eb * m * l + 4.0 * n * l
+        alg_bytes = ((q + 1) * nn_b + q * tn_b) / (2 * q + 1)
         achieved = alg_bytes / (per_launch_ms / 1000.0) / 1e9
+        kname = ("tc_gemm_kernel (bf16 sketch A*X / A^T*X, stream-K)" if prec == rs.RSVD_MIXED_BF16 else
+                 "tc_gemm_kernel<..., F8> (e4m3 sketch A8*X8t^T, kind::f8f6f4, stream-K)")
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": tc_traffic(m, n), "algorithmic_bytes": alg_bytes,
-                "kernel": "tc_gemm_kernel (bf16 sketch A*X / A^T*X, stream-K)",
+                "traffic": tc_traffic(m, n) if prec == rs.RSVD_MIXED_BF16 else None,
+                "algorithmic_bytes": alg_bytes, "kernel": kname,
                 "launches": sk_n, "avg_ms": per_launch_ms, "peak_source": peak_src,
                 "projection_split3_avg_ms": (pj_ms / pj_n) if pj_n else None}
     elif prec == rs.RSVD_F32:
@@ -367,26 +417,29 @@ def run_ours(a):
                "steps": steps_e2e}
         del Ah
 
-    # ---- plain fp32 comparator (same workload, SIMT binary32 path), 1 solve
-    f32 = None
-    if prec == rs.RSVD_MIXED_BF16 and not a.no_f32:
-        prm32 = rs.make_params(k, p, q, seed=a.seed, prec=rs.RSVD_F32, flags=0)
-        ws32 = torch.empty(rs.rsvd_workspace_size(h, m, n, prm32), dtype=torch.uint8, device=dev)
-        U32 = torch.empty_like(U)
-        D32 = torch.empty_like(D)
-        V32 = torch.empty_like(V)
-        rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm32, U32, k, D32, V32, k, ws32)
+    # ---- comparators on the same matrix (1 timed solve each): the plain
+    # binary32 SIMT path, and for the e4m3 workload also the bf16 path
+    def comparator(pc):
+        prm2 = rs.make_params(k, p, q, seed=a.seed, prec=pc, flags=0)
+        ws2 = torch.empty(rs.rsvd_workspace_size(h, m, n, prm2), dtype=torch.uint8, device=dev)
+        U2, D2, V2 = torch.empty_like(U), torch.empty_like(D), torch.empty_like(V)
+        rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm2, U2, k, D2, V2, k, ws2)
         torch.cuda.synchronize()
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm32, U32, k, D32, V32, k, ws32)
+        rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm2, U2, k, D2, V2, k, ws2)
         g1.record(stream)
         torch.cuda.synchronize()
-        d32 = float(((D32 - sig_true).abs() / sig_true).max())
-        f32 = {"value": 1000.0 / g0.elapsed_time(g1), "unit": "solves/s",
-               "max_rel_err_sigma_1..k_vs_construction": d32}
-        del ws32
+        nk = min(k, 48) if a.workload == "pca" else k
+        d2 = float(((D2[:nk] - sig_true[:nk]).abs() / sig_true[:nk]).max())
+        out = {"value": 1000.0 / g0.elapsed_time(g1), "unit": "solves/s", "max_rel_err_sigma": d2,
+               "fro_residual_rel": fro_rel(U2, D2, V2)[0]}
+        del ws2
+        return out
+
+    f32 = comparator(rs.RSVD_F32) if (prec != rs.RSVD_F32 and not a.no_f32) else None
+    bf16 = comparator(rs.RSVD_MIXED_BF16) if (prec == rs.RSVD_MIXED_FP8 and not a.no_f32) else None
 
     if rank != 0:
         if dist is not None:
@@ -398,12 +451,13 @@ def run_ours(a):
         cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": detail}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if prec == rs.RSVD_MIXED_BF16 else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {rs.RSVD_MIXED_BF16: "bf16", rs.RSVD_MIXED_FP8: "e4m3"}.get(prec, "f32"),
+            "data": "synthetic",
             "config": {"workload": workload_name(a), "precision": a.prec,
                        "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB)" % (m * n * 4 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "error": err, "plain_f32": f32,
+            "error": err, "plain_f32": f32, "mixed_bf16": bf16,
             "diagnostics": {"jacobi_sweeps_last_solve": diag["jacobi_sweeps"],
                             "shifted_cholesky_last_solve": diag["shift_count"],
                             "sketch_launches_timed": sk_n, "projection_launches_timed": pj_n}}

@@ -70,7 +70,11 @@ typedef enum {
                           cores with bf16 operands and fp32 accumulation; the
                           final B = Q^T A as a three-term split-bf16 product;
                           Gram matrices accumulated in binary64 */
-  RSVD_MIXED_FP8 = 3   /* reserved: e4m3 sketch with per-128-row scales */
+  RSVD_MIXED_FP8 = 3   /* A, U, V float; A*Omega, A^T Q, A W on tcgen05 tensor
+                          cores with e4m3 operands (A scaled per row, the thin
+                          operand per column; scales applied in the epilogue)
+                          and fp32 accumulation; B = Q^T A as in
+                          RSVD_MIXED_BF16 (three-term split bf16) */
 } rsvd_precision;
 
 /* Element types for the stage entry points. */
@@ -213,8 +217,13 @@ rsvd_status rsvd_gaussian(rsvd_handle_t handle, int n, int l, uint64_t seed, uin
  *   trans = 1:  Y (n x l) = A^T (n x m) X (m x l)
  * A row-major m x n (lda).  prec RSVD_F64: A, X, Y double; RSVD_F32: float
  * (SIMT fp32); RSVD_MIXED_BF16: A and X bf16 (raw 16-bit storage), Y float,
- * tcgen05 tensor-core product with fp32 accumulation.  Needs workspace
- * (rsvd_sketch_workspace_size) for split-K partial sums. */
+ * tcgen05 tensor-core product with fp32 accumulation; RSVD_MIXED_FP8: A, X, Y
+ * float, the library converts A to e4m3 per row (r_i = 448 / max_j |A_ij|
+ * in binary32, A8 = e4m3(A_ij r_i) rounded to nearest, saturating) and the
+ * thin operand per column the same way, after scaling its rows by 1 / r_i
+ * when trans = 1 (A^T Q = A8^T (S Q)); the e4m3 product (tcgen05
+ * kind::f8f6f4, fp32 accumulation) is then rescaled.  Needs workspace
+ * (rsvd_sketch_workspace_size) for split-K partial sums and the 8-bit copies. */
 rsvd_status rsvd_sketch_workspace_size(rsvd_handle_t handle, int prec, int trans, int m, int n,
                                        int l, size_t* bytes);
 rsvd_status rsvd_sketch(rsvd_handle_t handle, int prec, int trans, int m, int n, int l,

@@ -1,0 +1,205 @@
+// Conversions for the e4m3 (FP8) sketch: the sample products of Fig.
+// RSVDP_stabilized (A G, A^T Q, A W) taken with 8-bit operands.
+//
+//   rows:  A (fp32) -> A8 = e4m3(A_ij r_i), r_i = 448 / max_j |A_ij| (binary32),
+//          s_i = 1 / r_i, so A ~ diag(s) A8; one pass over A (a warp owns a
+//          row: the maximum first, then the conversion, which reads the row
+//          again from L2).  The same pass can write the bf16 pair Ah + Al that
+//          the split-bf16 projection B^T = A^T Q reads.
+//   transpose: A8^T for the transposed product (both tcgen05 operands of an
+//          e4m3 MMA are taken K-major).
+//   cols:  a thin operand X (K x N), optionally row-scaled in binary32 by s
+//          (X' = diag(s) X for A^T Q = A8^T (S Q)), converted per column and
+//          stored transposed: X8t = e4m3(X'^T diag(r)), c_j = 1 / r_j.
+// Conversion to e4m3 rounds to nearest (ties to even) and saturates at +-448.
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rsvd {
+
+namespace {
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ void split_store(__nv_bfloat16* Ah, __nv_bfloat16* Al, size_t idx, float a) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(a);
+  Ah[idx] = h;
+  Al[idx] = __float2bfloat16_rn(a - __bfloat162float(h));
+}
+
+}  // namespace
+
+// One warp per row (grid-stride).  vec: cols, lda multiples of 4 and A 16-byte
+// aligned, ld8 a multiple of 4, ldb a multiple of 4.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+    fp8_rows_kernel(int rows, int cols, const float* __restrict__ A, int lda, uint8_t* __restrict__ A8, int ld8,
+                    float* __restrict__ s, __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < rows; i += gridDim.x * wpb) {
+    const float* a = A + (size_t)i * lda;
+    float mx = 0.f;
+    if (VEC) {
+      for (int j = 4 * lane; j < cols; j += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(a + j);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+    } else {
+      for (int j = lane; j < cols; j += 32) mx = fmaxf(mx, fabsf(a[j]));
+    }
+    mx = warp_max(mx);
+    const float r = mx > 0.f ? 448.0f / mx : 1.0f;
+    if (lane == 0) s[i] = 1.0f / r;
+    uint8_t* q = A8 + (size_t)i * ld8;
+    if (VEC) {
+      for (int j = 4 * lane; j < cols; j += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(a + j);
+        const uint32_t packed = (uint32_t)to_e4m3(v.x * r) | ((uint32_t)to_e4m3(v.y * r) << 8) |
+                                ((uint32_t)to_e4m3(v.z * r) << 16) | ((uint32_t)to_e4m3(v.w * r) << 24);
+        *reinterpret_cast<uint32_t*>(q + j) = packed;
+        if (Ah) {
+          __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+          __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+          uint2 hv, lv;
+          hv.x = *reinterpret_cast<uint32_t*>(&h01);
+          hv.y = *reinterpret_cast<uint32_t*>(&h23);
+          lv.x = *reinterpret_cast<uint32_t*>(&l01);
+          lv.y = *reinterpret_cast<uint32_t*>(&l23);
+          *reinterpret_cast<uint2*>(Ah + (size_t)i * ldb + j) = hv;
+          *reinterpret_cast<uint2*>(Al + (size_t)i * ldb + j) = lv;
+        }
+      }
+    } else {
+      for (int j = lane; j < cols; j += 32) {
+        const float v = a[j];
+        q[j] = to_e4m3(v * r);
+        if (Ah) split_store(Ah, Al, (size_t)i * ldb + j, v);
+      }
+    }
+  }
+}
+
+void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, int ld8, float* s, __nv_bfloat16* Ah,
+                     __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return;
+  const bool vec = (cols % 4 == 0) && (lda % 4 == 0) && (ld8 % 4 == 0) && (((uintptr_t)A & 15) == 0) &&
+                   (((uintptr_t)A8 & 3) == 0) && (!Ah || (ldb % 4 == 0 && ((uintptr_t)Ah & 7) == 0 &&
+                                                         ((uintptr_t)Al & 7) == 0));
+  int blocks = ceil_div(rows, 8);
+  if (blocks > sms * 16) blocks = sms * 16;
+  if (vec)
+    fp8_rows_kernel<true><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb);
+  else
+    fp8_rows_kernel<false><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb);
+  note_launch();
+}
+
+// 64 x 64 byte tiles through shared memory.
+__global__ void __launch_bounds__(256)
+    u8_transpose_kernel(int rows, int cols, const uint8_t* __restrict__ A, int lda, uint8_t* __restrict__ B, int ldt) {
+  __shared__ uint8_t t[64][65];
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int r = e / 64, c = e % 64;
+    t[r][c] = (r0 + r < rows && c0 + c < cols) ? A[(size_t)(r0 + r) * lda + c0 + c] : (uint8_t)0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int c = e / 64, r = e % 64;  // output row c0 + c, column r0 + r
+    if (c0 + c < cols && r0 + r < rows) B[(size_t)(c0 + c) * ldt + r0 + r] = t[r][c];
+  }
+}
+
+void launch_u8_transpose(int rows, int cols, const uint8_t* A, int lda, uint8_t* B, int ldt, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return;
+  u8_transpose_kernel<<<dim3(ceil_div(cols, 64), ceil_div(rows, 64)), 256, 0, st>>>(rows, cols, A, lda, B, ldt);
+  note_launch();
+}
+
+constexpr int FC_ROWS = 1024;  // rows per partial column maximum
+
+// Partial column maxima of X' = diag(rsc) X over FC_ROWS-row blocks.
+__global__ void __launch_bounds__(256)
+    fp8_colmax_kernel(int rows, int cols, const float* __restrict__ X, int ldx, const float* __restrict__ rsc,
+                      float* __restrict__ part) {
+  const int i0 = blockIdx.x * FC_ROWS, i1 = min(rows, i0 + FC_ROWS);
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    float mx = 0.f;
+    for (int i = i0; i < i1; ++i) {
+      const float v = rsc ? X[(size_t)i * ldx + c] * rsc[i] : X[(size_t)i * ldx + c];
+      mx = fmaxf(mx, fabsf(v));
+    }
+    part[(size_t)blockIdx.x * cols + c] = mx;
+  }
+}
+
+// r_j = 448 / amax_j (1 for a zero column), c_j = 1 / r_j.
+__global__ void fp8_colscale_kernel(int nblk, int cols, const float* __restrict__ part, float* __restrict__ r,
+                                    float* __restrict__ c) {
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+    float mx = 0.f;
+    for (int b = 0; b < nblk; ++b) mx = fmaxf(mx, part[(size_t)b * cols + j]);
+    const float rr = mx > 0.f ? 448.0f / mx : 1.0f;
+    r[j] = rr;
+    c[j] = 1.0f / rr;
+  }
+}
+
+// X8t (cols x rows) = e4m3(X'^T diag(r)), 64 x 64 tiles through shared memory.
+__global__ void __launch_bounds__(256)
+    fp8_cols_convert_kernel(int rows, int cols, const float* __restrict__ X, int ldx, const float* __restrict__ rsc,
+                            const float* __restrict__ r, uint8_t* __restrict__ X8t, int ldt) {
+  __shared__ uint8_t t[64][65];
+  const int i0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int ii = e / 64, cc = e % 64;
+    const int i = i0 + ii, c = c0 + cc;
+    uint8_t q = 0;
+    if (i < rows && c < cols) {
+      const float v = rsc ? X[(size_t)i * ldx + c] * rsc[i] : X[(size_t)i * ldx + c];
+      q = to_e4m3(v * r[c]);
+    }
+    t[ii][cc] = q;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int cc = e / 64, ii = e % 64;
+    if (c0 + cc < cols && i0 + ii < rows) X8t[(size_t)(c0 + cc) * ldt + i0 + ii] = t[ii][cc];
+  }
+}
+
+size_t fp8_cols_workspace(int rows, int cols) {
+  Carver c(nullptr);
+  c.take<float>((size_t)ceil_div(rows > 0 ? rows : 1, FC_ROWS) * cols);
+  c.take<float>((size_t)cols);
+  return c.size();
+}
+
+void launch_fp8_cols(int rows, int cols, const float* X, int ldx, const float* rsc, uint8_t* X8t, int ldt, float* c,
+                     void* ws, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return;
+  Carver cv(ws);
+  const int nblk = ceil_div(rows, FC_ROWS);
+  float* part = cv.take<float>((size_t)nblk * cols);
+  float* r = cv.take<float>((size_t)cols);
+  fp8_colmax_kernel<<<nblk, 256, 0, st>>>(rows, cols, X, ldx, rsc, part);
+  fp8_colscale_kernel<<<1, 256, 0, st>>>(nblk, cols, part, r, c);
+  fp8_cols_convert_kernel<<<dim3(ceil_div(cols, 64), ceil_div(rows, 64)), 256, 0, st>>>(rows, cols, X, ldx, rsc, r,
+                                                                                         X8t, ldt);
+  note_launch(3);
+}
+
+}  // namespace rsvd

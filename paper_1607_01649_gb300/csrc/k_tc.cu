@@ -9,6 +9,11 @@
 // X is bf16 K x N row-major (MN-major operand), Y fp32.  N <= 256 is one MMA
 // tile wide (M = 128 rows per tile, K = 64 per pipeline stage, K = 16 per MMA).
 //
+//   e4m3 (NN only):  Y = diag(rs) (A8 X8t^T) diag(cs), A8 M x K and X8t N x K,
+//                    both e4m3 row-major (K-major operands), K = 128 bytes per
+//                    stage, K = 32 per MMA (kind::f8f6f4); the row and column
+//                    scales are applied in the epilogue.
+//
 // Persistent stream-K schedule: the T x KB (tile, k-block) units are cut into
 // G equal contiguous ranges, one per CTA (G <= #SMs), so every SM streams the
 // same number of bytes of A.  A tile whose k-blocks span two or more CTAs is
@@ -43,6 +48,8 @@ struct TcArgs {
   int ldy;
   float* part;   // [G][2][BM][Npad]
   DevStatus* st;
+  const float* rs;  // e4m3: per-row scale of Y (or null)
+  const float* cs;  // e4m3: per-column scale of Y
 };
 
 __host__ __device__ inline long long su0(long long c, long long W, int G) { return (c * W) / G; }
@@ -52,17 +59,18 @@ constexpr int TC_MAX_CTAS = 256;  // persistent grid cap (>= #SMs of the part)
 constexpr uint32_t A_TILE = 16384;   // 128 x 64 bf16
 constexpr uint32_t B_CHUNK = 8192;   // 64 x 64 bf16
 
-template <bool TRANS, bool SPLIT3, int SUB>
+template <bool TRANS, bool SPLIT3, int SUB, bool F8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                    const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX2, TcArgs g,
                    int stages) {
   static_assert(!SPLIT3 || SUB == 1, "the split-bf16 projection uses 128-row tiles");
+  static_assert(!F8 || (!TRANS && !SPLIT3), "e4m3 products take K-major operands only");
   constexpr int BM = 128 * SUB;       // rows per tile: SUB sub-tiles of 128 share each X tile
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   constexpr int NT = SPLIT3 ? 2 : 1;  // operand copies per stage
-  const uint32_t b_bytes = (uint32_t)g.nchunk * B_CHUNK;
+  const uint32_t b_bytes = F8 ? (uint32_t)g.Npad * 128u : (uint32_t)g.nchunk * B_CHUNK;
   const uint32_t stage_bytes = NT * (SUB * A_TILE + b_bytes);
   __shared__ uint64_t full[8], empty[8], tfull[2], tempty[2];
   __shared__ uint32_t tslot;
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         unsigned char* sA = sm + (size_t)s * stage_bytes;
         unsigned char* sB = sA + NT * SUB * A_TILE;
         mbar_arrive_expect_tx(&full[s], stage_bytes);
-        const int k0 = kb * 64;
+        const int k0 = kb * (F8 ? 128 : 64);
 #pragma unroll
         for (int sb = 0; sb < SUB; ++sb) {
           unsigned char* sAs = sA + sb * A_TILE;
@@ -138,15 +146,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           }
         }
-        for (int ch = 0; ch < g.nchunk; ++ch) {
-          tma_load_2d(sB + ch * B_CHUNK, &tmX, 64 * ch, k0, &full[s]);
-          if (SPLIT3) tma_load_2d(sB + b_bytes + ch * B_CHUNK, &tmX2, 64 * ch, k0, &full[s]);
+        if (F8) {
+          tma_load_2d(sB, &tmX, k0, 0, &full[s]);  // Npad rows x 128 bytes of K
+        } else {
+          for (int ch = 0; ch < g.nchunk; ++ch) {
+            tma_load_2d(sB + ch * B_CHUNK, &tmX, 64 * ch, k0, &full[s]);
+            if (SPLIT3) tma_load_2d(sB + b_bytes + ch * B_CHUNK, &tmX2, 64 * ch, k0, &full[s]);
+          }
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
-    const uint32_t idesc = idesc_bf16(128, g.Npad, TRANS ? 1 : 0, 1);
+    const uint32_t idesc = F8 ? idesc_e4m3(128, g.Npad) : idesc_bf16(128, g.Npad, TRANS ? 1 : 0, 1);
     int it = 0, j = 0;
     bool ok = true;
     for (int t = t_first; t <= t_last && ok; ++t, ++j) {
@@ -172,13 +184,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t aB = aA + NT * SUB * A_TILE;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const uint64_t bd = umma_desc(aB + 2048 * k, 8192, 1024);
+          // bf16: 16 K-elements (32 bytes) per MMA; e4m3: 32 K-elements (32 bytes)
+          const uint64_t bd = F8 ? umma_desc(aB + 32 * k, 16, 1024) : umma_desc(aB + 2048 * k, 8192, 1024);
           const uint32_t accum = (kb > kb_lo || k > 0) ? 1u : 0u;
 #pragma unroll
           for (int sb = 0; sb < SUB; ++sb) {
             const uint32_t aAs = aA + sb * A_TILE;
             const uint64_t ad = TRANS ? umma_desc(aAs + 2048 * k, 8192, 1024) : umma_desc(aAs + 32 * k, 16, 1024);
-            mma_bf16(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
+            if (F8)
+              mma_e4m3(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
+            else
+              mma_bf16(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
             if (SPLIT3) {
               const uint64_t ad2 = umma_desc(aAs + A_TILE + 2048 * k, 8192, 1024);
               const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
@@ -226,10 +242,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         dst = g.part + (((size_t)c * 2 + slot) * BM + 128 * sb + r) * g.Npad;
       }
       const uint32_t taddr = tbase + (uint32_t)((acc * SUB + sb) * g.NA) + ((uint32_t)(32 * q) << 16);
+      const float rsc = (F8 && g.rs && row < g.M) ? g.rs[row] : 1.0f;
       for (int c16 = 0; c16 < g.Npad; c16 += 16) {
         uint32_t v[16];
         tmem_ld16(taddr + c16, v);
         tmem_wait_ld();
+        if (F8) {
+          // scales are linear, so partial tiles can be scaled before the fix-up adds them
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float cv = (c16 + e < g.N) ? g.cs[c16 + e] : 0.0f;
+            v[e] = __float_as_uint(__uint_as_float(v[e]) * rsc * cv);
+          }
+        }
         if (store) {
           if (whole) {
 #pragma unroll
@@ -382,6 +407,8 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   g.ldy = ldy;
   g.part = part;
   g.st = st;
+  g.rs = nullptr;
+  g.cs = nullptr;
   CUtensorMap mA, mA2, mX, mX2;
   bool ok = true;
   if (!trans)
@@ -421,6 +448,82 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   else
     RSVD_TC_LAUNCH(true, false, 2);
 #undef RSVD_TC_LAUNCH
+  note_launch();
+  tc_fixup_kernel<<<dim3(g.T, bm / FIX_ROWS), 256, 0, s>>>(g, bm);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// e4m3 matrix (rows x cols bytes, ld bytes) as a 2-D map with a
+// (box_in x box_out) box and 128-byte swizzle.
+static bool make_map_u8(CUtensorMap* m, const void* ptr, int cols, int rows, int ld, int box_in, int box_out) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld};
+  cuuint32_t box[2] = {(cuuint32_t)box_in, (cuuint32_t)box_out};
+  cuuint32_t es[2] = {1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t tc_gemm_e4m3_workspace(int M, int N, int K, int sms) {
+  const int KB = ceil_div(K, 128), T = ceil_div(M, 128);
+  const long long W = (long long)T * KB;
+  int G = (int)(W < sms ? W : sms);
+  if (G > TC_MAX_CTAS) G = TC_MAX_CTAS;
+  const int Npad = ceil_div(N, 16) * 16;
+  return (size_t)G * 2 * 256 * Npad * sizeof(float);
+}
+
+cudaError_t launch_tc_gemm_e4m3(int M, int N, int K, const uint8_t* A8, int lda, const uint8_t* X8t, int ldx,
+                                const float* rs, const float* cs, float* Y, int ldy, float* part, int sms,
+                                DevStatus* st, cudaStream_t s) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  if (!get_encode()) return cudaErrorNotSupported;
+  if ((lda % 16) || (ldx % 16) || (((uintptr_t)A8 | (uintptr_t)X8t) & 15) || !cs || N > 256)
+    return cudaErrorInvalidValue;
+  const int bm = tc_rows_per_tile(M, false);
+  const int SUBT = bm / 128;
+  TcArgs g;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.KB = ceil_div(K, 128);
+  g.T = ceil_div(M, bm);
+  g.W = (long long)g.T * g.KB;
+  g.G = (int)(g.W < sms ? g.W : sms);
+  if (g.G > TC_MAX_CTAS) g.G = TC_MAX_CTAS;
+  g.Npad = ceil_div(N, 16) * 16;
+  g.NA = pow2_at_least(g.Npad);
+  g.nchunk = 1;
+  g.nbuf = (2 * SUBT * g.NA <= 512) ? 2 : 1;
+  g.Y = Y;
+  g.ldy = ldy;
+  g.part = part;
+  g.st = st;
+  g.rs = rs;
+  g.cs = cs;
+  CUtensorMap mA, mX;
+  bool ok = make_map_u8(&mA, A8, K, M, lda, 128, 128);   // A8: M x K bytes
+  ok &= make_map_u8(&mX, X8t, K, N, ldx, 128, g.Npad);     // X8t: N x K bytes
+  if (!ok) return cudaErrorInvalidValue;
+  const size_t stage_bytes = (size_t)SUBT * A_TILE + (size_t)g.Npad * 128;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return cudaErrorInvalidValue;
+  const size_t smem = stages * stage_bytes + 1024;
+  cudaError_t e;
+  if (SUBT == 1) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<false, false, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<false, false, 1, true><<<g.G, TC_THREADS, smem, s>>>(mA, mA, mX, mX, g, stages);
+  } else {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<false, false, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<false, false, 2, true><<<g.G, TC_THREADS, smem, s>>>(mA, mA, mX, mX, g, stages);
+  }
   note_launch();
   tc_fixup_kernel<<<dim3(g.T, bm / FIX_ROWS), 256, 0, s>>>(g, bm);
   note_launch();

@@ -56,6 +56,25 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
                            int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm = 0);
 void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb,
                        int sms, cudaStream_t s);
+// Y (M x N fp32) = diag(rs) (A8 X8t^T) diag(cs): A8 M x K, X8t N x K, e4m3
+// bytes row-major (ld in bytes, multiples of 16); rs may be null.
+size_t tc_gemm_e4m3_workspace(int M, int N, int K, int sms);
+cudaError_t launch_tc_gemm_e4m3(int M, int N, int K, const uint8_t* A8, int lda, const uint8_t* X8t, int ldx,
+                                const float* rs, const float* cs, float* Y, int ldy, float* part, int sms,
+                                DevStatus* st, cudaStream_t s);
+
+// k_fp8.cu
+// Rows of A (fp32) scaled to e4m3: A8 (rows x cols, ld8 bytes), s[i] = max_j |A_ij| / 448;
+// optionally the bf16 pair Ah + Al of A (ldb elements).
+void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, int ld8, float* s,
+                     __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st);
+// B (cols x rows bytes, ldt) = A^T for e4m3 bytes A (rows x cols, lda).
+void launch_u8_transpose(int rows, int cols, const uint8_t* A, int lda, uint8_t* B, int ldt, cudaStream_t st);
+// X (rows x cols fp32, ldx), optionally with row scales rsc: X' = diag(rsc) X in binary32;
+// X8t (cols x rows e4m3 bytes, ldt) = e4m3(X'^T diag(448 / amax_j)), c[j] = amax_j / 448 (column amax of X').
+size_t fp8_cols_workspace(int rows, int cols);
+void launch_fp8_cols(int rows, int cols, const float* X, int ldx, const float* rsc, uint8_t* X8t, int ldt, float* c,
+                     void* ws, cudaStream_t st);
 
 // k_adapt.cu
 size_t adapt_workspace_bytes(int m, int n, int R, int b, int sms, size_t es);

@@ -98,7 +98,7 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   if (!p) return fail(h, RSVD_E_INVALID, "params is NULL");
   if (m < 0 || n < 0) return fail(h, RSVD_E_INVALID, "negative size m=%d n=%d", m, n);
   if (p->k < 0 || p->p < 0 || p->q < 0) return fail(h, RSVD_E_INVALID, "k, p, q must be >= 0");
-  if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16)
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16 && p->prec != RSVD_MIXED_FP8)
     return fail(h, RSVD_E_UNSUPPORTED, "precision %d is not implemented", p->prec);
   const int l = p->k + p->p;
   const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
@@ -303,6 +303,127 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
   launch_sign_fix<float, float>(n, kk, l, V, ldv, L.Wsel, L.part, s);
   launch_gemm_simt<float>(false, m, kk, l, L.Y, l, L.Wsel, kk, U, ldu, nullptr, sms, s);
   return check_launch(h, "rsvd_fixed_rank (mixed)");
+}
+
+inline int round16(int v) { return (v + 15) / 16 * 16; }
+
+// e4m3 path: the mixed layout plus the 8-bit copies of A and of the thin operand.
+struct Fp8Extra {
+  uint8_t* A8;    // m x n16
+  uint8_t* A8T;   // n x m16
+  float* s;       // m row scales
+  float* Om;      // n x l fp32
+  uint8_t* X8t;   // l x max(m16, n16)
+  float* cvec;    // l column scales
+  void* colws;    // fp8_cols scratch
+  float* part8;   // e4m3 product partials
+  size_t bytes;
+};
+
+Fp8Extra fp8_extra(void* ws, int m, int n, int l, int sms) {
+  Carver c(ws);
+  Fp8Extra E;
+  E.A8 = c.take<uint8_t>((size_t)m * round16(n));
+  E.A8T = c.take<uint8_t>((size_t)n * round16(m));
+  E.s = c.take<float>((size_t)m);
+  E.Om = c.take<float>((size_t)n * l);
+  const int kmax = round16(m > n ? m : n);
+  E.X8t = c.take<uint8_t>((size_t)l * kmax);
+  E.cvec = c.take<float>((size_t)l);
+  size_t cw = fp8_cols_workspace(m, l);
+  if (fp8_cols_workspace(n, l) > cw) cw = fp8_cols_workspace(n, l);
+  E.colws = c.take<unsigned char>(cw);
+  size_t pw = tc_gemm_e4m3_workspace(m, l, n, sms);
+  if (tc_gemm_e4m3_workspace(n, l, m, sms) > pw) pw = tc_gemm_e4m3_workspace(n, l, m, sms);
+  E.part8 = c.take<float>(pw / sizeof(float) + 1);
+  E.bytes = c.size();
+  return E;
+}
+
+// Workspace of the e4m3 stage call rsvd_sketch(prec = RSVD_MIXED_FP8).
+struct SketchFp8 {
+  DevStatus* st;
+  uint8_t *A8, *A8T, *X8t;
+  float *s, *c, *part;
+  void* colws;
+  size_t bytes;
+};
+
+SketchFp8 sketch_fp8_layout(void* ws, int trans, int m, int n, int l, int sms) {
+  Carver c(ws);
+  SketchFp8 F;
+  F.st = c.take<DevStatus>(1);
+  F.A8 = c.take<uint8_t>((size_t)m * round16(n));
+  F.A8T = trans ? c.take<uint8_t>((size_t)n * round16(m)) : nullptr;
+  F.s = c.take<float>((size_t)m);
+  const int K = trans ? m : n, M = trans ? n : m;
+  F.X8t = c.take<uint8_t>((size_t)l * round16(K));
+  F.c = c.take<float>((size_t)l);
+  F.colws = c.take<unsigned char>(fp8_cols_workspace(K, l));
+  F.part = c.take<float>(tc_gemm_e4m3_workspace(M, l, K, sms) / sizeof(float) + 1);
+  F.bytes = c.size();
+  return F;
+}
+
+// e4m3 sketches (A G, A^T Q, A W) with per-row scales of A and per-column
+// scales of the thin operand, then the same split-bf16 projection, small SVD
+// and lift as the bf16 path.
+rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int lda, const rsvd_params* p, float* U,
+                           int ldu, double* D, float* V, int ldv, const MixedLayout& L, const Fp8Extra& E,
+                           cudaStream_t s) {
+  const int l = p->k + p->p;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
+  const int sms = h->sms;
+  const int n8 = round8(n), l8 = round8(l), n16 = round16(n), m16 = round16(m);
+  rsvd_status st;
+  // one pass over A: A8 with row scales, and the bf16 pair for the projection
+  launch_fp8_rows(m, n, A, lda, E.A8, n16, E.s, L.Ah, L.Al, n8, sms, s);
+  launch_u8_transpose(m, n, E.A8, n16, E.A8T, m16, s);
+  // G = randn(n, l); Y = A G
+  launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_F32, E.Om, l, s);
+  launch_fp8_cols(n, l, E.Om, l, nullptr, E.X8t, n16, E.cvec, E.colws, s);
+  {
+    ProfScope ps(h, 0, s);
+    if ((st = tc_call(h, launch_tc_gemm_e4m3(m, l, n, E.A8, n16, E.X8t, n16, E.s, E.cvec, L.Y, l, E.part8, sms, L.st,
+                                             s), "e4m3 sketch A G")) != RSVD_OK)
+      return st;
+  }
+  run_orth<float, float>(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  for (int j = 0; j < p->q; ++j) {
+    // Z = A^T Q = A8^T (S Q)
+    launch_fp8_cols(m, l, L.Y, l, E.s, E.X8t, m16, E.cvec, E.colws, s);
+    {
+      ProfScope ps(h, 0, s);
+      if ((st = tc_call(h, launch_tc_gemm_e4m3(n, l, m, E.A8T, m16, E.X8t, m16, nullptr, E.cvec, L.Z, l, E.part8, sms,
+                                               L.st, s), "e4m3 sketch A^T Q")) != RSVD_OK)
+        return st;
+    }
+    run_orth<float, float>(n, l, L.Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    launch_fp8_cols(n, l, L.Z, l, nullptr, E.X8t, n16, E.cvec, E.colws, s);
+    {
+      ProfScope ps(h, 0, s);
+      if ((st = tc_call(h, launch_tc_gemm_e4m3(m, l, n, E.A8, n16, E.X8t, n16, E.s, E.cvec, L.Y, l, E.part8, sms,
+                                               L.st, s), "e4m3 sketch A W")) != RSVD_OK)
+        return st;
+    }
+    run_orth<float, float>(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  }
+  // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
+  launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);
+  {
+    ProfScope ps(h, 1, s);
+    if ((st = tc_call(h, launch_tc_gemm(true, true, n, l, m, L.Ah, n8, L.Al, L.Yb, l8, L.Yl, L.Z, l, L.part, sms,
+                                        L.st, s), "projection")) != RSVD_OK)
+      return st;
+  }
+  run_orth<float, float>(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<float>(l, kk, L.sigma, L.Wt, L.Jt, D, L.Wsel, L.Jsel, s);
+  launch_gemm_simt<float>(false, n, kk, l, L.Z, l, L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_sign_fix<float, float>(n, kk, l, V, ldv, L.Wsel, L.part, s);
+  launch_gemm_simt<float>(false, m, kk, l, L.Y, l, L.Wsel, kk, U, ldu, nullptr, sms, s);
+  return check_launch(h, "rsvd_fixed_rank (e4m3)");
 }
 
 // ---------------------------------------------------------- adaptive path --
@@ -743,6 +864,8 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
   const int l = params->k + params->p;
   if (params->prec == RSVD_MIXED_BF16)
     *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes;
+  else if (params->prec == RSVD_MIXED_FP8)
+    *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes + fp8_extra(nullptr, m, n, l, handle->sms).bytes;
   else
     *bytes = fixed_layout(nullptr, m, n, l, kk, params->prec, handle->sms).bytes;
   return RSVD_OK;
@@ -768,6 +891,15 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
     const MixedLayout M = mixed_layout(workspace, m, n, l, kk, handle->sms);
     cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
     st = fixed_rank_mixed(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, s);
+    if (st != RSVD_OK) return st;
+    return finish_sync(handle, params, M.st, s);
+  }
+  if (params->prec == RSVD_MIXED_FP8) {
+    if (((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
+    const MixedLayout M = mixed_layout(workspace, m, n, l, kk, handle->sms);
+    const Fp8Extra E = fp8_extra((char*)workspace + M.bytes, m, n, l, handle->sms);
+    cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
+    st = fixed_rank_fp8(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, E, s);
     if (st != RSVD_OK) return st;
     return finish_sync(handle, params, M.st, s);
   }
@@ -908,6 +1040,8 @@ rsvd_status rsvd_sketch_workspace_size(rsvd_handle_t handle, int prec, int trans
     *bytes = simt_gemm_workspace(M, l, K, handle->sms, elem_size(prec)) + 512;
   else if (prec == RSVD_MIXED_BF16)
     *bytes = tc_gemm_workspace(M, l, K, handle->sms) + 512;
+  else if (prec == RSVD_MIXED_FP8)
+    *bytes = sketch_fp8_layout(nullptr, trans, m, n, l, handle->sms).bytes;
   else
     return fail(handle, RSVD_E_UNSUPPORTED, "precision %d is not built yet", prec);
   return RSVD_OK;
@@ -928,6 +1062,25 @@ rsvd_status rsvd_sketch(rsvd_handle_t handle, int prec, int trans, int m, int n,
   if (need > 512 && (!workspace || ws_bytes < need))
     return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == RSVD_MIXED_FP8) {
+    if (l > 256) return fail(handle, RSVD_E_UNSUPPORTED, "l = %d > 256", l);
+    const SketchFp8 F = sketch_fp8_layout(workspace, trans, m, n, l, handle->sms);
+    cudaMemsetAsync(F.st, 0, sizeof(DevStatus), s);
+    launch_fp8_rows(m, n, (const float*)A, lda, F.A8, round16(n), F.s, nullptr, nullptr, 0, handle->sms, s);
+    cudaError_t e;
+    if (!trans) {
+      launch_fp8_cols(n, l, (const float*)X, ldx, nullptr, F.X8t, round16(n), F.c, F.colws, s);
+      e = launch_tc_gemm_e4m3(m, l, n, F.A8, round16(n), F.X8t, round16(n), F.s, F.c, (float*)Y, ldy, F.part,
+                              handle->sms, F.st, s);
+    } else {
+      launch_u8_transpose(m, n, F.A8, round16(n), F.A8T, round16(m), s);
+      launch_fp8_cols(m, l, (const float*)X, ldx, F.s, F.X8t, round16(m), F.c, F.colws, s);
+      e = launch_tc_gemm_e4m3(n, l, m, F.A8T, round16(m), F.X8t, round16(m), nullptr, F.c, (float*)Y, ldy, F.part,
+                              handle->sms, F.st, s);
+    }
+    if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_sketch (e4m3): %s", cudaGetErrorString(e));
+    return check_launch(handle, "rsvd_sketch (e4m3)");
+  }
   if (prec == RSVD_MIXED_BF16) {
     if (l > 256) return fail(handle, RSVD_E_UNSUPPORTED, "l = %d > 256", l);
     if ((lda % 8) || (ldx % 8) || (((uintptr_t)A | (uintptr_t)X) & 15))

@@ -1,7 +1,7 @@
 // Blackwell (sm_100 family, built for sm_103a) primitives as inline PTX:
 // mbarriers, TMA tensor loads, tcgen05 tensor-memory allocation, UMMA
-// descriptors, tcgen05.mma (kind::f16, bf16 inputs, fp32 accumulation) and
-// tcgen05.ld.  Every wait is bounded: it gives up after a fixed number of
+// descriptors, tcgen05.mma (kind::f16 with bf16 inputs, kind::f8f6f4 with e4m3
+// inputs; fp32 accumulation) and tcgen05.ld.  Every wait is bounded: it gives up after a fixed number of
 // polls and reports the timeout to the caller.
 #pragma once
 
@@ -111,6 +111,22 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f8f6f4: fp32 accumulator, e4m3 A and B
+// (format code 0), both operands K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,

@@ -107,19 +107,31 @@ void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, i
   note_launch();
 }
 
-// 64 x 64 byte tiles through shared memory.
+// 64 x 64 byte tiles through shared memory, 16-byte loads and stores (lda and
+// ldt are multiples of 16: the padding columns of a row may be read, and
+// bytes past `rows` in an output row land in its padding).
 __global__ void __launch_bounds__(256)
     u8_transpose_kernel(int rows, int cols, const uint8_t* __restrict__ A, int lda, uint8_t* __restrict__ B, int ldt) {
-  __shared__ uint8_t t[64][65];
+  __shared__ __align__(16) uint8_t t[64][64 + 16];
   const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int r = e / 64, c = e % 64;
-    t[r][c] = (r0 + r < rows && c0 + c < cols) ? A[(size_t)(r0 + r) * lda + c0 + c] : (uint8_t)0;
+  {
+    const int r = threadIdx.x >> 2, v = threadIdx.x & 3;  // row r, bytes 16 v .. 16 v + 15
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    if (r0 + r < rows && c0 + 16 * v < lda)
+      x = *reinterpret_cast<const uint4*>(A + (size_t)(r0 + r) * lda + c0 + 16 * v);
+    *reinterpret_cast<uint4*>(&t[r][16 * v]) = x;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int c = e / 64, r = e % 64;  // output row c0 + c, column r0 + r
-    if (c0 + c < cols && r0 + r < rows) B[(size_t)(c0 + c) * ldt + r0 + r] = t[r][c];
+  {
+    const int c = threadIdx.x >> 2, v = threadIdx.x & 3;  // output row c0 + c, bytes 16 v ..
+    if (c0 + c < cols && r0 + 16 * v < ldt) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        w[q] = (uint32_t)t[16 * v + 4 * q][c] | ((uint32_t)t[16 * v + 4 * q + 1][c] << 8) |
+               ((uint32_t)t[16 * v + 4 * q + 2][c] << 16) | ((uint32_t)t[16 * v + 4 * q + 3][c] << 24);
+      *reinterpret_cast<uint4*>(B + (size_t)(c0 + c) * ldt + r0 + 16 * v) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
 
@@ -158,11 +170,13 @@ __global__ void fp8_colscale_kernel(int nblk, int cols, const float* __restrict_
   }
 }
 
-// X8t (cols x rows) = e4m3(X'^T diag(r)), 64 x 64 tiles through shared memory.
+// X8t (cols x rows) = e4m3(X'^T diag(r)), 64 x 64 tiles through shared memory;
+// output rows are written as 16-byte vectors (ldt is a multiple of 16, so
+// bytes past `rows` land in the row's padding).
 __global__ void __launch_bounds__(256)
     fp8_cols_convert_kernel(int rows, int cols, const float* __restrict__ X, int ldx, const float* __restrict__ rsc,
                             const float* __restrict__ r, uint8_t* __restrict__ X8t, int ldt) {
-  __shared__ uint8_t t[64][65];
+  __shared__ __align__(16) uint8_t t[64][64 + 16];
   const int i0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
   for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
     const int ii = e / 64, cc = e % 64;
@@ -175,9 +189,14 @@ __global__ void __launch_bounds__(256)
     t[ii][cc] = q;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int cc = e / 64, ii = e % 64;
-    if (c0 + cc < cols && i0 + ii < rows) X8t[(size_t)(c0 + cc) * ldt + i0 + ii] = t[ii][cc];
+  const int cc = threadIdx.x >> 2, v = threadIdx.x & 3;
+  if (c0 + cc < cols && i0 + 16 * v < ldt) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      w[q] = (uint32_t)t[16 * v + 4 * q][cc] | ((uint32_t)t[16 * v + 4 * q + 1][cc] << 8) |
+             ((uint32_t)t[16 * v + 4 * q + 2][cc] << 16) | ((uint32_t)t[16 * v + 4 * q + 3][cc] << 24);
+    *reinterpret_cast<uint4*>(X8t + (size_t)(c0 + cc) * ldt + i0 + 16 * v) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 

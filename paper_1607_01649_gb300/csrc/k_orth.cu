@@ -439,7 +439,7 @@ template <typename C, int NT>
 __global__ void __launch_bounds__(NT)
     chol_kernel(int l, const double* __restrict__ G, const float* __restrict__ Gf, C* __restrict__ Ub,
                 C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate,
-                const int* skip) {
+                const int* skip, int inverse) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = (l + CBK - 1) / CBK;
@@ -589,29 +589,78 @@ __global__ void __launch_bounds__(NT)
       st->shifted = 1;
     if (shift > C(0)) atomicAdd(&st->shift_count, 1);
   }
-  // outputs: Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a
-  // diagonal block (i <= j), 0 below;  R(i, j) = L(j, i) d_j for i <= j
-  for (int i = warp; i < l; i += nw) {
-    const int bi = i >> 5, ii = i & 31;
+  // R(i, j) = L(j, i) d_j for i <= j
+  if (R) {
+    for (int i = warp; i < l; i += nw) {
+      const int bi = i >> 5, ii = i & 31;
+      for (int j = lane; j < l; j += 32) {
+        const int bj = j >> 5, jj = j & 31;
+        R[(size_t)i * l + j] = (i <= j) ? (double)Ls[(size_t)lblk(bj, bi) * CBS + jj * CP + ii] * d[j] : 0.0;
+      }
+    }
+  }
+  if (!inverse) {
+    // Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a diagonal
+    // block (i <= j), 0 below
+    for (int i = warp; i < l; i += nw) {
+      const int bi = i >> 5, ii = i & 31;
+      for (int j = lane; j < l; j += 32) {
+        const int bj = j >> 5, jj = j & 31;
+        C v = C(0);
+        if (i <= j) v = (bi == bj) ? Xs[(size_t)bj * CBS + jj * CP + ii] : Ls[(size_t)lblk(bj, bi) * CBS + jj * CP + ii];
+        Ub[(size_t)i * l + j] = v;
+      }
+    }
+    for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
+    return;
+  }
+  // Explicit inverse.  W = L^-1 in place of the off-diagonal blocks, block
+  // column j from the last to the first (the trailing part already holds its
+  // inverse): T_i = sum_{k = j + 1}^{i} W_ik L_kj (i > j), W_ij = -T_i X_jj.
+  C* Ts = rdg + CBK * NB;  // NB - 1 scratch blocks
+  for (int j = NB - 2; j >= 0; --j) {
+    const int nrow = (NB - 1 - j) * CBK;
+    for (int rr = warp; rr < nrow; rr += nw) {
+      const int i = j + 1 + rr / CBK, r = rr % CBK;
+      C acc = C(0);
+      for (int k = j + 1; k <= i; ++k) {
+        const C* Wr = (k == i) ? Xs + (size_t)i * CBS + r * CP : Ls + (size_t)lblk(i, k) * CBS + r * CP;
+        const C* Lc = Ls + (size_t)lblk(k, j) * CBS + lane;
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) acc = fma(Wr[t], Lc[t * CP], acc);
+      }
+      Ts[(size_t)(i - j - 1) * CBS + r * CP + lane] = acc;
+    }
+    __syncthreads();
+    for (int rr = warp; rr < nrow; rr += nw) {
+      const int i = j + 1 + rr / CBK, r = rr % CBK;
+      const C* Tr = Ts + (size_t)(i - j - 1) * CBS + r * CP;
+      const C* Xc = Xs + (size_t)j * CBS + lane;  // X_jj(t, lane), zero for t < lane
+      C acc = C(0);
+#pragma unroll 8
+      for (int t = 0; t < 32; ++t) acc = fma(Tr[t], Xc[t * CP], acc);
+      Ls[(size_t)lblk(i, j) * CBS + r * CP + lane] = -acc;
+    }
+    __syncthreads();
+  }
+  // M = R^-1 = D^-1 W^T: M(k, j) = W(j, k) / d_k for j >= k, 0 below
+  for (int k = warp; k < l; k += nw) {
+    const int bk = k >> 5, kk = k & 31;
     for (int j = lane; j < l; j += 32) {
       const int bj = j >> 5, jj = j & 31;
       C v = C(0);
-      double rv = 0.0;
-      if (i <= j) {
-        const C lji = Ls[(size_t)lblk(bj, bi) * CBS + jj * CP + ii];
-        v = (bi == bj) ? Xs[(size_t)bj * CBS + jj * CP + ii] : lji;
-        rv = (double)lji * d[j];
+      if (j >= k) {
+        const C* blkp = (bj == bk) ? Xs + (size_t)bj * CBS : Ls + (size_t)lblk(bj, bk) * CBS;
+        v = blkp[jj * CP + kk] * rdc[k];
       }
-      Ub[(size_t)i * l + j] = v;
-      if (R) R[(size_t)i * l + j] = rv;
+      Ub[(size_t)k * l + j] = v;
     }
   }
-  for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
 }
 
 size_t chol_smem_bytes(int l, size_t csize) {
   const int NB = (l + CBK - 1) / CBK;
-  const size_t blocks = (size_t)NB * (NB + 1) / 2 + NB;
+  const size_t blocks = (size_t)NB * (NB + 1) / 2 + NB + (NB > 1 ? NB - 1 : 0);  // L, X, inverse scratch
   return blocks * CBS * csize + (size_t)l * sizeof(double) + (size_t)l * csize + (size_t)CBK * NB * csize;
 }
 
@@ -772,14 +821,14 @@ void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __
 
 template <typename C>
 void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
-                 const int* gate, cudaStream_t s, const int* skip) {
+                 const int* gate, cudaStream_t s, const int* skip, int inverse = 0) {
   // binary32: 512 threads (128 registers each: the diagonal-block warp keeps a
   // row of L and a row of its inverse in registers); binary64 (l <= 128): 256
   constexpr int NT = sizeof(C) == 4 ? 512 : 256;
   const size_t smem = chol_smem_bytes(l, sizeof(C));
   auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip);
+  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip, inverse);
   note_launch();
 }
 
@@ -842,6 +891,68 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
     // R = R3 R2 R1 (R3 only if the third pass ran)
     launch_triu_mm(l, Rp + (size_t)l * l, Rp, Rm, nullptr, 0, s, skip);
     launch_triu_mm(l, Rp + (size_t)2 * l * l, Rm, Rout, gate3, 1, s, skip);
+  }
+}
+
+// CholeskyQR2 (+ shifted third pass) for the mixed-precision paths with the
+// apply on tensor cores for tall blocks: Q = Y M, M = R^-1 from the Cholesky
+// kernel, as the three-term split-bf16 product Yh Mh + Yh Ml + Yl Mh (relative
+// error about 2^-16 instead of binary32's 2^-24; the Gram stays binary32
+// products with binary64 sums).  Shorter blocks take the SIMT solve.
+size_t orth_tc_workspace_bytes(int rows, int l, int sms) {
+  const int l8 = (l + 7) / 8 * 8;
+  Carver c(nullptr);
+  c.take<unsigned char>(orth_workspace_bytes(rows, l, sms, 4));
+  c.take<__nv_bfloat16>((size_t)2 * rows * l8);  // Yh, Yl
+  c.take<__nv_bfloat16>((size_t)2 * l * l8);     // Mh, Ml
+  c.take<unsigned char>(tc_gemm_workspace(rows, l, l, sms));
+  return c.size();
+}
+
+// The tensor-core apply pays for an explicit triangular inverse (on one SM)
+// and the bf16 splits; it wins once the block is tall: measured on GB300,
+// 2^20 x 128 (4.6x faster apply) but not 32768 x 256.
+bool orth_tc_pays(int rows, int l) { return (long long)rows >= 256LL * l; }
+
+void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
+                 DevStatus* st, int sms, cudaStream_t s) {
+  if (!orth_tc_pays(rows, l)) {
+    run_orth<float, float>(rows, l, Y, ldy, Rout, Ybf, lb, ws, st, sms, s);
+    return;
+  }
+  const int l8 = (l + 7) / 8 * 8;
+  Carver c0(ws);
+  void* base = c0.take<unsigned char>(orth_workspace_bytes(rows, l, sms, 4));
+  __nv_bfloat16* Yh = c0.take<__nv_bfloat16>((size_t)rows * l8);
+  __nv_bfloat16* Yl = c0.take<__nv_bfloat16>((size_t)rows * l8);
+  __nv_bfloat16* Mh = c0.take<__nv_bfloat16>((size_t)l * l8);
+  __nv_bfloat16* Ml = c0.take<__nv_bfloat16>((size_t)l * l8);
+  float* part = c0.take<float>(tc_gemm_workspace(rows, l, l, sms) / sizeof(float) + 1);
+  Carver c(base);
+  double* P = c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
+  double* G = c.take<double>((size_t)l * l);
+  float* Gf = c.take<float>((size_t)l * l);
+  float* M = c.take<float>((size_t)l * l);
+  float* dinv = c.take<float>((size_t)l);
+  double* Rp = c.take<double>((size_t)3 * l * l);
+  double* Rm = c.take<double>((size_t)2 * l * l);
+  const int* gate3 = &st->shifted;
+  for (int pass = 1; pass <= 3; ++pass) {
+    const int* gate = pass == 3 ? gate3 : nullptr;
+    launch_gram<float>(rows, l, Y, ldy, P, G, Gf, sms, gate, s, nullptr);
+    launch_chol<float>(l, G, Gf, M, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s,
+                       nullptr, 1);
+    // pass 3 runs only if pass 1 needed a shift (a device-side gate): the
+    // product then returns at once and leaves Y alone (the splits only fill
+    // scratch)
+    launch_split_bf16(rows, l, Y, ldy, Yh, Yl, l8, sms, s);
+    launch_split_bf16(l, l, M, l, Mh, Ml, l8, sms, s);
+    launch_tc_gemm(false, true, rows, l, l, Yh, l8, Yl, Mh, l8, Ml, Y, ldy, part, sms, st, s, 128, gate);
+  }
+  if (Ybf) launch_copy_bf16<float>(rows, l, Y, ldy, Ybf, lb, s);
+  if (Rout) {
+    launch_triu_mm(l, Rp + (size_t)l * l, Rp, Rm, nullptr, 0, s, nullptr);
+    launch_triu_mm(l, Rp + (size_t)2 * l * l, Rm, Rout, gate3, 1, s, nullptr);
   }
 }
 

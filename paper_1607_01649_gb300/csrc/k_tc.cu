@@ -3,8 +3,9 @@
 //
 //   NN:  Y[M x N] = A[M x K] X[K x N]      A bf16 row-major (K-major operand)
 //   TN:  Y[M x N] = A^T[M x K] X[K x N]    A bf16 K x M row-major (MN-major operand)
-//   split3 (TN only):  Y = Ah^T Xh + Ah^T Xl + Al^T Xh, the three-term split-bf16
-//                      product for B^T = A^T Q with A = Ah + Al, Q = Xh + Xl.
+//   split3:  Y = Ah^T Xh + Ah^T Xl + Al^T Xh (TN; B^T = A^T Q with A = Ah + Al,
+//            Q = Xh + Xl) or Yh Mh + Yh Ml + Yl Mh (NN; the orthonormalization's
+//            Q = Y R^-1), the three-term split-bf16 products.
 //
 // X is bf16 K x N row-major (MN-major operand), Y fp32.  N <= 256 is one MMA
 // tile wide (M = 128 rows per tile, K = 64 per pipeline stage, K = 16 per MMA).
@@ -50,6 +51,7 @@ struct TcArgs {
   DevStatus* st;
   const float* rs;  // e4m3: per-row scale of Y (or null)
   const float* cs;  // e4m3: per-column scale of Y
+  const int* gate;  // if non-null and *gate == 0 the product is skipped (device-side control)
 };
 
 __host__ __device__ inline long long su0(long long c, long long W, int G) { return (c * W) / G; }
@@ -66,6 +68,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                    int stages) {
   static_assert(!SPLIT3 || SUB == 1, "the split-bf16 projection uses 128-row tiles");
   static_assert(!F8 || (!TRANS && !SPLIT3), "e4m3 products take K-major operands only");
+  if (g.gate && *g.gate == 0) return;  // uniform over the grid, before any resource is taken
   constexpr int BM = 128 * SUB;       // rows per tile: SUB sub-tiles of 128 share each X tile
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int ms = m0 + 128 * sb;
           if (!TRANS) {
             tma_load_2d(sAs, &tmA, k0, ms, &full[s]);
+            if (SPLIT3) tma_load_2d(sAs + A_TILE, &tmA2, k0, ms, &full[s]);
           } else {
             tma_load_2d(sAs, &tmA, ms, k0, &full[s]);
             tma_load_2d(sAs + 8192, &tmA, ms + 64, k0, &full[s]);
@@ -196,7 +200,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             else
               mma_bf16(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
             if (SPLIT3) {
-              const uint64_t ad2 = umma_desc(aAs + A_TILE + 2048 * k, 8192, 1024);
+              const uint64_t ad2 = TRANS ? umma_desc(aAs + A_TILE + 2048 * k, 8192, 1024)
+                                         : umma_desc(aAs + A_TILE + 32 * k, 16, 1024);
               const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
               mma_bf16(dtm, ad, bd2, idesc, 1u);   // Ah^T Xl
               mma_bf16(dtm, ad2, bd, idesc, 1u);   // Al^T Xh
@@ -294,6 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // float4.
 constexpr int FIX_ROWS = 16;
 __global__ void __launch_bounds__(256) tc_fixup_kernel(TcArgs g, int BM) {
+  if (g.gate && *g.gate == 0) return;
   const int t = blockIdx.x;
   const int r0 = blockIdx.y * FIX_ROWS;
   __shared__ int s_cf, s_cl, s_slot[TC_MAX_CTAS + 1];
@@ -383,7 +389,7 @@ bool tc_supported(int N) { return N >= 1 && N <= 256; }
 
 cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const __nv_bfloat16* A, int lda,
                            const __nv_bfloat16* A2, const __nv_bfloat16* X, int ldx, const __nv_bfloat16* X2, float* Y,
-                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm) {
+                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm, const int* gate) {
   if (M == 0 || N == 0) return cudaSuccess;
   if (!get_encode()) return cudaErrorNotSupported;
   if ((lda % 8) || (ldx % 8) || (((uintptr_t)A | (uintptr_t)X) & 15)) return cudaErrorInvalidValue;
@@ -409,6 +415,7 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   g.st = st;
   g.rs = nullptr;
   g.cs = nullptr;
+  g.gate = gate;
   CUtensorMap mA, mA2, mX, mX2;
   bool ok = true;
   if (!trans)
@@ -417,7 +424,10 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
     ok &= make_map(&mA, A, M, K, lda, 64, 64);   // A: K x M row-major
   ok &= make_map(&mX, X, N, K, ldx, 64, 64);     // X: K x N row-major
   if (split3) {
-    ok &= make_map(&mA2, A2, M, K, lda, 64, 64);
+    if (!trans)
+      ok &= make_map(&mA2, A2, K, M, lda, 64, 128);
+    else
+      ok &= make_map(&mA2, A2, M, K, lda, 64, 64);
     ok &= make_map(&mX2, X2, N, K, ldx, 64, 64);
   } else {
     mA2 = mA;
@@ -437,8 +447,10 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
     if (e != cudaSuccess) return e;                                                                          \
     tc_gemm_kernel<TR, SP, SB><<<g.G, TC_THREADS, smem, s>>>(mA, mA2, mX, mX2, g, stages);                   \
   } while (0)
-  if (split3)
+  if (split3 && trans)
     RSVD_TC_LAUNCH(true, true, 1);
+  else if (split3)
+    RSVD_TC_LAUNCH(false, true, 1);
   else if (!trans && SUBT == 1)
     RSVD_TC_LAUNCH(false, false, 1);
   else if (!trans)
@@ -503,6 +515,7 @@ cudaError_t launch_tc_gemm_e4m3(int M, int N, int K, const uint8_t* A8, int lda,
   g.st = st;
   g.rs = rs;
   g.cs = cs;
+  g.gate = nullptr;
   CUtensorMap mA, mX;
   bool ok = make_map_u8(&mA, A8, K, M, lda, 128, 128);   // A8: M x K bytes
   ok &= make_map_u8(&mX, X8t, K, N, ldx, 128, g.Npad);     // X8t: N x K bytes

@@ -31,6 +31,10 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
               int sms, cudaStream_t s, const int* skip = nullptr);
 template <typename T>
 void launch_copy_bf16(int rows, int l, const T* Y, int ldy, __nv_bfloat16* Yb, int lb, cudaStream_t s);
+// CholeskyQR2 with the apply Q = Y R^-1 on tensor cores (three-term split bf16); binary32 data
+size_t orth_tc_workspace_bytes(int rows, int l, int sms);
+void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
+                 DevStatus* st, int sms, cudaStream_t s);
 void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const int* gate, int copy_if_gated,
                     cudaStream_t s, const int* skip = nullptr);
 
@@ -53,7 +57,8 @@ int tc_rows_per_tile(int M, bool split3);
 // bm: rows per tile (128 or 256); 0 lets the launcher choose (tc_rows_per_tile).
 cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const __nv_bfloat16* A, int lda,
                            const __nv_bfloat16* A2, const __nv_bfloat16* X, int ldx, const __nv_bfloat16* X2, float* Y,
-                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm = 0);
+                           int ldy, float* part, int sms, DevStatus* st, cudaStream_t s, int bm = 0,
+                           const int* gate = nullptr);
 void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb,
                        int sms, cudaStream_t s);
 // Y (M x N fp32) = diag(rs) (A8 X8t^T) diag(cs): A8 M x K, X8t N x K, e4m3

@@ -195,8 +195,8 @@ MixedLayout mixed_layout(void* ws, int m, int n, int l, int kk, int sms) {
   if (pw3 > pw) pw = pw3;
   if (sign_workspace_bytes(n, kk) > pw) pw = sign_workspace_bytes(n, kk);
   L.part = c.take<float>(pw / sizeof(float) + 1);
-  size_t ow = orth_workspace_bytes(m, l, sms, 4);
-  const size_t ow2 = orth_workspace_bytes(n, l, sms, 4);
+  size_t ow = orth_tc_workspace_bytes(m, l, sms);
+  const size_t ow2 = orth_tc_workspace_bytes(n, l, sms);
   if (ow2 > ow) ow = ow2;
   L.orthws = c.take<unsigned char>(ow);
   L.Rb = c.take<double>((size_t)l * l);
@@ -267,7 +267,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                         sms, L.st, s), "sketch A G")) != RSVD_OK)
       return st;
   }
-  run_orth<float, float>(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
+  run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
   // power steps
   for (int j = 0; j < p->q; ++j) {
     {
@@ -276,14 +276,14 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                           L.part, sms, L.st, s), "sketch A^T Q")) != RSVD_OK)
         return st;
     }
-    run_orth<float, float>(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s);
+    run_orth_tc(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s);
     {
       ProfScope ps(h, 0, s);
       if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Zb, l8, nullptr, L.Y, l,
                                           L.part, sms, L.st, s), "sketch A W")) != RSVD_OK)
         return st;
     }
-    run_orth<float, float>(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
+    run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
   }
   // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
   launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);
@@ -293,7 +293,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                         L.st, s), "projection")) != RSVD_OK)
       return st;
   }
-  run_orth<float, float>(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  run_orth_tc(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
   // SVD of R_B^T
   cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
   if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
@@ -388,7 +388,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                              s), "e4m3 sketch A G")) != RSVD_OK)
       return st;
   }
-  run_orth<float, float>(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   for (int j = 0; j < p->q; ++j) {
     // Z = A^T Q = A8^T (S Q)
     launch_fp8_cols(m, l, L.Y, l, E.s, E.X8t, m16, E.cvec, E.colws, s);
@@ -398,7 +398,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                                L.st, s), "e4m3 sketch A^T Q")) != RSVD_OK)
         return st;
     }
-    run_orth<float, float>(n, l, L.Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    run_orth_tc(n, l, L.Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
     launch_fp8_cols(n, l, L.Z, l, nullptr, E.X8t, n16, E.cvec, E.colws, s);
     {
       ProfScope ps(h, 0, s);
@@ -406,7 +406,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                                L.st, s), "e4m3 sketch A W")) != RSVD_OK)
         return st;
     }
-    run_orth<float, float>(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   }
   // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
   launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);
@@ -416,7 +416,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                         L.st, s), "projection")) != RSVD_OK)
       return st;
   }
-  run_orth<float, float>(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  run_orth_tc(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
   cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
   if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
   launch_sort_gather<float>(l, kk, L.sigma, L.Wt, L.Jt, D, L.Wsel, L.Jsel, s);

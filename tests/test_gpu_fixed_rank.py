@@ -85,6 +85,8 @@ def test_argument_errors(lib):
     assert lib.rsvd_fixed_rank(h, 50, 40, A, 40, prm, U, 5, D, V, 5, small) == lib.RSVD_E_NOMEM
     assert lib.rsvd_fixed_rank(h, 50, 40, A, 39, prm, U, 5, D, V, 5, small) == lib.RSVD_E_INVALID
     prm.prec = lib.RSVD_MIXED_FP8
+    assert lib.rsvd_fixed_rank(h, 50, 40, A, 40, prm, U, 5, D, V, 5, small) == lib.RSVD_E_NOMEM
+    prm.prec = 9  # no such precision
     assert lib.rsvd_fixed_rank(h, 50, 40, A, 40, prm, U, 5, D, V, 5, small) == lib.RSVD_E_UNSUPPORTED
     # k = 0: nothing to compute, nothing enqueued
     prm = lib.make_params(0, 0, 0, 0, lib.RSVD_F32, 0)

@@ -37,8 +37,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="poly", choices=["poly", "pca"],
-                    help="poly: 32768^2 polynomial decay (bf16); pca: 2^20 x 4096 PCA matrix (e4m3)")
+    ap.add_argument("--workload", default="poly", choices=["poly", "pca", "controller"],
+                    help="poly: 32768^2 polynomial decay (bf16); pca: 2^20 x 4096 PCA matrix (e4m3); "
+                         "controller: a stream of square matrices solved to tol 1e-4 (learned controller)")
+    ap.add_argument("--train", type=int, default=192, help="controller: training matrices")
+    ap.add_argument("--lo", type=int, default=512, help="controller: smallest n")
+    ap.add_argument("--hi", type=int, default=16384, help="controller: largest n")
     ap.add_argument("--prec", default=None, choices=["bf16", "f32", "fp8"])
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--n", type=int, default=None)
@@ -52,7 +56,8 @@ def parse():
     ap.add_argument("--sample", type=int, default=None, help="CPU oracle sample size (rows; square for poly)")
     a = ap.parse_args()
     dflt = {"poly": dict(prec="bf16", m=32768, n=32768, k=200, p=56, q=2, seed=2001, sample=8192),
-            "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768)}[a.workload]
+            "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768),
+            "controller": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=60000, sample=0)}[a.workload]
     for key, val in dflt.items():
         if getattr(a, key) is None:
             setattr(a, key, val)
@@ -466,9 +471,108 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- controller stream --
+def run_controller(a):
+    """Trains the controller on the GPU from the adaptive finder's own labels
+    (training seeds 50000+), then solves a held-out stream (seeds a.seed +
+    i, `steps` matrices, n log-uniform in [lo, hi]) to relative Frobenius
+    tolerance 1e-4 three ways: the controller (probe, network, fixed-rank
+    solve, judge, fallback), the blocked adaptive range finder alone, and a
+    fixed conservative l = min(n, 256), q = 2.  Matrices are synthesized
+    before each solve (untimed); solves are timed with CUDA events."""
+    import numpy as np
+    import torch
+    import paper_1607_01649_gb300 as rs
+    from workloads import controller_matrix, mlp_init
+    dev = torch.device("cuda", 0)
+    h = rs.handle(0)
+    tol = 1e-4
+    X, yl, yq = [], [], []
+    t0 = time.perf_counter()
+    for s in range(50000, 50000 + a.train):
+        A, _ = controller_matrix(s, lo=a.lo, hi=a.hi, device=dev)
+        f, _ = rs.probe_features(A, seed=s)
+        X.append(f)
+        _, _, (c, q) = rs.adaptive_labels(A, tol, seed=s, max_rank=min(A.shape[0], 256))
+        yl.append(c)
+        yq.append(q)
+        del A
+    X = torch.stack(X)
+    yl = torch.tensor(yl, dtype=torch.int32, device=dev)
+    yq = torch.tensor(yq, dtype=torch.int32, device=dev)
+    theta = torch.from_numpy(mlp_init(7).astype(np.float32)).to(dev)
+    tr = rs.Trainer(theta, lr=2e-3, lam=1.0)
+    for _ in range(3000):
+        tr.step(X, yl, yq)
+    loss = float(tr.step(X, yl, yq).item())
+    t_train = time.perf_counter() - t0
+
+    def rel_residual(A, U, D, V, r):
+        f2, a2 = 0.0, 0.0
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        try:
+            UD = U[:, :r] * D[:r].float()[None, :]
+            for r0 in range(0, A.shape[0], 4096):
+                Ab = A[r0:r0 + 4096]
+                R = Ab - UD[r0:r0 + 4096] @ V[:, :r].T
+                f2 += float((R.double() ** 2).sum())
+                a2 += float((Ab.double() ** 2).sum())
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+        return (f2 / a2) ** 0.5
+
+    stream = torch.cuda.current_stream()
+    res = {"adaptive": [0.0, 0, 0], "controller": [0.0, 0, 0], "fixed": [0.0, 0, 0]}
+    falls = 0
+    for i in range(a.warmup + a.steps):
+        s = a.seed + i
+        A, _ = controller_matrix(s, lo=a.lo, hi=a.hi, device=dev)
+        n = A.shape[0]
+        R = min(n, 256)
+        for meth in ("adaptive", "controller", "fixed"):
+            rs.rsvd_controller_attach(h, tr.theta, 0.9, 0.8)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if meth == "adaptive":
+                U, D, V, r, err, code = rs.adaptive_tol(A, tol, seed=s, max_rank=R)
+            elif meth == "controller":
+                U, D, V, r, err, code = rs.adaptive_tol(A, tol, seed=s, max_rank=R, controller=True)
+            else:
+                U, D, V = rs.fixed_rank(A, R, 0, 2, seed=s, full=True, sync=True)
+                r = R
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i < a.warmup:
+                continue
+            if meth == "controller":
+                falls += rs.rsvd_controller_last(h)["fallback"]
+            res[meth][0] += e0.elapsed_time(e1)
+            res[meth][1] += 1
+            res[meth][2] += rel_residual(A, U, D, V, r) <= tol
+            del U, D, V
+        del A
+    out = {m: {"solves_per_s": v[1] / (v[0] / 1000.0), "fraction_meeting_tol": v[2] / max(v[1], 1)}
+           for m, v in res.items()}
+    line = {"metric": METRIC, "value": out["controller"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["controller"][0] / max(res["controller"][1], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "controller stream: %d held-out square fp32 matrices, n log-uniform in [%d, %d], "
+                                   "spectra exp / poly / step, tol 1e-4 relative Frobenius" % (a.steps, a.lo, a.hi),
+                       "training": "%d matrices, labels from the adaptive finder (q = 0..3), 3000 Adam steps, "
+                                   "final loss %.3f, %.0f s" % (a.train, loss, t_train)},
+            "controller": out["controller"], "adaptive_only": out["adaptive"], "fixed_l256_q2": out["fixed"],
+            "fallbacks": falls}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.workload == "controller":
+        run_controller(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -10,6 +10,14 @@ split bf16, the small SVD, the lift to U and V).
 ``--workload pca``: the 2^20 x 4096 PCA-shaped matrix (rank-64 signal plus
 noise, column-centred), k = 64, p = 64, q = 1, e4m3 sketches.
 
+``--workload batched``: 4096 kernel-matrix blocks (1 / |x_i - y_j| between two
+point clouds 3 apart, m, n ~ U{64..1024}) solved to relative Frobenius
+tolerance 1e-6 by rsvd_batched, one persistent launch replayed from a CUDA
+graph; one step = the whole batch, `value` = blocks solved per second.
+
+``--workload controller``: a stream of square matrices solved to tolerance
+1e-4 with the learned (l, q) controller (trained first, on the GPU).
+
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own
 matrix (replicas; there is no exchange step), and `value` is the total over
 ranks.  ``--impl reference`` times the float64 CPU oracle instead, on a
@@ -37,9 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="poly", choices=["poly", "pca", "controller"],
+    ap.add_argument("--workload", default="poly", choices=["poly", "pca", "controller", "batched"],
                     help="poly: 32768^2 polynomial decay (bf16); pca: 2^20 x 4096 PCA matrix (e4m3); "
-                         "controller: a stream of square matrices solved to tol 1e-4 (learned controller)")
+                         "controller: a stream of square matrices solved to tol 1e-4 (learned controller); "
+                         "batched: 4096 kernel-matrix blocks to tol 1e-6 in one persistent launch")
+    ap.add_argument("--count", type=int, default=4096, help="batched: number of blocks")
     ap.add_argument("--train", type=int, default=192, help="controller: training matrices")
     ap.add_argument("--lo", type=int, default=512, help="controller: smallest n")
     ap.add_argument("--hi", type=int, default=16384, help="controller: largest n")
@@ -57,7 +67,8 @@ def parse():
     a = ap.parse_args()
     dflt = {"poly": dict(prec="bf16", m=32768, n=32768, k=200, p=56, q=2, seed=2001, sample=8192),
             "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768),
-            "controller": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=60000, sample=0)}[a.workload]
+            "controller": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=60000, sample=0),
+            "batched": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=4001, sample=0)}[a.workload]
     for key, val in dflt.items():
         if getattr(a, key) is None:
             setattr(a, key, val)
@@ -476,9 +487,11 @@ def run_controller(a):
     """Trains the controller on the GPU from the adaptive finder's own labels
     (training seeds 50000+), then solves a held-out stream (seeds a.seed +
     i, `steps` matrices, n log-uniform in [lo, hi]) to relative Frobenius
-    tolerance 1e-4 three ways: the controller (probe, network, fixed-rank
-    solve, judge, fallback), the blocked adaptive range finder alone, and a
-    fixed conservative l = min(n, 256), q = 2.  Matrices are synthesized
+    tolerance 1e-4 four ways: the controller (probe, network, fixed-rank
+    solve, judge, and the adaptive range finder as fallback), the same with
+    the escalating fallback (one more fixed-rank solve at l = 256, q >= 2),
+    the blocked adaptive range finder alone, and a fixed conservative
+    l = min(n, 256), q = 2.  Matrices are synthesized
     before each solve (untimed); solves are timed with CUDA events."""
     import numpy as np
     import torch
@@ -523,22 +536,23 @@ def run_controller(a):
         return (f2 / a2) ** 0.5
 
     stream = torch.cuda.current_stream()
-    res = {"adaptive": [0.0, 0, 0], "controller": [0.0, 0, 0], "fixed": [0.0, 0, 0]}
-    falls = 0
+    res = {"adaptive": [0.0, 0, 0], "controller": [0.0, 0, 0], "escalate": [0.0, 0, 0], "fixed": [0.0, 0, 0]}
+    falls = {"controller": 0, "escalate": 0}
     for i in range(a.warmup + a.steps):
         s = a.seed + i
         A, _ = controller_matrix(s, lo=a.lo, hi=a.hi, device=dev)
         n = A.shape[0]
         R = min(n, 256)
-        for meth in ("adaptive", "controller", "fixed"):
+        for meth in ("adaptive", "controller", "escalate", "fixed"):
             rs.rsvd_controller_attach(h, tr.theta, 0.9, 0.8)
+            rs.rsvd_controller_fallback(h, 1 if meth == "escalate" else 0)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if meth == "adaptive":
                 U, D, V, r, err, code = rs.adaptive_tol(A, tol, seed=s, max_rank=R)
-            elif meth == "controller":
+            elif meth in ("controller", "escalate"):
                 U, D, V, r, err, code = rs.adaptive_tol(A, tol, seed=s, max_rank=R, controller=True)
             else:
                 U, D, V = rs.fixed_rank(A, R, 0, 2, seed=s, full=True, sync=True)
@@ -547,8 +561,9 @@ def run_controller(a):
             torch.cuda.synchronize()
             if i < a.warmup:
                 continue
-            if meth == "controller":
-                falls += rs.rsvd_controller_last(h)["fallback"]
+            if meth in ("controller", "escalate"):
+                info = rs.rsvd_controller_last(h)
+                falls[meth] += info["fallback"] or info["escalated"]
             res[meth][0] += e0.elapsed_time(e1)
             res[meth][1] += 1
             res[meth][2] += rel_residual(A, U, D, V, r) <= tol
@@ -563,14 +578,245 @@ def run_controller(a):
                                    "spectra exp / poly / step, tol 1e-4 relative Frobenius" % (a.steps, a.lo, a.hi),
                        "training": "%d matrices, labels from the adaptive finder (q = 0..3), 3000 Adam steps, "
                                    "final loss %.3f, %.0f s" % (a.train, loss, t_train)},
-            "controller": out["controller"], "adaptive_only": out["adaptive"], "fixed_l256_q2": out["fixed"],
-            "fallbacks": falls}
+            "controller": out["controller"], "controller_escalating": out["escalate"],
+            "adaptive_only": out["adaptive"], "fixed_l256_q2": out["fixed"], "fallbacks": falls}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------- batched -------
+BATCH_TOL = 1e-6
+BATCH_R = 64
+BATCH_B = 16
+
+
+def batched_name(a):
+    return ("batched adaptive: %d fp32 blocks A_ij = 1/|x_i - y_j| (unit-cube clouds 3 apart), m, n ~ U{64..1024}, "
+            "tol %g relative Frobenius, b = %d, max rank %d" % (a.count, BATCH_TOL, BATCH_B, BATCH_R))
+
+
+def batched_oracle_sample(a, seconds, start=0):
+    """The float64 oracle's blocked adaptive finder on blocks start, start + 1,
+    ... of the same workload (formed on the host), for about `seconds`.
+    Returns (blocks solved, seconds, mean m n of the sample)."""
+    import numpy as np
+    import oracle
+    from workloads import kernel_block
+    done, t_run, mn = 0, 0.0, 0
+    p = start
+    while t_run < seconds and done < a.count:
+        A = kernel_block(p % a.count, seed=a.seed).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.adaptive_blocked(A, BATCH_TOL, b=BATCH_B, seed=a.seed + (p % a.count), max_rank=BATCH_R)
+        t_run += time.perf_counter() - t0
+        mn += A.shape[0] * A.shape[1]
+        done += 1
+        p += 1
+    return done, t_run, mn / max(done, 1)
+
+
+def run_batched(a):
+    """rsvd_batched on the whole batch per step, replayed from a CUDA graph;
+    beside it the plain binary32 single-problem adaptive path on a sample of
+    the blocks, and the float64 oracle on a sample on the host cores."""
+    import numpy as np
+    import torch
+    import paper_1607_01649_gb300 as rs
+    from workloads import kernel_block_shapes, kernel_block_torch
+
+    world, rank, local = dist_setup(a)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist = None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    seed = a.seed + 1000 * rank
+    shapes = kernel_block_shapes(a.count, seed=seed)
+    plan = rs.BatchPlan(shapes, R=BATCH_R, device=dev)
+    for p in range(a.count):
+        kernel_block_torch(p, plan.block(p), seed=seed)
+    h = rs.handle(local)
+    side = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(side):
+        for _ in range(a.warmup):
+            code = rs.batched_run(plan, BATCH_TOL, block=BATCH_B, seed=seed, stream=side)
+            if code != rs.RSVD_OK:
+                raise rs.RsvdError(code, rs.last_error(h))
+    side.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    launches0 = rs.rsvd_kernel_launches(h)
+    with torch.cuda.graph(graph, stream=side):
+        code = rs.batched_run(plan, BATCH_TOL, block=BATCH_B, seed=seed, stream=side)
+    if code != rs.RSVD_OK:
+        raise rs.RsvdError(code, rs.last_error(h))
+    launches_per_step = rs.rsvd_kernel_launches(h) - launches0
+    graph.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K graph replays (inputs 4.9 GB, larger than L2)
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    with torch.cuda.stream(side):
+        ev[0].record(side)
+        for i in range(a.steps):
+            graph.replay()
+            ev[i + 1].record(side)
+    barrier()
+    clk = clocks.stop()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
+    ms = ev[0].elapsed_time(ev[-1])
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * a.count * a.steps / (ms / 1000.0)
+    status = plan.status[:a.count].cpu().numpy()
+    ranks = plan.rank[:a.count].cpu().numpy().astype(np.int64)
+    errs = plan.err[:a.count].cpu().numpy()
+
+    # ---- roofline: the persistent kernel moves A once for ||A||_F and the
+    # first sample, then 4 passes of the working copy per block step (read for
+    # A_j G, read for Q^T A_j, read and write for the update)
+    mn = np.array([m * n for m, n in shapes], dtype=np.float64)
+    steps_p = np.ceil(ranks / float(BATCH_B))
+    alg_bytes = float(np.sum(4.0 * mn * (1.0 + 4.0 * steps_p)))
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        hbm, peak_src = 6800.0, "fallback"
+    per_ms = statistics.median(per)
+    achieved = alg_bytes / (per_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "algorithmic_bytes": alg_bytes,
+            "kernel": "batched_kernel (one CTA per problem, persistent, largest-first queue)",
+            "avg_ms": per_ms, "peak_source": peak_src,
+            "note": "graph replay time (order kernel + persistent kernel); the working copies A_j partly hit L2"}
+
+    # ---- e2e: every block copied in from pinned host memory, U, D, V, ranks
+    # and residuals copied out, all inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        Ah = torch.empty_like(plan.A, device="cpu").pin_memory()
+        Ah.copy_(plan.A)
+        Uh = torch.empty_like(plan.U, device="cpu").pin_memory()
+        Vh = torch.empty_like(plan.V, device="cpu").pin_memory()
+        Dh = torch.empty_like(plan.D, device="cpu").pin_memory()
+        rh = torch.empty_like(plan.rank, device="cpu").pin_memory()
+        eh = torch.empty_like(plan.err, device="cpu").pin_memory()
+        steps_e2e = max(1, min(a.steps, 5))
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(side):
+            f0.record(side)
+            for i in range(steps_e2e):
+                plan.A.copy_(Ah, non_blocking=True)
+                rs.batched_run(plan, BATCH_TOL, block=BATCH_B, seed=seed, stream=side)
+                for d_, h_ in ((plan.U, Uh), (plan.V, Vh), (plan.D, Dh), (plan.rank, rh), (plan.err, eh)):
+                    h_.copy_(d_, non_blocking=True)
+            f1.record(side)
+        barrier()
+        ems = f0.elapsed_time(f1)
+        if dist is not None:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        nb = lambda t: t.numel() * t.element_size()
+        e2e = {"value": world * a.count * steps_e2e / (ems / 1000.0), "unit": "solves/s",
+               "h2d_bytes_per_step": nb(plan.A),
+               "d2h_bytes_per_step": nb(plan.U) + nb(plan.V) + nb(plan.D) + nb(plan.rank) + nb(plan.err),
+               "steps": steps_e2e}
+        del Ah, Uh, Vh
+
+    # ---- plain binary32: the single-problem adaptive path (rsvd_adaptive_tol),
+    # one call per block, on an evenly spaced sample of the blocks
+    f32 = None
+    if not a.no_f32:
+        idx = list(range(0, a.count, max(1, a.count // 256)))
+        for p in idx[:4]:
+            rs.adaptive_tol(plan.block(p), BATCH_TOL, block=BATCH_B, max_rank=BATCH_R, seed=seed + p)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record()
+        agree = 0
+        for p in idx:
+            _, D1, _, r1, _, _ = rs.adaptive_tol(plan.block(p), BATCH_TOL, block=BATCH_B, max_rank=BATCH_R,
+                                                 seed=seed + p)
+            agree += int(r1 == int(ranks[p]))
+        g1.record()
+        torch.cuda.synchronize()
+        f32 = {"value": len(idx) / (g0.elapsed_time(g1) / 1000.0), "unit": "solves/s",
+               "sample": "%d evenly spaced blocks, one rsvd_adaptive_tol call each" % len(idx),
+               "same_rank_as_batched": agree / float(len(idx))}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not a.no_cpu:
+        done, t_run, mn_s = batched_oracle_sample(a, 12.0)
+        cpu = {"value": done / t_run, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "float64 oracle adaptive_blocked on blocks 0..%d of the workload (mean m n %.0f vs %.0f "
+                         "over the batch), %.1f s" % (done - 1, mn_s, float(mn.mean()), t_run)}
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": batched_name(a), "graph": "one CUDA graph replay per step",
+                       "l2": "inputs larger than L2 (%.2f GB of blocks; L2 129 MB)" % (4.0 * mn.sum() / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * a.steps, "clocks": clk,
+            "error": {"max_residual_rel": float(errs.max()), "tol": BATCH_TOL,
+                      "blocks_converged": int(np.sum(status == 0)), "mean_rank": float(ranks.mean()),
+                      "max_rank": int(ranks.max())},
+            "plain_f32": f32}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference_batched(a):
+    """The oracle arm for the batched workload: each step solves a bounded
+    sample of blocks with the float64 oracle on the host cores."""
+    world, rank, local = dist_setup(a)
+    if rank != 0:
+        return
+    for w in range(a.warmup):
+        batched_oracle_sample(a, 0.5, start=w)
+    done, t_run, mn_s = 0, 0.0, 0.0
+    for i in range(a.steps):
+        d, t, m_ = batched_oracle_sample(a, 10.0 / max(a.steps, 1), start=done)
+        done, t_run, mn_s = done + d, t_run + t, mn_s + m_ * d
+    value = done / t_run
+    sample = ("float64 oracle adaptive_blocked on blocks 0..%d of the workload (mean m n %.0f), about %.1f s per "
+              "step" % (done - 1, mn_s / max(done, 1), t_run / a.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * a.count / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": batched_name(a)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def main():
     a = parse()
-    if a.workload == "controller":
+    if a.workload == "batched":
+        (run_reference_batched if a.impl == "reference" else run_batched)(a)
+    elif a.workload == "controller":
         run_controller(a)
     elif a.impl == "reference":
         run_reference(a)

@@ -314,9 +314,18 @@ rsvd_status rsvd_mlp_train_step(rsvd_handle_t handle, int batch, const float* X,
  * safety * tol * ||A||_F. */
 rsvd_status rsvd_controller_attach(rsvd_handle_t handle, const float* theta, double quantile, double safety);
 
+/* What a controlled solve does when the judge rejects the network's (l, q):
+ * mode 0 (default): the blocked adaptive range finder (Sec. 12.3) recomputes
+ * the result from scratch; mode 1: the fixed-rank solve is repeated once at
+ * the largest rank allowed (max_rank) with q = max(q, 2) and judged again
+ * (NOT_CONVERGED if that also misses the tolerance). */
+rsvd_status rsvd_controller_fallback(rsvd_handle_t handle, int mode);
+
 /* Host-side record of the last controlled solve on this handle:
- * info[0] = l chosen, info[1] = q chosen, info[2] = accepted by the judge,
- * info[3] = fell back to the adaptive range finder, info[4] = output rank;
+ * info[0] = l, info[1] = q of the last fixed-rank solve (the network's choice,
+ * or the escalated one when info[3] = 2), info[2] = accepted by the judge,
+ * info[3] = 0 no fallback, 1 fell back to the adaptive range finder, 2
+ * escalated to the largest rank, info[4] = output rank;
  * est[0] = Frobenius residual estimate / ||A||_F, est[1] = spectral bound /
  * ||A||_F (Lemma thm:aposteriori).  info: 5 ints, est: 2 doubles (host). */
 rsvd_status rsvd_controller_last(rsvd_handle_t handle, int* info, double* est);

@@ -51,6 +51,7 @@ EXPORTED = [
     "rsvd_sketch_noalloc", "rsvd_batched_workspace_size", "rsvd_batched",
     "rsvd_probe_workspace_size", "rsvd_probe_features", "rsvd_mlp_workspace_size", "rsvd_mlp_forward",
     "rsvd_mlp_grad", "rsvd_mlp_train_step", "rsvd_controller_attach", "rsvd_controller_last",
+    "rsvd_controller_fallback",
 ]
 
 CTRL_D_IN = 17
@@ -117,6 +118,7 @@ def load():
         "rsvd_mlp_train_step": [vp, i, vp, vp, vp, ctypes.c_float, vp, vp, vp, i, ctypes.c_float, vp, vp, sz, vp],
         "rsvd_controller_attach": [vp, vp, ctypes.c_double, ctypes.c_double],
         "rsvd_controller_last": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
+        "rsvd_controller_fallback": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -299,8 +301,12 @@ def rsvd_controller_last(h):
     info = (ctypes.c_int * 5)()
     est = (ctypes.c_double * 2)()
     _check(load().rsvd_controller_last(h, info, est), h)
-    return {"l": info[0], "q": info[1], "accepted": bool(info[2]), "fallback": bool(info[3]), "rank": info[4],
-            "est_rel": est[0], "spec_bound_rel": est[1]}
+    return {"l": info[0], "q": info[1], "accepted": bool(info[2]), "fallback": info[3] == 1,
+            "escalated": info[3] == 2, "rank": info[4], "est_rel": est[0], "spec_bound_rel": est[1]}
+
+
+def rsvd_controller_fallback(h, mode):
+    return _check(load().rsvd_controller_fallback(h, int(mode)), h)
 
 
 def rsvd_kernel_launches(h):

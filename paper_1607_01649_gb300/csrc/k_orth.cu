@@ -145,7 +145,8 @@ __device__ __forceinline__ void gram_store_chunk(float (*S)[GT], const float4 (&
 
 __global__ void __launch_bounds__(G32_THREADS)
     gram_partial_f32_kernel(int rows, int l, const float* __restrict__ Y, int ldy, double* __restrict__ P,
-                            int rows_per_split, const int* gate, const int* skip) {
+                            int rows_per_split, const int* gate, const int* skip, __nv_bfloat16* __restrict__ Yh,
+                            __nv_bfloat16* __restrict__ Yl, int lb) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   __shared__ __align__(16) float Yi[GCH][GT];
   __shared__ __align__(16) float Yj[GCH][GT];
@@ -178,6 +179,38 @@ __global__ void __launch_bounds__(G32_THREADS)
     __syncthreads();  // previous chunk's reads are done
     gram_store_chunk(Yi, ri);
     if (!diag) gram_store_chunk(Yj, rj);
+    if (diag && Yh) {
+      // the diagonal tiles read every element of Y exactly once: write the
+      // bf16 pair Y = Yh + Yl that the tensor-core apply takes
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + G32_THREADS * u;
+        const int gr = r0 + e / 16, gc = bi * GT + 4 * (e % 16);
+        if (gr < r_end && gc < l) {
+          const float4 a = ri[u];
+          const __nv_bfloat162 h01 = __floats2bfloat162_rn(a.x, a.y), h23 = __floats2bfloat162_rn(a.z, a.w);
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          const __nv_bfloat162 l01 = __floats2bfloat162_rn(a.x - f01.x, a.y - f01.y);
+          const __nv_bfloat162 l23 = __floats2bfloat162_rn(a.z - f23.x, a.w - f23.y);
+          __nv_bfloat16* ph = Yh + (size_t)gr * lb + gc;
+          __nv_bfloat16* pl = Yl + (size_t)gr * lb + gc;
+          if (gc + 4 <= l && (lb % 4) == 0) {
+            *reinterpret_cast<uint2*>(ph) = make_uint2(*reinterpret_cast<const uint32_t*>(&h01),
+                                                       *reinterpret_cast<const uint32_t*>(&h23));
+            *reinterpret_cast<uint2*>(pl) = make_uint2(*reinterpret_cast<const uint32_t*>(&l01),
+                                                       *reinterpret_cast<const uint32_t*>(&l23));
+          } else {
+            const __nv_bfloat16 hv[4] = {h01.x, h01.y, h23.x, h23.y}, lv[4] = {l01.x, l01.y, l23.x, l23.y};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (gc + q < l) {
+                ph[q] = hv[q];
+                pl[q] = lv[q];
+              }
+          }
+        }
+      }
+    }
     __syncthreads();
     if (r0 + GCH < r_end) {  // prefetch the next chunk
       gram_load_chunk(Y, ldy, r0 + GCH, r_end, bi * GT, l, vec, ri);
@@ -253,7 +286,7 @@ int gram_splits(int rows, int l, int sms) {
 
 template <typename T>
 void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
-                 cudaStream_t s, const int* skip) {
+                 cudaStream_t s, const int* skip, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int lb) {
   const int nb = ceil_div(l, GT);
   const int tiles = nb * (nb + 1) / 2;
   const int splits = gram_splits(rows, l, sms);
@@ -261,7 +294,7 @@ void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, flo
   const int used = ceil_div(rows, rps);
   if (sizeof(T) == 4)
     gram_partial_f32_kernel<<<dim3(tiles, used), G32_THREADS, 0, s>>>(rows, l, (const float*)Y, ldy, P, rps, gate,
-                                                                      skip);
+                                                                      skip, Yh, Yl, lb);
   else
     gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate, skip);
   note_launch();
@@ -396,6 +429,25 @@ __device__ __forceinline__ void warp_blk_nt(C* Cb, const C* Ab, const C* Bb, boo
       *p = sub ? *p - acc[x][y] : acc[x][y];
     }
   __syncwarp();
+}
+
+// One warp: acc (lane's 4 x 8 tile, rows 4 lr .., columns 8 lc ..) += A B for
+// 32 x 32 blocks A, B with row stride CP.
+template <typename C>
+__device__ __forceinline__ void warp_blk_nn_acc(C (&acc)[4][8], const C* Ab, const C* Bb) {
+  const int lane = threadIdx.x % 32, lr = lane >> 2, lc = lane & 3;
+#pragma unroll 4
+  for (int t = 0; t < 32; ++t) {
+    C a[4], b[8];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) a[x] = Ab[(4 * lr + x) * CP + t];
+#pragma unroll
+    for (int y = 0; y < 8; ++y) b[y] = Bb[t * CP + 8 * lc + y];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+  }
 }
 
 // One warp: Cholesky of diagonal block k in place, and 1 / L(q, q) into
@@ -618,30 +670,43 @@ __global__ void __launch_bounds__(NT)
   // column j from the last to the first (the trailing part already holds its
   // inverse): T_i = sum_{k = j + 1}^{i} W_ik L_kj (i > j), W_ij = -T_i X_jj.
   C* Ts = rdg + CBK * NB;  // NB - 1 scratch blocks
-  for (int j = NB - 2; j >= 0; --j) {
-    const int nrow = (NB - 1 - j) * CBK;
-    for (int rr = warp; rr < nrow; rr += nw) {
-      const int i = j + 1 + rr / CBK, r = rr % CBK;
-      C acc = C(0);
-      for (int k = j + 1; k <= i; ++k) {
-        const C* Wr = (k == i) ? Xs + (size_t)i * CBS + r * CP : Ls + (size_t)lblk(i, k) * CBS + r * CP;
-        const C* Lc = Ls + (size_t)lblk(k, j) * CBS + lane;
-#pragma unroll 8
-        for (int t = 0; t < 32; ++t) acc = fma(Wr[t], Lc[t * CP], acc);
+  {
+    const int lr = lane >> 2, lc = lane & 3;
+    for (int j = NB - 2; j >= 0; --j) {
+      // T_i = sum_k W_ik L_kj, one warp per block row i (register-tiled products)
+      for (int i = j + 1 + warp; i < NB; i += nw) {
+        C acc[4][8];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
+        for (int k = j + 1; k <= i; ++k) {
+          const C* Wb = (k == i) ? Xs + (size_t)i * CBS : Ls + (size_t)lblk(i, k) * CBS;
+          warp_blk_nn_acc<C>(acc, Wb, Ls + (size_t)lblk(k, j) * CBS);
+        }
+        C* Tb = Ts + (size_t)(i - j - 1) * CBS;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) Tb[(4 * lr + x) * CP + 8 * lc + y] = acc[x][y];
       }
-      Ts[(size_t)(i - j - 1) * CBS + r * CP + lane] = acc;
+      __syncthreads();
+      // W_ij = -T_i X_jj
+      for (int i = j + 1 + warp; i < NB; i += nw) {
+        C acc[4][8];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
+        warp_blk_nn_acc<C>(acc, Ts + (size_t)(i - j - 1) * CBS, Xs + (size_t)j * CBS);
+        C* Wb = Ls + (size_t)lblk(i, j) * CBS;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) Wb[(4 * lr + x) * CP + 8 * lc + y] = -acc[x][y];
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int rr = warp; rr < nrow; rr += nw) {
-      const int i = j + 1 + rr / CBK, r = rr % CBK;
-      const C* Tr = Ts + (size_t)(i - j - 1) * CBS + r * CP;
-      const C* Xc = Xs + (size_t)j * CBS + lane;  // X_jj(t, lane), zero for t < lane
-      C acc = C(0);
-#pragma unroll 8
-      for (int t = 0; t < 32; ++t) acc = fma(Tr[t], Xc[t * CP], acc);
-      Ls[(size_t)lblk(i, j) * CBS + r * CP + lane] = -acc;
-    }
-    __syncthreads();
   }
   // M = R^-1 = D^-1 W^T: M(k, j) = W(j, k) / d_k for j >= k, 0 below
   for (int k = warp; k < l; k += nw) {
@@ -910,9 +975,10 @@ size_t orth_tc_workspace_bytes(int rows, int l, int sms) {
 }
 
 // The tensor-core apply pays for an explicit triangular inverse (on one SM)
-// and the bf16 splits; it wins once the block is tall: measured on GB300,
-// 2^20 x 128 (4.6x faster apply) but not 32768 x 256.
-bool orth_tc_pays(int rows, int l) { return (long long)rows >= 256LL * l; }
+// and the bf16 split of M; it wins once the block is tall.  Measured on
+// GB300 with the register-tiled inverse: from 64 l rows (32768 x 256 and
+// 2^20 x 128 both gain; the SIMT solve wins below).
+bool orth_tc_pays(int rows, int l) { return (long long)rows >= 64LL * l; }
 
 void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
                  DevStatus* st, int sms, cudaStream_t s) {
@@ -939,13 +1005,13 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
   const int* gate3 = &st->shifted;
   for (int pass = 1; pass <= 3; ++pass) {
     const int* gate = pass == 3 ? gate3 : nullptr;
-    launch_gram<float>(rows, l, Y, ldy, P, G, Gf, sms, gate, s, nullptr);
+    // the Gram kernel also writes the bf16 pair Yh + Yl of Y
+    launch_gram<float>(rows, l, Y, ldy, P, G, Gf, sms, gate, s, nullptr, Yh, Yl, l8);
     launch_chol<float>(l, G, Gf, M, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s,
                        nullptr, 1);
     // pass 3 runs only if pass 1 needed a shift (a device-side gate): the
-    // product then returns at once and leaves Y alone (the splits only fill
-    // scratch)
-    launch_split_bf16(rows, l, Y, ldy, Yh, Yl, l8, sms, s);
+    // product then returns at once and leaves Y alone (the split of M only
+    // fills scratch)
     launch_split_bf16(l, l, M, l, Mh, Ml, l8, sms, s);
     launch_tc_gemm(false, true, rows, l, l, Yh, l8, Yl, Mh, l8, Ml, Y, ldy, part, sms, st, s, 128, gate);
   }
@@ -961,9 +1027,9 @@ template void run_orth<float, float>(int, int, float*, int, double*, __nv_bfloat
 template void run_orth<double, double>(int, int, double*, int, double*, __nv_bfloat16*, int, void*,
                                        DevStatus*, int, cudaStream_t, const int*);
 template void launch_gram<float>(int, int, const float*, int, double*, double*, float*, int, const int*,
-                                 cudaStream_t, const int*);
+                                 cudaStream_t, const int*, __nv_bfloat16*, __nv_bfloat16*, int);
 template void launch_gram<double>(int, int, const double*, int, double*, double*, float*, int, const int*,
-                                  cudaStream_t, const int*);
+                                  cudaStream_t, const int*, __nv_bfloat16*, __nv_bfloat16*, int);
 
 // ------------------------------------------------------------ bf16 copy --
 template <typename T>

@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------ epilogue
     const int q = warp % 4;
     const int r = 32 * q + lane;
+    const bool yvec = (g.ldy % 4) == 0 && (((uintptr_t)g.Y) & 15) == 0;
     int j = 0;
     for (int t = t_first; t <= t_last; ++t, ++j) {
       const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
@@ -261,7 +262,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         if (store) {
-          if (whole) {
+          if (whole && yvec && c16 + 16 <= g.N) {
+            // 16-byte stores: a quarter of the store instructions (each still
+            // touches the 32 rows of the warp)
+#pragma unroll
+            for (int e = 0; e < 16; e += 4)
+              *reinterpret_cast<float4*>(dst + c16 + e) = make_float4(
+                  __uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+          } else if (whole) {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
               if (c16 + e < g.N) dst[c16 + e] = __uint_as_float(v[e]);
@@ -405,6 +413,17 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   g.W = (long long)g.T * g.KB;
   g.G = (int)(g.W < sms ? g.W : sms);
   if (g.G > TC_MAX_CTAS) g.G = TC_MAX_CTAS;
+  // short reductions (K <= 512): whole tiles per CTA when a divisor of the tile
+  // count keeps at least 3/4 of the SMs busy -- no split tiles, no fix-up
+  bool whole_tiles = false;
+  if (g.KB <= 8 && g.T >= sms) {
+    for (int gg = sms; gg * 4 >= sms * 3; --gg)
+      if (g.T % gg == 0) {
+        g.G = gg;
+        whole_tiles = true;
+        break;
+      }
+  }
   g.Npad = ceil_div(N, 16) * 16;
   g.NA = pow2_at_least(g.Npad);
   g.nchunk = ceil_div(N, 64);
@@ -461,8 +480,10 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
     RSVD_TC_LAUNCH(true, false, 2);
 #undef RSVD_TC_LAUNCH
   note_launch();
-  tc_fixup_kernel<<<dim3(g.T, bm / FIX_ROWS), 256, 0, s>>>(g, bm);
-  note_launch();
+  if (!whole_tiles) {
+    tc_fixup_kernel<<<dim3(g.T, bm / FIX_ROWS), 256, 0, s>>>(g, bm);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -563,15 +584,20 @@ __global__ void split_bf16_vec_kernel(int rows, int cols, const float* __restric
                                       __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb) {
   const int c4 = cols / 4;
   const long long total = (long long)rows * c4;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / c4), c = (int)(e % c4) * 4;
-    const float4 a = *reinterpret_cast<const float4*>(A + (size_t)r * lda + c);
+  // row-major walk: the row index advances by whole rows per grid stride, so
+  // no 64-bit division runs per element
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = (int)(e0 / c4), c = (int)(e0 % c4);
+  const int dr = (int)(stride / c4), dc = (int)(stride % c4);
+  for (long long e = e0; e < total; e += stride) {
+    const int cc = c * 4;
+    const float4 a = *reinterpret_cast<const float4*>(A + (size_t)r * lda + cc);
     __nv_bfloat162 h01 = __floats2bfloat162_rn(a.x, a.y), h23 = __floats2bfloat162_rn(a.z, a.w);
     uint2 hv;
     hv.x = *reinterpret_cast<uint32_t*>(&h01);
     hv.y = *reinterpret_cast<uint32_t*>(&h23);
-    *reinterpret_cast<uint2*>(Ah + (size_t)r * ldb + c) = hv;
+    *reinterpret_cast<uint2*>(Ah + (size_t)r * ldb + cc) = hv;
     if (Al) {
       const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
       __nv_bfloat162 l01 = __floats2bfloat162_rn(a.x - f01.x, a.y - f01.y);
@@ -579,7 +605,13 @@ __global__ void split_bf16_vec_kernel(int rows, int cols, const float* __restric
       uint2 lv;
       lv.x = *reinterpret_cast<uint32_t*>(&l01);
       lv.y = *reinterpret_cast<uint32_t*>(&l23);
-      *reinterpret_cast<uint2*>(Al + (size_t)r * ldb + c) = lv;
+      *reinterpret_cast<uint2*>(Al + (size_t)r * ldb + cc) = lv;
+    }
+    r += dr;
+    c += dc;
+    if (c >= c4) {
+      c -= c4;
+      ++r;
     }
   }
 }
@@ -588,7 +620,10 @@ void launch_split_bf16(int rows, int cols, const float* A, int lda, __nv_bfloat1
                        int sms, cudaStream_t s) {
   if ((long long)rows * cols == 0) return;
   const bool vec = (cols % 4 == 0) && (lda % 4 == 0) && (ldb % 4 == 0) && (((uintptr_t)A & 15) == 0);
-  const int blocks = sms * 8;
+  const long long units = vec ? (long long)rows * (cols / 4) : (long long)rows * cols;
+  long long want = (units + 4 * 256 - 1) / (4 * 256);  // about four units per thread
+  if (want < 1) want = 1;
+  const int blocks = (int)(want < sms * 8 ? want : sms * 8);
   if (vec)
     split_bf16_vec_kernel<<<blocks, 256, 0, s>>>(rows, cols, A, lda, Ah, Al, ldb);
   else

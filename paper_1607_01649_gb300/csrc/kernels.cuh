@@ -22,7 +22,8 @@ void launch_gemm_simt(bool trans, int M, int N, int K, const T* A, int lda, cons
 int gram_splits(int rows, int l, int sms);
 template <typename T>
 void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
-                 cudaStream_t s, const int* skip = nullptr);
+                 cudaStream_t s, const int* skip = nullptr, __nv_bfloat16* Yh = nullptr, __nv_bfloat16* Yl = nullptr,
+                 int lb = 0);
 size_t chol_smem_bytes(int l, size_t csize);
 size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize);
 template <typename T, typename C>

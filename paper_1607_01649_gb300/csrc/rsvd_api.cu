@@ -21,6 +21,7 @@ struct rsvd_handle_s {
   // learned controller: caller-owned parameters and the last decision
   const float* ctrl_theta;
   double ctrl_quantile, ctrl_safety;
+  int ctrl_fallback;  // 0: adaptive range finder, 1: fixed rank at the largest rank
   int ctrl_info[5];
   double ctrl_est[2];
 };
@@ -677,58 +678,73 @@ rsvd_status controlled_impl(rsvd_handle_t h, int m, int n, const float* A, int l
   e = cudaMemcpyAsync(&hb, L.blk, sizeof(hb), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "controller read: %s", cudaGetErrorString(e));
-  const int l = hb.l_hat < 1 ? 1 : (hb.l_hat > lmax ? lmax : hb.l_hat);
-  const int q = hb.q_hat;
-  // the fixed-rank solve with the chosen (l, q), all l triplets returned
-  rsvd_params fp = *p;
-  fp.k = l;
-  fp.p = 0;
-  fp.q = q;
-  fp.flags = RSVD_FLAG_RETURN_FULL_L;
-  DevStatus* fst;
-  if (p->prec == RSVD_MIXED_BF16) {
-    const MixedLayout M = mixed_layout(L.rest, m, n, l, l, h->sms);
-    fst = M.st;
-    cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
-    st = fixed_rank_mixed(h, m, n, A, lda, &fp, U, ldu, D, V, ldv, M, s);
-  } else {
-    const FixedLayout F = fixed_layout(L.rest, m, n, l, l, RSVD_F32, h->sms);
-    fst = F.st;
-    cudaMemsetAsync(F.st, 0, sizeof(DevStatus), s);
-    st = fixed_rank_simt<float, float>(h, m, n, A, lda, &fp, U, ldu, D, V, ldv, F, s);
-  }
-  if (st != RSVD_OK) return st;
-  // judge: E = A Gc - U (D (V^T Gc)), Gc = 16 columns of Philox stream 2
-  launch_gaussian(n, CTRL_NC, p->seed, 2u, 0, RSVD_DT_F32, L.G, CTRL_NC, s);
-  launch_thin_sketch(m, n, A, lda, L.G, L.Yp, L.Y, nullptr, h->sms, s);
-  launch_gemm_simt<float>(true, l, CTRL_NC, n, V, ldv, L.G, CTRL_NC, L.T, CTRL_NC, L.Tpart, h->sms, s);
-  launch_judge(m, l, L.Y, U, ldu, D, L.T, L.rpart, p->tol, h->ctrl_safety, L.blk, h->sms, s);
-  st = check_launch(h, "controller judge");
-  if (st != RSVD_OK) return st;
-  int fcode = 0;
-  e = cudaMemcpyAsync(&hb, L.blk, sizeof(hb), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&fcode, &fst->code, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "judge read: %s", cudaGetErrorString(e));
-  const double fro = sqrt(hb.fro2 > 0.0 ? hb.fro2 : 0.0);
+  int l = hb.l_hat < 1 ? 1 : (hb.l_hat > lmax ? lmax : hb.l_hat);
+  int q = hb.q_hat;
   h->ctrl_info[0] = l;
   h->ctrl_info[1] = q;
-  h->ctrl_info[2] = (hb.accepted && fcode == 0) ? 1 : 0;
   h->ctrl_info[3] = 0;
-  h->ctrl_est[0] = fro > 0.0 ? sqrt(hb.est2) / fro : 0.0;
-  h->ctrl_est[1] = fro > 0.0 ? hb.spec_bound / fro : 0.0;
-  if (hb.accepted && fcode == 0) {
+  // one fixed-rank solve with (l, q), all l triplets returned, and the judge:
+  // E = A Gc - U (D (V^T Gc)), Gc = 16 columns of Philox stream 2
+  int fcode = 0;
+  auto solve_and_judge = [&](int ll, int qq) -> rsvd_status {
+    rsvd_params fp = *p;
+    fp.k = ll;
+    fp.p = 0;
+    fp.q = qq;
+    fp.flags = RSVD_FLAG_RETURN_FULL_L;
+    DevStatus* fst;
+    rsvd_status r2;
+    if (p->prec == RSVD_MIXED_BF16) {
+      const MixedLayout M = mixed_layout(L.rest, m, n, ll, ll, h->sms);
+      fst = M.st;
+      cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
+      r2 = fixed_rank_mixed(h, m, n, A, lda, &fp, U, ldu, D, V, ldv, M, s);
+    } else {
+      const FixedLayout F = fixed_layout(L.rest, m, n, ll, ll, RSVD_F32, h->sms);
+      fst = F.st;
+      cudaMemsetAsync(F.st, 0, sizeof(DevStatus), s);
+      r2 = fixed_rank_simt<float, float>(h, m, n, A, lda, &fp, U, ldu, D, V, ldv, F, s);
+    }
+    if (r2 != RSVD_OK) return r2;
+    launch_gaussian(n, CTRL_NC, p->seed, 2u, 0, RSVD_DT_F32, L.G, CTRL_NC, s);
+    launch_thin_sketch(m, n, A, lda, L.G, L.Yp, L.Y, nullptr, h->sms, s);
+    launch_gemm_simt<float>(true, ll, CTRL_NC, n, V, ldv, L.G, CTRL_NC, L.T, CTRL_NC, L.Tpart, h->sms, s);
+    launch_judge(m, ll, L.Y, U, ldu, D, L.T, L.rpart, p->tol, h->ctrl_safety, L.blk, h->sms, s);
+    r2 = check_launch(h, "controller judge");
+    if (r2 != RSVD_OK) return r2;
+    cudaError_t e2 = cudaMemcpyAsync(&hb, L.blk, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&fcode, &fst->code, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+    if (e2 != cudaSuccess) return fail(h, RSVD_E_CUDA, "judge read: %s", cudaGetErrorString(e2));
+    const double fro = sqrt(hb.fro2 > 0.0 ? hb.fro2 : 0.0);
+    h->ctrl_info[2] = (hb.accepted && fcode == 0) ? 1 : 0;
+    h->ctrl_est[0] = fro > 0.0 ? sqrt(hb.est2) / fro : 0.0;
+    h->ctrl_est[1] = fro > 0.0 ? hb.spec_bound / fro : 0.0;
+    return RSVD_OK;
+  };
+  auto accept = [&]() -> rsvd_status {
     const int r = hb.rank;
     zero_tail(m, n, r, z.R, U, ldu, D, V, ldv, s);
     const double err = h->ctrl_est[0];
     if (rank_out) cudaMemcpyAsync(rank_out, &r, sizeof(int), cudaMemcpyHostToDevice, s);
     if (err_out) cudaMemcpyAsync(err_out, &err, sizeof(double), cudaMemcpyHostToDevice, s);
     h->ctrl_info[4] = r;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e));
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e2 != cudaSuccess) return fail(h, RSVD_E_CUDA, "synchronize: %s", cudaGetErrorString(e2));
     return check_launch(h, "rsvd_adaptive_tol (controller)");
-  }
-  if (l < z.R) {
+  };
+  if ((st = solve_and_judge(l, q)) != RSVD_OK) return st;
+  if (h->ctrl_info[2]) return accept();
+  if (l < lmax && h->ctrl_fallback == 1) {
+    // escalate: the largest rank allowed, at least two power steps
+    l = lmax;
+    q = q > 2 ? q : 2;
+    h->ctrl_info[0] = l;
+    h->ctrl_info[1] = q;
+    h->ctrl_info[3] = 2;
+    if ((st = solve_and_judge(l, q)) != RSVD_OK) return st;
+    if (h->ctrl_info[2]) return accept();
+  } else if (l < z.R) {
     // fall back: the blocked adaptive range finder in binary32, q = 0
     rsvd_params ap = *p;
     ap.prec = RSVD_F32;
@@ -784,6 +800,7 @@ rsvd_status rsvd_create(rsvd_handle_t* handle, int device) {
   h->ctrl_theta = nullptr;
   h->ctrl_quantile = 0.9;
   h->ctrl_safety = 0.8;
+  h->ctrl_fallback = 0;
   if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete h;
     return RSVD_E_CUDA;
@@ -1284,6 +1301,13 @@ rsvd_status rsvd_controller_attach(rsvd_handle_t handle, const float* theta, dou
   handle->ctrl_theta = theta;
   handle->ctrl_quantile = quantile;
   handle->ctrl_safety = safety;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_controller_fallback(rsvd_handle_t handle, int mode) {
+  if (!handle) return RSVD_E_INVALID;
+  if (mode != 0 && mode != 1) return fail(handle, RSVD_E_INVALID, "fallback mode must be 0 or 1");
+  handle->ctrl_fallback = mode;
   return RSVD_OK;
 }
 

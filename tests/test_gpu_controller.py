@@ -168,6 +168,14 @@ def test_controlled_solve_accept_fallback_and_cap(lib):
     assert code == lib.RSVD_OK and info["l"] == 16 and not info["accepted"] and info["fallback"]
     ref = oracle.adaptive_blocked(A64.astype(np.float32).astype(np.float64), tol, b=16, seed=seed, max_rank=64)
     assert rank == ref["rank"] and _true_rel_residual(A, U, D, V, rank) <= tol
+    # (b') the same rejection with the escalation fallback: one more fixed-rank
+    # solve at max_rank with q = 2, accepted and truncated to the step
+    lib.rsvd_controller_fallback(h, 1)
+    U, D, V, rank, err, code = lib.adaptive_tol(A, tol, seed=seed, max_rank=64, controller=True)
+    info = lib.rsvd_controller_last(h)
+    lib.rsvd_controller_fallback(h, 0)
+    assert code == lib.RSVD_OK and info["escalated"] and not info["fallback"] and info["accepted"]
+    assert info["l"] == 64 and info["q"] == 2 and rank == 24 and _true_rel_residual(A, U, D, V, rank) <= tol
     # (c) a slowly decaying spectrum misses the tolerance at the largest allowed rank
     P = _t(poly_decay_matrix_np(400, 300, seed=2, alpha=0.6))
     lib.rsvd_controller_attach(h, _t(_fixed_theta(15, 2)), 0.9, 0.8)

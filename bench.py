@@ -644,6 +644,10 @@ def run_batched(a):
         kernel_block_torch(p, plan.block(p), seed=seed)
     h = rs.handle(local)
     side = torch.cuda.Stream(device=dev)
+    # the launch variant (loads in flight per thread) is chosen by the
+    # library's autotuner on this batch before the graph is captured
+    variant, variant_ms = rs.batched_autotune(plan, BATCH_TOL, block=BATCH_B, seed=seed, stream=side)
+    side.synchronize()
     with torch.cuda.stream(side):
         for _ in range(a.warmup):
             code = rs.batched_run(plan, BATCH_TOL, block=BATCH_B, seed=seed, stream=side)
@@ -774,6 +778,8 @@ def run_batched(a):
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": batched_name(a), "graph": "one CUDA graph replay per step",
+                       "autotuned_variant": {"chosen": variant, "rows_cols_ahead": rs.rsvd_batched_variant_info(variant),
+                                             "ms_per_variant": variant_ms},
                        "l2": "inputs larger than L2 (%.2f GB of blocks; L2 129 MB)" % (4.0 * mn.sum() / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -183,6 +183,35 @@ rsvd_status rsvd_batched(rsvd_handle_t handle, int count, const int* m, const in
                          double* err_out, int* status_out, void* workspace, size_t ws_bytes,
                          rsvd_stream_t stream);
 
+/* Launch variants of rsvd_batched and their autotuner.  A variant fixes how
+ * many loads each thread keeps in flight in the passes over a problem's
+ * matrix (rows ahead in the column-owned passes, columns ahead in the row-
+ * owned ones); the arithmetic and its order are the same in every variant,
+ * so all variants produce bit-identical outputs and the choice affects only
+ * time.  rsvd_batched uses the handle's variant (the library default until
+ * one is set).
+ *   rsvd_batched_variants: *count = number of variants.
+ *   rsvd_batched_variant_info: rows and columns ahead of variant v.
+ *   rsvd_batched_set_variant: v in [0, count) or -1 (library default).
+ *   rsvd_batched_get_variant: the variant rsvd_batched will launch.
+ *   rsvd_batched_autotune: same arguments as rsvd_batched; runs the batch
+ *     twice per variant on `stream` (the second run timed with CUDA events),
+ *     stores the fastest variant in the handle, writes it to *variant_out
+ *     (host, may be NULL) and each variant's time in ms to ms_out (host
+ *     array of `count` variants, may be NULL).  It synchronizes, so it must
+ *     not be called while `stream` is being captured.  The outputs hold the
+ *     batch's result afterwards; a per-problem failure is returned as for
+ *     rsvd_batched with RSVD_FLAG_SYNC. */
+rsvd_status rsvd_batched_variants(int* count);
+rsvd_status rsvd_batched_variant_info(int variant, int* rows_ahead, int* cols_ahead);
+rsvd_status rsvd_batched_set_variant(rsvd_handle_t handle, int variant);
+rsvd_status rsvd_batched_get_variant(rsvd_handle_t handle, int* variant);
+rsvd_status rsvd_batched_autotune(rsvd_handle_t handle, int count, const int* m, const int* n,
+                                  const void* const* A, const int* lda, const rsvd_params* params,
+                                  void* const* U, double* const* D, void* const* V, int* rank_out,
+                                  double* err_out, int* status_out, void* workspace, size_t ws_bytes,
+                                  rsvd_stream_t stream, float* ms_out, int* variant_out);
+
 /* Reads the device status word of the last solve that used `workspace`
  * (synchronizes `stream` first).  *status receives an rsvd_status value. */
 rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status,

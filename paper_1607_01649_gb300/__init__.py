@@ -51,7 +51,8 @@ EXPORTED = [
     "rsvd_sketch_noalloc", "rsvd_batched_workspace_size", "rsvd_batched",
     "rsvd_probe_workspace_size", "rsvd_probe_features", "rsvd_mlp_workspace_size", "rsvd_mlp_forward",
     "rsvd_mlp_grad", "rsvd_mlp_train_step", "rsvd_controller_attach", "rsvd_controller_last",
-    "rsvd_controller_fallback",
+    "rsvd_controller_fallback", "rsvd_batched_variants", "rsvd_batched_variant_info", "rsvd_batched_set_variant",
+    "rsvd_batched_get_variant", "rsvd_batched_autotune",
 ]
 
 CTRL_D_IN = 17
@@ -110,6 +111,11 @@ def load():
         "rsvd_sketch_noalloc": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp],
         "rsvd_batched_workspace_size": [vp, i, P, ctypes.POINTER(sz)],
         "rsvd_batched": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp],
+        "rsvd_batched_variants": [ctypes.POINTER(i)],
+        "rsvd_batched_variant_info": [i, ctypes.POINTER(i), ctypes.POINTER(i)],
+        "rsvd_batched_set_variant": [vp, i],
+        "rsvd_batched_get_variant": [vp, ctypes.POINTER(i)],
+        "rsvd_batched_autotune": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp, vp],
         "rsvd_probe_workspace_size": [vp, i, i, ctypes.POINTER(sz)],
         "rsvd_probe_features": [vp, i, i, vp, i, u64, vp, vp, vp, sz, vp],
         "rsvd_mlp_workspace_size": [vp, i, ctypes.POINTER(sz)],
@@ -198,6 +204,40 @@ def rsvd_batched(h, count, m, n, A, lda, params, U, D, V, rank_out, err_out, sta
     return load().rsvd_batched(h, count, _ptr(m), _ptr(n), _ptr(A), _ptr(lda), ctypes.byref(params), _ptr(U),
                                _ptr(D), _ptr(V), _ptr(rank_out), _ptr(err_out), _ptr(status_out), _ptr(ws),
                                ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def rsvd_batched_variants():
+    out = ctypes.c_int()
+    _check(load().rsvd_batched_variants(ctypes.byref(out)), None)
+    return out.value
+
+
+def rsvd_batched_variant_info(v):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().rsvd_batched_variant_info(int(v), ctypes.byref(a), ctypes.byref(b)), None)
+    return a.value, b.value
+
+
+def rsvd_batched_set_variant(h, v):
+    return _check(load().rsvd_batched_set_variant(h, int(v)), h)
+
+
+def rsvd_batched_get_variant(h):
+    out = ctypes.c_int()
+    _check(load().rsvd_batched_get_variant(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def rsvd_batched_autotune(h, count, m, n, A, lda, params, U, D, V, rank_out, err_out, status_out, ws, stream=None):
+    """Returns (status, chosen variant, list of per-variant ms)."""
+    nv = rsvd_batched_variants()
+    ms = (ctypes.c_float * nv)()
+    var = ctypes.c_int(-1)
+    code = load().rsvd_batched_autotune(h, count, _ptr(m), _ptr(n), _ptr(A), _ptr(lda), ctypes.byref(params),
+                                        _ptr(U), _ptr(D), _ptr(V), _ptr(rank_out), _ptr(err_out), _ptr(status_out),
+                                        _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream), ms,
+                                        ctypes.byref(var))
+    return code, var.value, list(ms)
 
 
 def rsvd_query_status(h, ws, stream=None):
@@ -445,6 +485,20 @@ def batched_run(plan, tol, block=16, seed=0, flags=0, stream=None):
         plan.ws = _empty_ws(rsvd_batched_workspace_size(h, plan.count, prm), plan.A.device)
     return rsvd_batched(h, plan.count, plan.m, plan.n, plan.a_ptr, plan.lda, prm, plan.u_ptr, plan.d_ptr,
                         plan.v_ptr, plan.rank, plan.err, plan.status, plan.ws, stream)
+
+
+def batched_autotune(plan, tol, block=16, seed=0, stream=None):
+    """Time every launch variant of rsvd_batched on a BatchPlan and keep the
+    fastest for this device's handle.  Returns (variant, per-variant ms)."""
+    h = handle(plan.A.device.index)
+    prm = make_params(0, 0, 0, seed, RSVD_F32, 0, tol=tol, block=block, max_rank=plan.R)
+    if plan.ws is None:
+        plan.ws = _empty_ws(rsvd_batched_workspace_size(h, plan.count, prm), plan.A.device)
+    code, var, ms = rsvd_batched_autotune(h, plan.count, plan.m, plan.n, plan.a_ptr, plan.lda, prm, plan.u_ptr,
+                                          plan.d_ptr, plan.v_ptr, plan.rank, plan.err, plan.status, plan.ws, stream)
+    if code not in (RSVD_OK, RSVD_E_NOT_CONVERGED, RSVD_E_INVALID, RSVD_E_BREAKDOWN, RSVD_E_NONFINITE):
+        raise RsvdError(code, last_error(h))
+    return var, ms
 
 
 def batched(blocks, tol, block=16, max_rank=64, seed=0):

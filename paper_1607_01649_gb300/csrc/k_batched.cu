@@ -36,6 +36,7 @@ constexpr int BB = 16;       // largest block width b (row stride of Y, G, C)
 constexpr int RMAX = 64;     // rank cap
 constexpr int NMAX = 1024;   // largest m, n
 constexpr int CHUNK = 64;    // binary32 partial-sum length before a binary64 fold
+constexpr int YLD = BB + 1;  // odd row stride of the copy of Y being orthonormalized
 
 // dynamic shared memory, in floats
 constexpr int SQ_OFF = 0;                   // Y / Q_new, [i][16]   (NMAX x 16)
@@ -84,10 +85,29 @@ __device__ __forceinline__ void lds16(const float* p, float (&v)[BB]) {
   }
 }
 
+// Swizzled 16-wide rows (G and C): element (j, c) at j 16 + 4 ((c / 4) xor
+// ((j / 2) mod 4)) + c mod 4.  Rows are 64 bytes, so without the swizzle the
+// 16-byte chunks that 8 consecutive rows read at the same c fall in 2 bank
+// groups (4-way conflicts); with it they fall in 8 distinct ones.
+__device__ __forceinline__ int swz(int j, int c) { return j * BB + ((((c >> 2) ^ (j >> 1)) & 3) << 2) + (c & 3); }
+
+__device__ __forceinline__ void lds16s(const float* base, int j, float (&v)[BB]) {
+  const float* p = base + j * BB;
+  const int x = (j >> 1) & 3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 t = *reinterpret_cast<const float4*>(p + 4 * (q ^ x));
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+
 // ------------------------------------------------------------ Gaussians --
-// G[j][c] for c < bb: column col0 + c of Philox stream 1 under key (k0, k1);
-// element 4 g + t of a column is Box-Muller output t of counter (g, col, 1, 0).
-// Columns bb .. 15 are zero.
+// G(j, c) for c < bb (swizzled rows): column col0 + c of Philox stream 1
+// under key (k0, k1); element 4 g + t of a column is Box-Muller output t of
+// counter (g, col, 1, 0).  Columns bb .. 15 are zero.
 __device__ void gen_gauss(int n, int bb, int col0, uint32_t k0, uint32_t k1, float* sG) {
   const int groups = (n + 3) >> 2;
   for (int e = threadIdx.x; e < groups * BB; e += BT) {
@@ -100,7 +120,7 @@ __device__ void gen_gauss(int n, int bb, int col0, uint32_t k0, uint32_t k1, flo
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if (4 * g + t < n) sG[(4 * g + t) * BB + c] = z[t];
+      if (4 * g + t < n) sG[swz(4 * g + t, c)] = z[t];
   }
   __syncthreads();
 }
@@ -140,7 +160,7 @@ __device__ __forceinline__ int scatter_index64(int lane) {
 //   y(i, c) += a G(j, c)                           (AG)
 // y overwrites the rows of sQ the warp owns, after their q has been read.
 // Returns ||a||_F^2 (binary64; the same value in every thread).
-template <bool UPD, bool AG>
+template <bool UPD, bool AG, int PD>
 __device__ double pass_rows(int m, int n, const float* src, int lds, float* dst, float* sQ, const float* sC,
                             const float* sG, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -158,33 +178,61 @@ __device__ double pass_rows(int m, int n, const float* src, int lds, float* dst,
     float nrm = 0.f;
     const float* s0 = src + (size_t)i0 * lds;
     float* d0 = UPD ? dst + (size_t)i0 * n : nullptr;
-    for (int j = lane; j < n; j += 32) {
-      float a[4];
+    // double-buffered loads: the next PD columns' values are loaded while
+    // the current PD are processed
+    float nb[PD][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = r < rows ? s0[(size_t)r * lds + j] : 0.f;
-      if (UPD) {
-        float cj[BB];
-        lds16(sC + j * BB, cj);
+    for (int d = 0; d < PD; ++d) {
+      const int j = lane + 32 * d;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (r < rows) {
-            float s = 0.f;
+      for (int r = 0; r < 4; ++r) nb[d][r] = (r < rows && j < n) ? s0[(size_t)r * lds + j] : 0.f;
+    }
+    for (int j0 = lane; j0 < n; j0 += 32 * PD) {
+      float cur[PD][4];
 #pragma unroll
-            for (int c = 0; c < BB; ++c) s = fmaf(q[r][c], cj[c], s);
-            a[r] -= s;
-            d0[(size_t)r * n + j] = a[r];
-          }
+      for (int d = 0; d < PD; ++d)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) cur[d][r] = nb[d][r];
+      if (j0 + 32 * PD < n) {
+#pragma unroll
+        for (int d = 0; d < PD; ++d) {
+          const int jn = j0 + 32 * (PD + d);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) nb[d][r] = (r < rows && jn < n) ? s0[(size_t)r * lds + jn] : 0.f;
         }
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) nrm = fmaf(a[r], a[r], nrm);
-      if (AG) {
-        float g[BB];
-        lds16(sG + j * BB, g);
+      for (int d = 0; d < PD; ++d) {
+        const int j = j0 + 32 * d;
+        if (j < n) {
+          float a[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 4; ++r) a[r] = cur[d][r];
+          if (UPD) {
+            float cj[BB];
+            lds16s(sC, j, cj);
 #pragma unroll
-          for (int c = 0; c < BB; ++c) y[r * BB + c] = fmaf(a[r], g[c], y[r * BB + c]);
+            for (int r = 0; r < 4; ++r) {
+              if (r < rows) {
+                float s = 0.f;
+#pragma unroll
+                for (int c = 0; c < BB; ++c) s = fmaf(q[r][c], cj[c], s);
+                a[r] -= s;
+                d0[(size_t)r * n + j] = a[r];
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) nrm = fmaf(a[r], a[r], nrm);
+          if (AG) {
+            float g[BB];
+            lds16s(sG, j, g);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < BB; ++c) y[r * BB + c] = fmaf(a[r], g[c], y[r * BB + c]);
+          }
+        }
       }
     }
     norm += (double)nrm;
@@ -204,35 +252,52 @@ __device__ double pass_rows(int m, int n, const float* src, int lds, float* dst,
 
 // ---------------------------------------------------- column-owned passes --
 // The CTA is split into `groups` row groups of `ncol` threads (ncol = 32, 64,
-// 128 or 256: the smallest power-of-two multiple of 32 covering n, at most
-// 256); thread tj of group g owns column j0 + tj and rows g, g + groups, ...
+// 128 or 256, groups = 256 / ncol); thread tj of group g owns column j0 + tj
+// of each column chunk and rows g, g + groups, ...  The split is the one with
+// the fewest row visits per thread, ceil(n / ncol) ceil(m / groups), plus
+// the cost of a partial-sum exchange per chunk when groups > 1.
 struct ColSplit {
   int ncol, groups;
 };
-__device__ __forceinline__ ColSplit col_split(int n) {
-  int ncol = 32;
-  while (ncol < n && ncol < BT) ncol <<= 1;
-  return ColSplit{ncol, BT / ncol};
+__device__ __forceinline__ ColSplit col_split(int m, int n) {
+  ColSplit best{BT, 1};
+  int bc = 0x7fffffff;
+  for (int ncol = BT; ncol >= 32; ncol >>= 1) {
+    const int groups = BT / ncol;
+    const int cost = ((n + ncol - 1) / ncol) * ((m + groups - 1) / groups + (groups > 1 ? 24 : 0));
+    if (cost < bc) {
+      bc = cost;
+      best = ColSplit{ncol, groups};
+    }
+  }
+  return best;
 }
 
-// UPD = false (pass C):  sC[j][c] = sum_i Q_new(i, c) src(i, j)
-// UPD = true  (pass U1): with C1 = sC on entry,
+// UPD = false (pass C):  C(j, c) = sum_i Q_new(i, c) src(i, j)
+// UPD = true  (pass U1): with C1 = C on entry,
 //     dst(i, j) = src(i, j) - sum_c Q_new(i, c) C1(c, j),
-//     sC[j][c]  = sum_i Q_new(i, c) dst(i, j)                  (C2)
+//     C(j, c)   = sum_i Q_new(i, c) dst(i, j)                  (C2)
 //     Bt[j][k0 + c] = C1(c, j) + C2(c, j)   for c < bb
-// Row-group partial sums meet in `part` (binary64, in the sG region).
-template <bool UPD>
+// C lives in sC (swizzled rows).  Binary32 sums over CHUNK rows are folded
+// into binary64; row-group partial sums meet in `part` (binary64, in the sG
+// region).  Each thread keeps PF rows' loads in flight; PF changes only the
+// load schedule, never the order of the arithmetic.
+template <bool UPD, int PF>
 __device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, const float* sQ, float* sC,
                           double* part, float* Bt, int k0, int bb) {
-  const ColSplit cs = col_split(n);
+  const ColSplit cs = col_split(m, n);
   const int g = threadIdx.x / cs.ncol, tj = threadIdx.x % cs.ncol;
+  const int G = cs.groups;
   for (int j0 = 0; j0 < n; j0 += cs.ncol) {
     const int j = j0 + tj;
     const bool live = j < n;
     float c1[BB];
     if (UPD) {
+      if (live) lds16s(sC, j, c1);
+      else {
 #pragma unroll
-      for (int c = 0; c < BB; ++c) c1[c] = live ? sC[j * BB + c] : 0.f;
+        for (int c = 0; c < BB; ++c) c1[c] = 0.f;
+      }
     }
     double acc64[BB];
     float acc[BB];
@@ -243,33 +308,58 @@ __device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, c
     }
     if (live) {
       int cnt = 0;
-      for (int i = g; i < m; i += cs.groups) {
-        float a = src[(size_t)i * lds + j];
-        float qi[BB];
-        lds16(sQ + i * BB, qi);
-        if (UPD) {
-          float s = 0.f;
+      const float* sp = src + j;
+      // double-buffered loads: the next PF rows are loaded while the current
+      // PF are processed
+      float nb[PF];
 #pragma unroll
-          for (int c = 0; c < BB; ++c) s = fmaf(qi[c], c1[c], s);
-          a -= s;
-          dst[(size_t)i * n + j] = a;
+      for (int u = 0; u < PF; ++u) {
+        const int i = g + u * G;
+        nb[u] = i < m ? sp[(size_t)i * lds] : 0.f;
+      }
+      for (int i0 = g; i0 < m; i0 += PF * G) {
+        float cur[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) cur[u] = nb[u];
+        if (i0 + PF * G < m) {
+#pragma unroll
+          for (int u = 0; u < PF; ++u) {
+            const int i = i0 + (PF + u) * G;
+            nb[u] = i < m ? sp[(size_t)i * lds] : 0.f;
+          }
         }
 #pragma unroll
-        for (int c = 0; c < BB; ++c) acc[c] = fmaf(qi[c], a, acc[c]);
-        if (++cnt == CHUNK) {
+        for (int u = 0; u < PF; ++u) {
+          const int i = i0 + u * G;
+          if (i < m) {
+            float av = cur[u];
+            float qi[BB];
+            lds16(sQ + i * BB, qi);
+            if (UPD) {
+              float s = 0.f;
 #pragma unroll
-          for (int c = 0; c < BB; ++c) {
-            acc64[c] += (double)acc[c];
-            acc[c] = 0.f;
+              for (int c = 0; c < BB; ++c) s = fmaf(qi[c], c1[c], s);
+              av -= s;
+              dst[(size_t)i * n + j] = av;
+            }
+#pragma unroll
+            for (int c = 0; c < BB; ++c) acc[c] = fmaf(qi[c], av, acc[c]);
+            if (++cnt == CHUNK) {
+#pragma unroll
+              for (int c = 0; c < BB; ++c) {
+                acc64[c] += (double)acc[c];
+                acc[c] = 0.f;
+              }
+              cnt = 0;
+            }
           }
-          cnt = 0;
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < BB; ++c) acc64[c] += (double)acc[c];
-    if (cs.groups > 1) {  // then ncol >= n and this loop runs once
-      __syncthreads();    // the sG region is free for the partials
+    if (G > 1) {
+      __syncthreads();  // the sG region is free for the partials; earlier chunks' sums are read
       if (live) {
 #pragma unroll
         for (int c = 0; c < BB; ++c) part[((size_t)g * cs.ncol + tj) * BB + c] = acc64[c];
@@ -278,15 +368,15 @@ __device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, c
       if (g == 0 && live) {
 #pragma unroll
         for (int c = 0; c < BB; ++c) {
-          double s = 0.0;
-          for (int h = 0; h < cs.groups; ++h) s += part[((size_t)h * cs.ncol + tj) * BB + c];
-          acc64[c] = s;
+          double sum = 0.0;
+          for (int h = 0; h < G; ++h) sum += part[((size_t)h * cs.ncol + tj) * BB + c];
+          acc64[c] = sum;
         }
       }
     }
     if (g == 0 && live) {
 #pragma unroll
-      for (int c = 0; c < BB; ++c) sC[j * BB + c] = (float)acc64[c];
+      for (int c = 0; c < BB; ++c) sC[swz(j, c)] = (float)acc64[c];
       if (UPD) {
 #pragma unroll
         for (int c = 0; c < BB; ++c)
@@ -339,8 +429,9 @@ __device__ void gram16(int rows, int l, const float* Y, int ldy, double* g64, do
   __syncthreads();
 }
 
-// Gram of a rows x l block (l <= 64) in global memory with row stride ldy:
-// one thread per upper-triangle entry, binary32 partials of 64 rows.
+// Gram of a rows x l block (l <= 64, shared or global memory, row stride
+// ldy): one thread per upper-triangle entry; four binary32 partial sums over
+// interleaved rows of each 64-row chunk, folded into binary64 per chunk.
 __device__ void gram_wide(int rows, int l, const float* Y, int ldy, double* g64) {
   const int nent = l * (l + 1) / 2;
   for (int e = threadIdx.x; e < nent; e += BT) {
@@ -352,10 +443,18 @@ __device__ void gram_wide(int rows, int l, const float* Y, int ldy, double* g64)
     const int j = i + rem;
     double acc = 0.0;
     for (int r0 = 0; r0 < rows; r0 += CHUNK) {
-      float part = 0.f;
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
       const int r1 = min(rows, r0 + CHUNK);
-      for (int r = r0; r < r1; ++r) part = fmaf(Y[(size_t)r * ldy + i], Y[(size_t)r * ldy + j], part);
-      acc += (double)part;
+      int r = r0;
+      for (; r + 3 < r1; r += 4) {
+        const float* y = Y + (size_t)r * ldy;
+        p0 = fmaf(y[i], y[j], p0);
+        p1 = fmaf(y[ldy + i], y[ldy + j], p1);
+        p2 = fmaf(y[2 * ldy + i], y[2 * ldy + j], p2);
+        p3 = fmaf(y[3 * ldy + i], y[3 * ldy + j], p3);
+      }
+      for (; r < r1; ++r) p0 = fmaf(Y[(size_t)r * ldy + i], Y[(size_t)r * ldy + j], p0);
+      acc += ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
     }
     g64[i * l + j] = acc;
     g64[j * l + i] = acc;
@@ -397,10 +496,16 @@ __device__ bool chol_warp(int l, const double* g64, float* L, float* dinv) {
       for (int i = k + 1 + lane; i < l; i += 32) L[i * l + k] *= rp;
       __syncwarp();
       if (lane == 0) L[k * l + k] = akk * rp;
-      const int nr = l - k - 1;
-      for (int e = lane; e < nr * nr; e += 32) {
-        const int i = k + 1 + e / nr, j = k + 1 + e % nr;
-        if (j <= i) L[i * l + j] = fmaf(-L[i * l + k], L[j * l + k], L[i * l + j]);
+      // trailing update, lane j owning column j: row i of the update reads
+      // L(i, k) once for the whole warp and L(i, j) from consecutive banks
+      for (int jb = k + 1; jb < l; jb += 32) {
+        const int j = jb + lane;
+        const bool act = j < l;
+        const float ljk = act ? L[j * l + k] : 0.f;
+        for (int i = jb; i < l; ++i) {
+          const float lik = L[i * l + k];
+          if (act && j <= i) L[i * l + j] = fmaf(-lik, ljk, L[i * l + j]);
+        }
       }
       __syncwarp();
     }
@@ -416,6 +521,7 @@ __device__ void apply_rows(int rows, int l, float* Y, int ldy, const float* L, c
     float* y = Y + (size_t)r * ldy;
     for (int c = 0; c < l; ++c) {
       float s = y[c] * dinv[c];
+#pragma unroll 4
       for (int k = 0; k < c; ++k) s = fmaf(-y[k], L[c * l + k], s);
       y[c] = s / L[c * l + c];
     }
@@ -479,6 +585,7 @@ __device__ void lu_rows(int rows, int l, float* Y, int ldy, float* U, unsigned c
       float* yi = Y + (size_t)i * ldy;
       const float lik = yi[k] * rpiv;
       yi[k] = lik;
+#pragma unroll 4
       for (int j = k + 1; j < l; ++j) yi[j] = fmaf(-lik, yp[j], yi[j]);
     }
     __syncthreads();
@@ -523,39 +630,42 @@ __device__ bool lu_cholqr2(int rows, int l, float* Y, int ldy, double* g64, doub
   for (int pass = 0; pass < 2; ++pass) {
     if (!chol_factor<GLOBAL>(rows, l, Y, ldy, g64, wpart, L, dinv, s_flag)) return false;
     if (R) {
-      // R <- (L^T D^-1) R, both upper, in place: a thread per column; going
-      // top-down, row i reads only rows k >= i of its column, still the old ones
+      // R <- (L^T D^-1) R, both upper: a thread per entry into the scratch
+      // Ulu (free once the LU's U was copied to R), then copied back
       for (int e = threadIdx.x; e < l * l; e += BT) {
         const int i = e / l, j = e % l;
         Rt[e] = (i <= j && dinv[j] > 0.f) ? L[j * l + i] / dinv[j] : 0.f;
       }
       __syncthreads();
-      for (int j = threadIdx.x; j < l; j += BT) {
-        for (int i = 0; i < l; ++i) {
-          float s = 0.f;
-          for (int k = i; k <= j; ++k) s = fmaf(Rt[i * l + k], R[k * l + j], s);
-          R[i * l + j] = i <= j ? s : 0.f;
-        }
+      for (int e = threadIdx.x; e < l * l; e += BT) {
+        const int i = e / l, j = e % l;
+        float s = 0.f;
+        for (int k = i; k <= j; ++k) s = fmaf(Rt[i * l + k], R[k * l + j], s);
+        Ulu[e] = s;
       }
+      __syncthreads();
+      for (int e = threadIdx.x; e < l * l; e += BT) R[e] = Ulu[e];
     }
     apply_rows(rows, l, Y, ldy, L, dinv);
   }
   return true;
 }
 
-// Y -= Q (Q^T Y) for the rows x 16 block Y in shared memory (row stride 16)
-// and the rank columns of Q stored transposed (Qt[k][i], row stride NMAX);
-// P (rank x 16) is scratch.  A warp per k forms P, a thread per row applies it.
-__device__ void project_out(int rows, int rank, const float* Qt, float* Y, float* P) {
+// Y -= Q (Q^T Y) for the rows x 16 block Y in shared memory (row stride ldy,
+// odd, so that a thread per row reads conflict-free) and the rank columns of
+// Q stored transposed (Qt[k][i], row stride NMAX); P (rank x 16, 16-byte
+// aligned) is scratch.  A warp per k forms P, a thread per row applies it.
+__device__ void project_out(int rows, int rank, const float* Qt, float* Y, int ldy, float* P) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = warp; k < rank; k += BW) {
     float acc[BB];
 #pragma unroll
     for (int c = 0; c < BB; ++c) acc[c] = 0.f;
+    const float* qk = Qt + (size_t)k * NMAX;
+#pragma unroll 2
     for (int i = lane; i < rows; i += 32) {
-      const float qv = Qt[(size_t)k * NMAX + i];
-      float yi[BB];
-      lds16(Y + i * BB, yi);
+      const float qv = qk[i];
+      const float* yi = Y + i * ldy;
 #pragma unroll
       for (int c = 0; c < BB; ++c) acc[c] = fmaf(qv, yi[c], acc[c]);
     }
@@ -572,6 +682,7 @@ __device__ void project_out(int rows, int rank, const float* Qt, float* Y, float
     float acc[BB];
 #pragma unroll
     for (int c = 0; c < BB; ++c) acc[c] = 0.f;
+#pragma unroll 4
     for (int k = 0; k < rank; ++k) {
       const float qv = Qt[(size_t)k * NMAX + i];
       float pk[BB];
@@ -579,50 +690,61 @@ __device__ void project_out(int rows, int rank, const float* Qt, float* Y, float
 #pragma unroll
       for (int c = 0; c < BB; ++c) acc[c] = fmaf(qv, pk[c], acc[c]);
     }
+    float* yi = Y + i * ldy;
 #pragma unroll
-    for (int c = 0; c < BB; ++c) Y[i * BB + c] -= acc[c];
+    for (int c = 0; c < BB; ++c) yi[c] -= acc[c];
   }
   __syncthreads();
 }
 
 // One-sided Jacobi on the columns of X (l x l, column c at X + c l),
 // accumulating the rotations in J (same layout, identity on entry).  Round-
-// robin pair order, one warp per pair, at most 30 sweeps.
+// robin pair order, one half-warp per pair (all pairs of a step at once for
+// l <= 32), at most 30 sweeps.
 __device__ void jacobi_cols(int l, float* X, float* J, int* s_cnt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, hl = lane & 15;
   const int P = (l & 1) ? l + 1 : l;
   const float tol = 4.f * (float)l * 5.9604644775390625e-08f;
   for (int sweep = 0; sweep < 30; ++sweep) {
     if (threadIdx.x == 0) *s_cnt = 0;
     __syncthreads();
     for (int step = 0; step < P - 1; ++step) {
-      for (int pr = warp; pr < P / 2; pr += BW) {
-        const int ia = pr == 0 ? 0 : 1 + (pr - 1 + step) % (P - 1);
-        const int qq = P - 1 - pr;
-        const int ib = 1 + (qq - 1 + step) % (P - 1);
-        if (ia >= l || ib >= l) continue;
+      // the loop is uniform over the warp: both halves run every round and
+      // take part in every shuffle
+      for (int base = 2 * warp; base < P / 2; base += 2 * BW) {
+        const int pr = base + half;
+        int ia = 0, ib = 0;
+        if (pr < P / 2) {
+          ia = pr == 0 ? 0 : 1 + (pr - 1 + step) % (P - 1);
+          const int qq = P - 1 - pr;
+          ib = 1 + (qq - 1 + step) % (P - 1);
+        }
+        const bool live = pr < P / 2 && ia < l && ib < l;
         float* xa = X + ia * l;
         float* xb = X + ib * l;
         float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < l; i += 32) {
-          const float a = xa[i], b = xb[i];
-          al = fmaf(a, a, al);
-          be = fmaf(b, b, be);
-          ga = fmaf(a, b, ga);
+        if (live) {
+          for (int i = hl; i < l; i += 16) {
+            const float a = xa[i], b = xb[i];
+            al = fmaf(a, a, al);
+            be = fmaf(b, b, be);
+            ga = fmaf(a, b, ga);
+          }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 8; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+        if (live && ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
           const float zeta = (be - al) / (2.f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
           const float cs = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = cs * t;
           float* ja = J + ia * l;
           float* jb = J + ib * l;
-          for (int i = lane; i < l; i += 32) {
+          for (int i = hl; i < l; i += 16) {
             const float a = xa[i], b = xb[i];
             xa[i] = cs * a - sn * b;
             xb[i] = sn * a + cs * b;
@@ -630,7 +752,7 @@ __device__ void jacobi_cols(int l, float* X, float* J, int* s_cnt) {
             ja[i] = cs * p - sn * w;
             jb[i] = sn * p + cs * w;
           }
-          if (lane == 0) atomicAdd(s_cnt, 1);
+          if (hl == 0) atomicAdd(s_cnt, 1);
         }
       }
       __syncthreads();
@@ -651,6 +773,7 @@ struct Work {
   unsigned char* used;  // NMAX row flags of the LU
 };
 
+template <int PF, int PD>
 __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R, int b, float* base, float* sm,
                           const Work& W, int* rank_out, double* err_out, int* status_out, DevStatus* st) {
   double* red = W.red;
@@ -667,6 +790,8 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
   float* sU = sL + BB * BB;
   float* sDinv = sU + BB * BB;
   double* wpart = reinterpret_cast<double*>(sG);  // 8 x 16 x 16 binary64 Gram partials
+  float* Yo = sC;                                 // m x YLD copy of Y during the orthonormalization
+  float* sPj = sG + 2 * BW * BB * BB;             // rank x 16 projection scratch, after wpart
   const int rmax = min(R, min(m, n));
   const uint64_t key = seed + (uint64_t)p;
   const uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
@@ -675,7 +800,7 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
   // first pass: Y = A G_0 and ||A||_F^2
   int bb = min(b, rmax);
   gen_gauss(n, bb, 0, k0, k1, sG);
-  const double a2 = pass_rows<false, true>(m, n, P.A, P.lda, nullptr, sQ, sC, sG, red);
+  const double a2 = pass_rows<false, true, PD>(m, n, P.A, P.lda, nullptr, sQ, sC, sG, red);
   const double eps2 = tol * tol * a2;
   double r2 = a2;
   const float* src = P.A;
@@ -687,9 +812,14 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
       break;
     }
     bb = min(b, rmax - rank);
-    if (rank > 0) project_out(m, rank, Qt, sQ, sP);
+    // the orthonormalization works on a copy of Y with the odd row stride
+    // YLD (in the sC and sP regions, free until the next pass): every thread-
+    // per-row walk below is then free of bank conflicts
+    for (int e = tid; e < m * BB; e += BT) Yo[(e / BB) * YLD + e % BB] = sQ[e];
+    __syncthreads();
+    if (rank > 0) project_out(m, rank, Qt, Yo, YLD, sPj);
     // Q_new = CholeskyQR2(Y)
-    if (!lu_cholqr2<false>(m, bb, sQ, BB, g16, wpart, sL, sDinv, sU, nullptr, nullptr, W.used, W.rv, W.ri,
+    if (!lu_cholqr2<false>(m, bb, Yo, YLD, g16, wpart, sL, sDinv, sU, nullptr, nullptr, W.used, W.rv, W.ri,
                            W.flag)) {
       status = RSVD_E_BREAKDOWN;
       break;
@@ -699,31 +829,32 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
       // to kappa(Y): project once more and renormalize (block Gram-Schmidt,
       // twice), so that Q^T Q_new stays at the binary32 round-off level
       for (int e = tid; e < m * BB; e += BT)
-        if (e % BB >= bb) sQ[e] = 0.f;
+        if (e % BB >= bb) Yo[(e / BB) * YLD + e % BB] = 0.f;
       __syncthreads();
-      project_out(m, rank, Qt, sQ, sP);
-      if (!chol_factor<false>(m, bb, sQ, BB, g16, wpart, sL, sDinv, W.flag)) {
+      project_out(m, rank, Qt, Yo, YLD, sPj);
+      if (!chol_factor<false>(m, bb, Yo, YLD, g16, wpart, sL, sDinv, W.flag)) {
         status = RSVD_E_BREAKDOWN;
         break;
       }
-      apply_rows(m, bb, sQ, BB, sL, sDinv);
+      apply_rows(m, bb, Yo, YLD, sL, sDinv);
     }
     for (int e = tid; e < m * BB; e += BT) {
       const int i = e / BB, c = e % BB;
-      if (c >= bb) sQ[e] = 0.f;
-      else Qt[(size_t)(rank + c) * NMAX + i] = sQ[e];
+      const float v = c < bb ? Yo[i * YLD + c] : 0.f;
+      sQ[e] = v;
+      if (c < bb) Qt[(size_t)(rank + c) * NMAX + i] = v;
     }
     __syncthreads();
-    pass_cols<false>(m, n, src, lds, nullptr, sQ, sC, reinterpret_cast<double*>(sG), Bt, rank, bb);
-    pass_cols<true>(m, n, src, lds, Aj, sQ, sC, reinterpret_cast<double*>(sG), Bt, rank, bb);
+    pass_cols<false, PF>(m, n, src, lds, nullptr, sQ, sC, reinterpret_cast<double*>(sG), Bt, rank, bb);
+    pass_cols<true, PF>(m, n, src, lds, Aj, sQ, sC, reinterpret_cast<double*>(sG), Bt, rank, bb);
     src = Aj;
     lds = n;
     const int bnext = min(b, rmax - rank - bb);
     if (bnext > 0) {
       gen_gauss(n, bnext, (t + 1) * b, k0, k1, sG);
-      r2 = pass_rows<true, true>(m, n, Aj, n, Aj, sQ, sC, sG, red);
+      r2 = pass_rows<true, true, PD>(m, n, Aj, n, Aj, sQ, sC, sG, red);
     } else {
-      r2 = pass_rows<true, false>(m, n, Aj, n, Aj, sQ, sC, sG, red);
+      r2 = pass_rows<true, false, PD>(m, n, Aj, n, Aj, sQ, sC, sG, red);
     }
     rank += bb;
     ++t;
@@ -732,22 +863,71 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
   if (status == RSVD_OK && !(r2 <= eps2)) status = RSVD_E_NOT_CONVERGED;
   __syncthreads();
 
-  // Stage B on A ~= Q B with l = rank
+  // Stage B on A ~= Q B with l = rank: B^T = Q_B R_B (LU-CholeskyQR2), one-
+  // sided Jacobi on X = R_B^T (X J = W), V = Q_B J, U = Q W / sigma.  B^T is
+  // copied into shared memory (odd row stride) when it fits beside the
+  // small l x l arrays, else the factorization runs on it in place in the
+  // CTA's workspace slot.
   const int l = rank;
   const bool have = l > 0 && status != RSVD_E_BREAKDOWN && status != RSVD_E_NONFINITE;
   bool ok = true;
   if (have) {
-    double* g64 = reinterpret_cast<double*>(sG);     // l x l binary64
-    float* Xc = sG + 2 * RMAX * RMAX;                // l x l, column c at Xc + c l
-    float* Jm = Xc + RMAX * RMAX;                    // l x l
-    float* L = sC;                                   // l x l
-    float* Rb = L + RMAX * RMAX;                     // R_B
-    float* Rt = Rb + RMAX * RMAX;                    // scratch
-    float* Ulu = Rt + RMAX * RMAX;                   // U of the LU
-    float* dv = sP;                                  // l
-    float* sig = dv + RMAX;                          // l
-    int* perm = reinterpret_cast<int*>(sig + RMAX);  // l
-    ok = lu_cholqr2<true>(n, l, Bt, RMAX, g64, nullptr, L, dv, Ulu, Rb, Rt, W.used, W.rv, W.ri, W.flag);
+    const int LP = (l + 31) / 32 * 32;  // row stride of the permuted lift operands
+    const int ldb = l | 1;
+    const bool in_smem = (size_t)n * ldb + 8 * l * l + 2 * l * LP + 6 * l + 64 <= (size_t)SMEM_FLOATS;
+    float* Y;
+    int ldy;
+    double* g64;
+    float *Xc, *Jm, *L, *Rb, *Rt, *Ulu, *Jp, *Xp, *dv, *sig, *flip;
+    int* perm;
+    unsigned long long* keys;
+    if (in_smem) {
+      size_t off = 0;
+      auto take = [&](size_t nf) {
+        float* p = sm + off;
+        off += (nf + 3) & ~(size_t)3;
+        return p;
+      };
+      Y = take((size_t)n * ldb);
+      ldy = ldb;
+      g64 = reinterpret_cast<double*>(take((size_t)2 * l * l));
+      Xc = take((size_t)l * l);
+      Jm = take((size_t)l * l);
+      L = take((size_t)l * l);
+      Rb = take((size_t)l * l);
+      Rt = take((size_t)l * l);
+      Ulu = take((size_t)l * l);
+      Jp = take((size_t)l * LP);
+      Xp = take((size_t)l * LP);
+      dv = take(l);
+      sig = take(l);
+      flip = take(l);
+      perm = reinterpret_cast<int*>(take(l));
+      keys = reinterpret_cast<unsigned long long*>(take((size_t)2 * l));
+      for (int e = tid; e < n * l; e += BT) {
+        const int j = e / l, c = e % l;
+        Y[(size_t)j * ldb + c] = Bt[(size_t)j * RMAX + c];
+      }
+      __syncthreads();
+    } else {
+      Y = Bt;
+      ldy = RMAX;
+      g64 = reinterpret_cast<double*>(sG);  // l x l binary64
+      Xc = sG + 2 * RMAX * RMAX;            // l x l, column c at Xc + c l
+      Jm = Xc + RMAX * RMAX;                // l x l
+      L = sC;                               // l x l
+      Rb = L + RMAX * RMAX;                 // R_B
+      Rt = Rb + RMAX * RMAX;                // scratch
+      Ulu = Rt + RMAX * RMAX;               // U of the LU
+      Jp = sQ;                              // l x LP
+      Xp = sQ + RMAX * RMAX;                // l x LP
+      dv = sP;
+      sig = dv + RMAX;
+      flip = sig + RMAX;
+      perm = reinterpret_cast<int*>(flip + RMAX);
+      keys = reinterpret_cast<unsigned long long*>(flip + 2 * RMAX);
+    }
+    ok = lu_cholqr2<true>(n, l, Y, ldy, g64, nullptr, L, dv, Ulu, Rb, Rt, W.used, W.rv, W.ri, W.flag);
     if (ok) {
       for (int e = tid; e < l * l; e += BT) {  // X = R_B^T: column c is row c of R_B
         const int c = e / l, r = e % l;
@@ -757,58 +937,119 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
       __syncthreads();
       jacobi_cols(l, Xc, Jm, W.flag);
       for (int c = tid; c < l; c += BT) {
-        float s = 0.f;
-        for (int r = 0; r < l; ++r) s = fmaf(Xc[c * l + r], Xc[c * l + r], s);
-        sig[c] = sqrtf(s);
+        float sq = 0.f;
+        for (int r = 0; r < l; ++r) sq = fmaf(Xc[c * l + r], Xc[c * l + r], sq);
+        sig[c] = sqrtf(sq);
       }
       __syncthreads();
       for (int c = tid; c < l; c += BT) {  // descending; ties by index
         int rk = 0;
         for (int c2 = 0; c2 < l; ++c2) rk += (sig[c2] > sig[c]) || (sig[c2] == sig[c] && c2 < c);
         perm[rk] = c;
+        keys[c] = 0ull;
       }
       __syncthreads();
-      for (int e = tid; e < n * l; e += BT) {  // V = Q_B J
-        const int j = e / l, k = e % l, sc = perm[k];
-        float s = 0.f;
-        for (int c = 0; c < l; ++c) s = fmaf(Bt[(size_t)j * RMAX + c], Jm[sc * l + c], s);
-        P.V[(size_t)j * R + k] = s;
+      // Jp(c, k) = J(c, perm k), zero for k >= l
+      for (int e = tid; e < l * LP; e += BT) {
+        const int c = e / LP, k = e % LP;
+        Jp[e] = k < l ? Jm[perm[k] * l + c] : 0.f;
       }
-      for (int e = tid; e < m * l; e += BT) {  // U = Q X / sigma
-        const int i = e / l, k = e % l, sc = perm[k];
-        const float inv = sig[sc] > 0.f ? 1.f / sig[sc] : 0.f;
-        float s = 0.f;
-        for (int c = 0; c < l; ++c) s = fmaf(Qt[(size_t)c * NMAX + i], Xc[sc * l + c], s);
-        P.U[(size_t)i * R + k] = s * inv;
-      }
-      for (int k = tid; k < l; k += BT) P.D[k] = (double)sig[perm[k]];
       __syncthreads();
-      // sign convention: the largest |V(:, k)| entry (lowest row on ties) is positive
-      const int lane = tid & 31, warp = tid >> 5;
-      for (int k = warp; k < l; k += BW) {
-        float best = -1.f;
-        int bi = 0x7fffffff;
-        for (int j = lane; j < n; j += 32) {
-          const float a = fabsf(P.V[(size_t)j * R + k]);
-          if (a > best) {
-            best = a;
-            bi = j;
-          }
-        }
+      // V = Q_B Jp, a thread per row and 32 columns; the largest |V(:, k)|
+      // (lowest row on ties) is recorded as a 64-bit key per column
+      const bool vec4 = (R % 4) == 0 && ((reinterpret_cast<uintptr_t>(P.V) | reinterpret_cast<uintptr_t>(P.U)) & 15) == 0;
+      for (int k0 = 0; k0 < l; k0 += 32) {
+        for (int j = tid; j < n; j += BT) {
+          float acc[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
+          for (int kk = 0; kk < 32; ++kk) acc[kk] = 0.f;
+          const float* yr = Y + (size_t)j * ldy;
+#pragma unroll 2
+          for (int c = 0; c < l; ++c) {
+            const float yv = yr[c];
+            const float4* jp = reinterpret_cast<const float4*>(Jp + c * LP + k0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 t = jp[q];
+              acc[4 * q] = fmaf(yv, t.x, acc[4 * q]);
+              acc[4 * q + 1] = fmaf(yv, t.y, acc[4 * q + 1]);
+              acc[4 * q + 2] = fmaf(yv, t.z, acc[4 * q + 2]);
+              acc[4 * q + 3] = fmaf(yv, t.w, acc[4 * q + 3]);
+            }
           }
+          float* vr = P.V + (size_t)j * R + k0;
+          const int kn = min(32, l - k0);
+          if (vec4 && kn == 32) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              reinterpret_cast<float4*>(vr)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk)
+              if (kk < kn) vr[kk] = acc[kk];
+          }
+#pragma unroll
+          for (int kk = 0; kk < 32; ++kk)
+            if (kk < kn) {
+              const unsigned long long key = ((unsigned long long)__float_as_uint(fabsf(acc[kk])) << 32) |
+                                             (unsigned long long)(0xffffffffu - (unsigned)j);
+              atomicMax(&keys[k0 + kk], key);
+            }
         }
-        const bool flip = bi < n && P.V[(size_t)bi * R + k] < 0.f;
-        __syncwarp();
-        if (flip) {
-          for (int j = lane; j < n; j += 32) P.V[(size_t)j * R + k] = -P.V[(size_t)j * R + k];
-          for (int i = lane; i < m; i += 32) P.U[(size_t)i * R + k] = -P.U[(size_t)i * R + k];
+      }
+      __syncthreads();
+      for (int k = tid; k < l; k += BT) {
+        const int jb = (int)(0xffffffffu - (unsigned)(keys[k] & 0xffffffffull));
+        flip[k] = (jb < n && P.V[(size_t)jb * R + k] < 0.f) ? -1.f : 1.f;
+        P.D[k] = (double)sig[perm[k]];
+      }
+      __syncthreads();
+      for (int e = tid; e < n * l; e += BT) {
+        const int j = e / l, k = e % l;
+        if (flip[k] < 0.f) P.V[(size_t)j * R + k] = -P.V[(size_t)j * R + k];
+      }
+      // Xp(c, k) = flip_k W(c, perm k) / sigma_perm k, zero for k >= l
+      for (int e = tid; e < l * LP; e += BT) {
+        const int c = e / LP, k = e % LP;
+        float v = 0.f;
+        if (k < l) {
+          const int sc = perm[k];
+          const float inv = sig[sc] > 0.f ? 1.f / sig[sc] : 0.f;
+          v = flip[k] * (Xc[sc * l + c] * inv);
+        }
+        Xp[e] = v;
+      }
+      __syncthreads();
+      // U = Q Xp, a thread per row and 32 columns (Q^T rows read coalesced)
+      for (int k0 = 0; k0 < l; k0 += 32) {
+        for (int i = tid; i < m; i += BT) {
+          float acc[32];
+#pragma unroll
+          for (int kk = 0; kk < 32; ++kk) acc[kk] = 0.f;
+#pragma unroll 4
+          for (int c = 0; c < l; ++c) {
+            const float qv = Qt[(size_t)c * NMAX + i];
+            const float4* xp = reinterpret_cast<const float4*>(Xp + c * LP + k0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 t = xp[q];
+              acc[4 * q] = fmaf(qv, t.x, acc[4 * q]);
+              acc[4 * q + 1] = fmaf(qv, t.y, acc[4 * q + 1]);
+              acc[4 * q + 2] = fmaf(qv, t.z, acc[4 * q + 2]);
+              acc[4 * q + 3] = fmaf(qv, t.w, acc[4 * q + 3]);
+            }
+          }
+          float* ur = P.U + (size_t)i * R + k0;
+          const int kn = min(32, l - k0);
+          if (vec4 && kn == 32) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              reinterpret_cast<float4*>(ur)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk)
+              if (kk < kn) ur[kk] = acc[kk];
+          }
         }
       }
     } else {
@@ -833,6 +1074,7 @@ __device__ void solve_one(const Prob& P, int p, uint64_t seed, double tol, int R
   __syncthreads();
 }
 
+template <int PF, int PD>
 __global__ void __launch_bounds__(BT, 1)
     batched_kernel(int count, const int* __restrict__ order, const int* __restrict__ pm, const int* __restrict__ pn,
                    const int* __restrict__ plda, const float* const* __restrict__ pA, float* const* __restrict__ pU,
@@ -873,7 +1115,7 @@ __global__ void __launch_bounds__(BT, 1)
       }
       continue;
     }
-    solve_one(P, p, seed, tol, R, b, base, sm, W, rank_out, err_out, status_out, st);
+    solve_one<PF, PD>(P, p, seed, tol, R, b, base, sm, W, rank_out, err_out, status_out, st);
   }
 }
 
@@ -904,7 +1146,30 @@ __global__ void batched_order_kernel(int count, const int* __restrict__ pm, cons
   if (p < count) order[rk] = p;
 }
 
+// The variants differ only in how far ahead each thread loads (PF rows in the
+// column-owned passes, PD columns in the row-owned ones); the arithmetic and
+// its order are the same in all of them, so their outputs are bit-identical.
+struct Variant {
+  int pf, pd;
+  void (*fn)(int, const int*, const int*, const int*, const int*, const float* const*, float* const*,
+             double* const*, float* const*, int, int, uint64_t, double, int*, float*, int*, double*, int*,
+             DevStatus*);
+};
+const Variant kVariants[] = {{8, 1, batched_kernel<8, 1>},
+                             {16, 2, batched_kernel<16, 2>},
+                             {32, 2, batched_kernel<32, 2>},
+                             {32, 3, batched_kernel<32, 3>}};
+constexpr int NVAR = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr int DEFAULT_VARIANT = 1;
+
 }  // namespace
+
+int batched_variants() { return NVAR; }
+int batched_default_variant() { return DEFAULT_VARIANT; }
+void batched_variant_info(int v, int* pf, int* pd) {
+  *pf = kVariants[v].pf;
+  *pd = kVariants[v].pd;
+}
 
 int batched_max_rank() { return RMAX; }
 int batched_max_dim() { return NMAX; }
@@ -922,7 +1187,8 @@ size_t batched_workspace_bytes(int count, int ctas) {
 cudaError_t launch_batched(int count, const int* m, const int* n, const int* lda, const float* const* A,
                            float* const* U, double* const* D, float* const* V, int R, int b, uint64_t seed,
                            double tol, int* rank_out, double* err_out, int* status_out, void* ws, int ctas,
-                           cudaStream_t s) {
+                           cudaStream_t s, int variant) {
+  if (variant < 0 || variant >= NVAR) variant = DEFAULT_VARIANT;
   Carver c(ws);
   DevStatus* st = c.take<DevStatus>(1);
   int* counter = c.take<int>(1);
@@ -932,20 +1198,21 @@ cudaError_t launch_batched(int count, const int* m, const int* n, const int* lda
   if (e != cudaSuccess) return e;
   batched_order_kernel<<<(count + BT - 1) / BT, BT, 0, s>>>(count, m, n, order);
   note_launch();
-  // the shared-memory opt-in is set once per device, outside any later graph capture
-  static std::atomic<unsigned long long> smem_set{0};
+  // the shared-memory opt-in is set once per device and variant, outside any
+  // later graph capture
+  static std::atomic<unsigned long long> smem_set[NVAR];
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
-  if (!(smem_set.load() & bit)) {
-    e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (!(smem_set[variant].load() & bit)) {
+    e = cudaFuncSetAttribute(kVariants[variant].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    smem_set.fetch_or(bit);
+    smem_set[variant].fetch_or(bit);
   }
   const int grid = count < ctas ? count : ctas;
-  batched_kernel<<<grid, BT, SMEM_BYTES, s>>>(count, order, m, n, lda, A, U, D, V, R, b, seed, tol, counter, slots,
-                                              rank_out, err_out, status_out, st);
+  kVariants[variant].fn<<<grid, BT, SMEM_BYTES, s>>>(count, order, m, n, lda, A, U, D, V, R, b, seed, tol, counter,
+                                                     slots, rank_out, err_out, status_out, st);
   note_launch();
   return cudaGetLastError();
 }

@@ -93,10 +93,13 @@ int batched_max_rank();
 int batched_max_dim();
 int batched_max_block();
 size_t batched_workspace_bytes(int count, int ctas);
+int batched_variants();
+int batched_default_variant();
+void batched_variant_info(int v, int* pf, int* pd);
 cudaError_t launch_batched(int count, const int* m, const int* n, const int* lda, const float* const* A,
                            float* const* U, double* const* D, float* const* V, int R, int b, uint64_t seed,
                            double tol, int* rank_out, double* err_out, int* status_out, void* ws, int ctas,
-                           cudaStream_t s);
+                           cudaStream_t s, int variant);
 
 // k_ctrl.cu
 int thin_splits(int m, int n, int sms);

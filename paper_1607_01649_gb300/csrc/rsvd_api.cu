@@ -24,6 +24,8 @@ struct rsvd_handle_s {
   int ctrl_fallback;  // 0: adaptive range finder, 1: fixed rank at the largest rank
   int ctrl_info[5];
   double ctrl_est[2];
+  // rsvd_batched launch variant (-1: the library default), set by the autotuner
+  int batched_variant;
 };
 
 namespace rsvd {
@@ -801,6 +803,7 @@ rsvd_status rsvd_create(rsvd_handle_t* handle, int device) {
   h->ctrl_quantile = 0.9;
   h->ctrl_safety = 0.8;
   h->ctrl_fallback = 0;
+  h->batched_variant = -1;
   if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete h;
     return RSVD_E_CUDA;
@@ -1015,9 +1018,91 @@ rsvd_status rsvd_batched(rsvd_handle_t handle, int count, const int* m, const in
   cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e =
       launch_batched(count, m, n, lda, (const float* const*)A, (float* const*)U, D, (float* const*)V, R, b,
-                     params->seed, params->tol, rank_out, err_out, status_out, workspace, handle->sms, s);
+                     params->seed, params->tol, rank_out, err_out, status_out, workspace, handle->sms, s,
+                     handle->batched_variant);
   if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_batched launch: %s", cudaGetErrorString(e));
   return finish_sync(handle, params, (DevStatus*)workspace, s);
+}
+
+rsvd_status rsvd_batched_variants(int* count) {
+  if (!count) return RSVD_E_INVALID;
+  *count = batched_variants();
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_batched_variant_info(int variant, int* rows_ahead, int* cols_ahead) {
+  if (variant < 0 || variant >= batched_variants() || !rows_ahead || !cols_ahead) return RSVD_E_INVALID;
+  batched_variant_info(variant, rows_ahead, cols_ahead);
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_batched_set_variant(rsvd_handle_t handle, int variant) {
+  if (!handle) return RSVD_E_INVALID;
+  if (variant < -1 || variant >= batched_variants())
+    return fail(handle, RSVD_E_INVALID, "variant must lie in [-1, %d]", batched_variants() - 1);
+  handle->batched_variant = variant;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_batched_get_variant(rsvd_handle_t handle, int* variant) {
+  if (!handle || !variant) return RSVD_E_INVALID;
+  *variant = handle->batched_variant < 0 ? batched_default_variant() : handle->batched_variant;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_batched_autotune(rsvd_handle_t handle, int count, const int* m, const int* n, const void* const* A,
+                                  const int* lda, const rsvd_params* params, void* const* U, double* const* D,
+                                  void* const* V, int* rank_out, double* err_out, int* status_out, void* workspace,
+                                  size_t ws_bytes, rsvd_stream_t stream, float* ms_out, int* variant_out) {
+  int R = 0, b = 0;
+  rsvd_status st = validate_batched(handle, count, params, &R, &b);
+  if (st != RSVD_OK) return st;
+  if (!m || !n || !A || !lda || !U || !D || !V) return fail(handle, RSVD_E_INVALID, "NULL array argument");
+  const size_t need = batched_workspace_bytes(count, handle->sms);
+  if (!workspace || ws_bytes < need)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nv = batched_variants();
+  int best = batched_default_variant();
+  float best_ms = 0.f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(handle, RSVD_E_CUDA, "event create failed");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(handle, RSVD_E_CUDA, "event create failed");
+  }
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < nv && e == cudaSuccess && count > 0; ++v) {
+    // one untimed run (first launch of the variant), then one timed run
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      if (rep == 1) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess)
+        e = launch_batched(count, m, n, lda, (const float* const*)A, (float* const*)U, D, (float* const*)V, R, b,
+                           params->seed, params->tol, rank_out, err_out, status_out, workspace, handle->sms, s, v);
+      if (rep == 1 && e == cudaSuccess) e = cudaEventRecord(e1, s);
+    }
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) {
+      if (ms_out) ms_out[v] = ms;
+      if (v == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "rsvd_batched_autotune: %s", cudaGetErrorString(e));
+  handle->batched_variant = best;
+  if (variant_out) *variant_out = best;
+  int code = 0;
+  e = cudaMemcpy(&code, &((const DevStatus*)workspace)->code, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "status read: %s", cudaGetErrorString(e));
+  if (code != RSVD_OK) return fail(handle, (rsvd_status)code, "a problem of the batch reported status %d", code);
+  return RSVD_OK;
 }
 
 rsvd_status rsvd_query_status(rsvd_handle_t handle, const void* workspace, int* status, rsvd_stream_t stream) {

@@ -187,3 +187,34 @@ def test_batched_full_workload_sampled(lib):
     rng = np.random.default_rng(11)
     for p in list(rng.choice(len(shapes), 6, replace=False)) + [int(np.argmax([m * n for m, n in shapes]))]:
         _check_problem(plan.block(int(p)).cpu().numpy(), plan, int(p), 1e-6, 0)
+
+
+def test_batched_variants_bit_identical_and_autotune(lib):
+    """Every launch variant (loads in flight per thread) gives the same bits;
+    the autotuner keeps the fastest and rsvd_batched launches it."""
+    import torch
+    blocks = [kernel_block(b, seed=4001) for b in range(40, 64)]
+    plan = _plan(lib, blocks)
+    h = lib.handle()
+    nv = lib.rsvd_batched_variants()
+    assert nv >= 2
+    with pytest.raises(lib.RsvdError):
+        lib.rsvd_batched_set_variant(h, nv)
+    outs = []
+    try:
+        for v in range(nv):
+            lib.rsvd_batched_set_variant(h, v)
+            assert lib.rsvd_batched_get_variant(h) == v
+            assert lib.batched_run(plan, 1e-6, seed=3, flags=lib.RSVD_FLAG_SYNC) == lib.RSVD_OK
+            outs.append([t.clone() for t in (plan.U, plan.D, plan.V, plan.rank, plan.err, plan.status)])
+        for o in outs[1:]:
+            for a, b in zip(outs[0], o):
+                assert torch.equal(a, b)
+        var, ms = lib.batched_autotune(plan, 1e-6, seed=3)
+        assert 0 <= var < nv and len(ms) == nv and all(x > 0 for x in ms) and ms[var] == min(ms)
+        assert lib.rsvd_batched_get_variant(h) == var
+        for a, b in zip(outs[0], (plan.U, plan.D, plan.V, plan.rank, plan.err, plan.status)):
+            assert torch.equal(a, b)
+    finally:
+        lib.rsvd_batched_set_variant(h, -1)
+    _check_problem(blocks[0], plan, 0, 1e-6, 3)

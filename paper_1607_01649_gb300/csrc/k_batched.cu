@@ -160,6 +160,44 @@ __device__ __forceinline__ int scatter_index64(int lane) {
 //   y(i, c) += a G(j, c)                           (AG)
 // y overwrites the rows of sQ the warp owns, after their q has been read.
 // Returns ||a||_F^2 (binary64; the same value in every thread).
+// One column j of a row-owned pass over the warp's 4 rows (rows valid): with
+// UPD, a(r) -= Q_new(r, :) . C(:, j), stored; then ||a||^2 and y(r, :) +=
+// a(r) G(j, :).  Rows past `rows` hold zeros and stay zero (selects, not
+// branches, so the four dependent chains interleave).
+template <bool UPD, bool AG>
+__device__ __forceinline__ void row_col(const float (&ain)[4], int j, int rows, int n, const float (&q)[4][BB],
+                                        const float* sC, const float* sG, float* d0, float& nrm, float (&y)[64]) {
+  float a[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) a[r] = ain[r];
+  if (UPD) {
+    float cj[BB];
+    lds16s(sC, j, cj);
+    float s[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      s[r] = 0.f;
+#pragma unroll
+      for (int c = 0; c < BB; ++c) s[r] = fmaf(q[r][c], cj[c], s[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a[r] = r < rows ? a[r] - s[r] : 0.f;
+      if (r < rows) d0[(size_t)r * n + j] = a[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) nrm = fmaf(a[r], a[r], nrm);
+  if (AG) {
+    float g[BB];
+    lds16s(sG, j, g);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < BB; ++c) y[r * BB + c] = fmaf(a[r], g[c], y[r * BB + c]);
+  }
+}
+
 template <bool UPD, bool AG, int PD>
 __device__ double pass_rows(int m, int n, const float* src, int lds, float* dst, float* sQ, const float* sC,
                             const float* sG, double* red) {
@@ -201,37 +239,16 @@ __device__ double pass_rows(int m, int n, const float* src, int lds, float* dst,
           for (int r = 0; r < 4; ++r) nb[d][r] = (r < rows && jn < n) ? s0[(size_t)r * lds + jn] : 0.f;
         }
       }
+      if ((j0 - lane) + 32 * PD <= n) {
+        // a full batch of columns: no branches between them
 #pragma unroll
-      for (int d = 0; d < PD; ++d) {
-        const int j = j0 + 32 * d;
-        if (j < n) {
-          float a[4];
+        for (int d = 0; d < PD; ++d)
+          row_col<UPD, AG>(cur[d], j0 + 32 * d, rows, n, q, sC, sG, d0, nrm, y);
+      } else {
 #pragma unroll
-          for (int r = 0; r < 4; ++r) a[r] = cur[d][r];
-          if (UPD) {
-            float cj[BB];
-            lds16s(sC, j, cj);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              if (r < rows) {
-                float s = 0.f;
-#pragma unroll
-                for (int c = 0; c < BB; ++c) s = fmaf(q[r][c], cj[c], s);
-                a[r] -= s;
-                d0[(size_t)r * n + j] = a[r];
-              }
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < 4; ++r) nrm = fmaf(a[r], a[r], nrm);
-          if (AG) {
-            float g[BB];
-            lds16s(sG, j, g);
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-              for (int c = 0; c < BB; ++c) y[r * BB + c] = fmaf(a[r], g[c], y[r * BB + c]);
-          }
+        for (int d = 0; d < PD; ++d) {
+          const int j = j0 + 32 * d;
+          if (j < n) row_col<UPD, AG>(cur[d], j, rows, n, q, sC, sG, d0, nrm, y);
         }
       }
     }
@@ -282,9 +299,28 @@ __device__ __forceinline__ ColSplit col_split(int m, int n) {
 // into binary64; row-group partial sums meet in `part` (binary64, in the sG
 // region).  Each thread keeps PF rows' loads in flight; PF changes only the
 // load schedule, never the order of the arithmetic.
+// One row of a column-owned pass: with UPD, a -= Q_new(i, :) . C1(:, j) and
+// the result stored; then acc(c) += Q_new(i, c) a.
+template <bool UPD>
+__device__ __forceinline__ void col_row(float av, int i, int n, int j, const float* sQ, const float (&c1)[BB],
+                                        float* dst, float (&acc)[BB]) {
+  float qi[BB];
+  lds16(sQ + i * BB, qi);
+  if (UPD) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < BB; ++c) s = fmaf(qi[c], c1[c], s);
+    av -= s;
+    dst[(size_t)i * n + j] = av;
+  }
+#pragma unroll
+  for (int c = 0; c < BB; ++c) acc[c] = fmaf(qi[c], av, acc[c]);
+}
+
 template <bool UPD, int PF>
 __device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, const float* sQ, float* sC,
                           double* part, float* Bt, int k0, int bb) {
+  static_assert(CHUNK % PF == 0, "the fold points must fall on batch boundaries");
   const ColSplit cs = col_split(m, n);
   const int g = threadIdx.x / cs.ncol, tj = threadIdx.x % cs.ncol;
   const int G = cs.groups;
@@ -328,29 +364,35 @@ __device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, c
             nb[u] = i < m ? sp[(size_t)i * lds] : 0.f;
           }
         }
+        if (i0 + (PF - 1) * G < m) {
+          // a full batch: no branch between its rows, so their dependent
+          // chains interleave; the binary64 fold comes at batch granularity
+          // (PF divides CHUNK: the fold points are the same rows)
 #pragma unroll
-        for (int u = 0; u < PF; ++u) {
-          const int i = i0 + u * G;
-          if (i < m) {
-            float av = cur[u];
-            float qi[BB];
-            lds16(sQ + i * BB, qi);
-            if (UPD) {
-              float s = 0.f;
+          for (int u = 0; u < PF; ++u) col_row<UPD>(cur[u], i0 + u * G, n, j, sQ, c1, dst, acc);
+          cnt += PF;
+          if (cnt == CHUNK) {
 #pragma unroll
-              for (int c = 0; c < BB; ++c) s = fmaf(qi[c], c1[c], s);
-              av -= s;
-              dst[(size_t)i * n + j] = av;
+            for (int c = 0; c < BB; ++c) {
+              acc64[c] += (double)acc[c];
+              acc[c] = 0.f;
             }
+            cnt = 0;
+          }
+        } else {
 #pragma unroll
-            for (int c = 0; c < BB; ++c) acc[c] = fmaf(qi[c], av, acc[c]);
-            if (++cnt == CHUNK) {
+          for (int u = 0; u < PF; ++u) {
+            const int i = i0 + u * G;
+            if (i < m) {
+              col_row<UPD>(cur[u], i, n, j, sQ, c1, dst, acc);
+              if (++cnt == CHUNK) {
 #pragma unroll
-              for (int c = 0; c < BB; ++c) {
-                acc64[c] += (double)acc[c];
-                acc[c] = 0.f;
+                for (int c = 0; c < BB; ++c) {
+                  acc64[c] += (double)acc[c];
+                  acc[c] = 0.f;
+                }
+                cnt = 0;
               }
-              cnt = 0;
             }
           }
         }
@@ -1156,11 +1198,11 @@ struct Variant {
              DevStatus*);
 };
 const Variant kVariants[] = {{8, 1, batched_kernel<8, 1>},
+                             {8, 2, batched_kernel<8, 2>},
                              {16, 2, batched_kernel<16, 2>},
-                             {32, 2, batched_kernel<32, 2>},
-                             {32, 3, batched_kernel<32, 3>}};
+                             {32, 2, batched_kernel<32, 2>}};
 constexpr int NVAR = sizeof(kVariants) / sizeof(kVariants[0]);
-constexpr int DEFAULT_VARIANT = 1;
+constexpr int DEFAULT_VARIANT = 2;
 
 }  // namespace
 

@@ -473,7 +473,8 @@ __device__ void gram16(int rows, int l, const float* Y, int ldy, double* g64, do
 
 // Gram of a rows x l block (l <= 64, shared or global memory, row stride
 // ldy): one thread per upper-triangle entry; four binary32 partial sums over
-// interleaved rows of each 64-row chunk, folded into binary64 per chunk.
+// interleaved rows of each 64-row chunk, added in binary32 and folded into
+// binary64 per chunk.
 __device__ void gram_wide(int rows, int l, const float* Y, int ldy, double* g64) {
   const int nent = l * (l + 1) / 2;
   for (int e = threadIdx.x; e < nent; e += BT) {
@@ -496,7 +497,7 @@ __device__ void gram_wide(int rows, int l, const float* Y, int ldy, double* g64)
         p3 = fmaf(y[3 * ldy + i], y[3 * ldy + j], p3);
       }
       for (; r < r1; ++r) p0 = fmaf(Y[(size_t)r * ldy + i], Y[(size_t)r * ldy + j], p0);
-      acc += ((double)p0 + (double)p1) + ((double)p2 + (double)p3);
+      acc += (double)((p0 + p1) + (p2 + p3));  // one binary64 add per chunk
     }
     g64[i * l + j] = acc;
     g64[j * l + i] = acc;
@@ -515,16 +516,23 @@ __device__ bool chol_warp(int l, const double* g64, float* L, float* dinv) {
   const int lane = threadIdx.x & 31;
   const float u = 5.9604644775390625e-08f;
   float shift = 0.f;
+  // the scaling d_i = G_ii^-1/2 in binary64 (rounded to binary32), once per
+  // diagonal entry: binary64 square roots and divisions run at a small
+  // fraction of the binary32 rate on this part
+  for (int i = lane; i < l; i += 32) {
+    const double gii = g64[i * l + i];
+    dinv[i] = gii > 0.0 ? (float)(1.0 / sqrt(gii)) : 0.f;
+  }
+  __syncwarp();
   for (int attempt = 0; attempt < 6; ++attempt) {
-    for (int e = lane; e < l * l; e += 32) {
-      const int i = e / l, j = e % l;
-      const double gii = g64[i * l + i], gjj = g64[j * l + j];
-      const float di = gii > 0.0 ? (float)(1.0 / sqrt(gii)) : 0.f;
-      const float dj = gjj > 0.0 ? (float)(1.0 / sqrt(gjj)) : 0.f;
-      float v = (float)g64[e] * di * dj;
-      if (i == j) v = (gii > 0.0 ? 1.f : 0.f) + shift;
-      L[e] = (i >= j) ? v : 0.f;
-      if (i == j) dinv[i] = di;
+    for (int i = 0; i < l; ++i) {
+      const float di = dinv[i];
+      const bool pos = g64[i * l + i] > 0.0;
+      for (int j = lane; j < l; j += 32) {
+        float v = (float)g64[i * l + j] * di * dinv[j];
+        if (i == j) v = (pos ? 1.f : 0.f) + shift;
+        L[i * l + j] = (i >= j) ? v : 0.f;
+      }
     }
     __syncwarp();
     bool ok = true;

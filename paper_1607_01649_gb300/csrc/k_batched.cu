@@ -35,7 +35,9 @@ constexpr int BW = BT / 32;  // warps per CTA
 constexpr int BB = 16;       // largest block width b (row stride of Y, G, C)
 constexpr int RMAX = 64;     // rank cap
 constexpr int NMAX = 1024;   // largest m, n
-constexpr int CHUNK = 64;    // binary32 partial-sum length before a binary64 fold
+// binary32 partial-sum length before a binary64 fold (binary64 adds run at
+// 1/64 of the binary32 rate on this part)
+constexpr int CHUNK = 256;
 constexpr int YLD = BB + 1;  // odd row stride of the copy of Y being orthonormalized
 
 // dynamic shared memory, in floats
@@ -432,7 +434,7 @@ __device__ void pass_cols(int m, int n, const float* src, int lds, float* dst, c
 // --------------------------------------------------------- small algebra --
 // Gram of the rows x l block Y (row stride ldy >= 16, l <= 16, columns l..15
 // zero) into g64 (l x l, binary64).  Warp w sums rows w, w + 8, ...; lane
-// holds the pairs (lane / 2, 8 (lane % 2) + 0..7); binary32 partials of 64
+// holds the pairs (lane / 2, 8 (lane % 2) + 0..7); binary32 partials of CHUNK
 // rows are folded into binary64.
 __device__ void gram16(int rows, int l, const float* Y, int ldy, double* g64, double* wpart) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -473,7 +475,7 @@ __device__ void gram16(int rows, int l, const float* Y, int ldy, double* g64, do
 
 // Gram of a rows x l block (l <= 64, shared or global memory, row stride
 // ldy): one thread per upper-triangle entry; four binary32 partial sums over
-// interleaved rows of each 64-row chunk, added in binary32 and folded into
+// interleaved rows of each CHUNK-row chunk, added in binary32 and folded into
 // binary64 per chunk.
 __device__ void gram_wide(int rows, int l, const float* Y, int ldy, double* g64) {
   const int nent = l * (l + 1) / 2;

@@ -24,6 +24,10 @@ namespace rsvd {
 constexpr int GT = 64;       // Gram tile
 constexpr int GCH = 32;      // rows per chunk in shared memory
 constexpr int GFOLD = 4;     // chunks per binary64 fold (128 rows)
+// The binary32 Gram folds its partial sums into binary64 every 512 rows:
+// binary64 adds run at 1/64 of the binary32 rate on this part, and a fold
+// every 128 rows spent one binary64 add per 128 FMAs of a thread.
+constexpr int GFOLD32 = 16;
 
 // Partial Gram of rows [r_beg, r_end) for the upper-triangular tile
 // (bi, bj), bi <= bj, written to P[split][bi*GT + i][bj*GT + j] (ld = l).
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(G32_THREADS)
 #pragma unroll
         for (int v = 0; v < 4; ++v) part[u][v] = fmaf(a[u], b[v], part[u][v]);
     }
-    if ((chunk % GFOLD) == GFOLD - 1 || r0 + GCH >= r_end) {
+    if ((chunk % GFOLD32) == GFOLD32 - 1 || r0 + GCH >= r_end) {
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll

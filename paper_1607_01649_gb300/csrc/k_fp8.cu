@@ -92,12 +92,85 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same conversion with a CTA per row for rows of at most 1024 NV
+// columns: the row is read once into registers (NV 16-byte vectors per
+// thread), the next row's loads are issued before this row is converted, and
+// the row maximum meets in shared memory.  Same values as fp8_rows_kernel.
+template <int NV>
+__global__ void __launch_bounds__(256)
+    fp8_rows_block_kernel(int rows, int cols, const float* __restrict__ A, int lda, uint8_t* __restrict__ A8,
+                          int ld8, float* __restrict__ s, __nv_bfloat16* __restrict__ Ah,
+                          __nv_bfloat16* __restrict__ Al, int ldb) {
+  __shared__ float red[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4 nxt[NV];
+  auto load = [&](int i, float4(&v)[NV]) {
+    const float* a = A + (size_t)i * lda;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int j = 4 * (tid + 256 * u);
+      v[u] = j < cols ? *reinterpret_cast<const float4*>(a + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  int i = blockIdx.x;
+  if (i < rows) load(i, nxt);
+  for (; i < rows; i += gridDim.x) {
+    float4 cur[NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) cur[u] = nxt[u];
+    if (i + (int)gridDim.x < rows) load(i + gridDim.x, nxt);
+    float mx = 0.f;
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(cur[u].x), fabsf(cur[u].y)), fmaxf(fabsf(cur[u].z), fabsf(cur[u].w))));
+    mx = warp_max(mx);
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    float m = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+    __syncthreads();  // red is rewritten for the next row
+    const float r = m > 0.f ? 448.0f / m : 1.0f;
+    if (tid == 0) s[i] = 1.0f / r;
+    uint8_t* q = A8 + (size_t)i * ld8;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int j = 4 * (tid + 256 * u);
+      if (j < cols) {
+        const float4 v = cur[u];
+        const uint32_t packed = (uint32_t)to_e4m3(v.x * r) | ((uint32_t)to_e4m3(v.y * r) << 8) |
+                                ((uint32_t)to_e4m3(v.z * r) << 16) | ((uint32_t)to_e4m3(v.w * r) << 24);
+        *reinterpret_cast<uint32_t*>(q + j) = packed;
+        if (Ah) {
+          __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+          const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+          __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+          __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+          uint2 hv, lv;
+          hv.x = *reinterpret_cast<uint32_t*>(&h01);
+          hv.y = *reinterpret_cast<uint32_t*>(&h23);
+          lv.x = *reinterpret_cast<uint32_t*>(&l01);
+          lv.y = *reinterpret_cast<uint32_t*>(&l23);
+          *reinterpret_cast<uint2*>(Ah + (size_t)i * ldb + j) = hv;
+          *reinterpret_cast<uint2*>(Al + (size_t)i * ldb + j) = lv;
+        }
+      }
+    }
+  }
+}
+
 void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, int ld8, float* s, __nv_bfloat16* Ah,
                      __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st) {
   if (rows == 0 || cols == 0) return;
   const bool vec = (cols % 4 == 0) && (lda % 4 == 0) && (ld8 % 4 == 0) && (((uintptr_t)A & 15) == 0) &&
                    (((uintptr_t)A8 & 3) == 0) && (!Ah || (ldb % 4 == 0 && ((uintptr_t)Ah & 7) == 0 &&
                                                          ((uintptr_t)Al & 7) == 0));
+  if (vec && cols <= 4096) {
+    const int blocks = rows < sms * 4 ? rows : sms * 4;
+    fp8_rows_block_kernel<4><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb);
+    note_launch();
+    return;
+  }
   int blocks = ceil_div(rows, 8);
   if (blocks > sms * 16) blocks = sms * 16;
   if (vec)
@@ -107,37 +180,75 @@ void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, i
   note_launch();
 }
 
-// 64 x 64 byte tiles through shared memory, 16-byte loads and stores (lda and
-// ldt are multiples of 16: the padding columns of a row may be read, and
-// bytes past `rows` in an output row land in its padding).
+// 64 x 256 byte tiles through shared memory (lda and ldt are multiples of
+// 16: the padding columns of a row may be read, and bytes past `rows` in an
+// output row land in its padding).  Loads: four 16-byte vectors per thread,
+// all issued before any is stored.  Transpose: thread (column group g, row
+// group v) reads 16 rows x 4 columns as 32-bit words, transposes each 4 x 4
+// byte block with byte permutes, and writes 16 bytes of each of its 4
+// output rows; the 4 threads of a column group sit in adjacent lanes, so a
+// warp writes 64 contiguous bytes of 8 output rows per store.  Row r keeps
+// its words rotated by 8 (r / 16) positions, which puts the 32 words a warp
+// reads in 32 distinct banks.
+constexpr int TR_R = 64, TR_C = 256, TR_LDW = TR_C / 4 + 4;  // row stride in 32-bit words
+
+__device__ __forceinline__ void transpose4x4(const uint32_t (&w)[4], uint32_t (&c)[4]) {
+  // word i holds row i's bytes of 4 columns; c[k] receives column k's bytes of the 4 rows
+  const uint32_t t0 = __byte_perm(w[0], w[1], 0x5140), t1 = __byte_perm(w[0], w[1], 0x7362);
+  const uint32_t t2 = __byte_perm(w[2], w[3], 0x5140), t3 = __byte_perm(w[2], w[3], 0x7362);
+  c[0] = __byte_perm(t0, t2, 0x5410);
+  c[1] = __byte_perm(t0, t2, 0x7632);
+  c[2] = __byte_perm(t1, t3, 0x5410);
+  c[3] = __byte_perm(t1, t3, 0x7632);
+}
+
 __global__ void __launch_bounds__(256)
     u8_transpose_kernel(int rows, int cols, const uint8_t* __restrict__ A, int lda, uint8_t* __restrict__ B, int ldt) {
-  __shared__ __align__(16) uint8_t t[64][64 + 16];
-  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
-  {
-    const int r = threadIdx.x >> 2, v = threadIdx.x & 3;  // row r, bytes 16 v .. 16 v + 15
-    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+  __shared__ __align__(16) uint32_t t[TR_R * TR_LDW];
+  const int r0 = blockIdx.y * TR_R, c0 = blockIdx.x * TR_C;
+  uint4 x[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    const int r = e >> 4, v = e & 15;  // row r, bytes 16 v .. 16 v + 15
+    x[u] = make_uint4(0u, 0u, 0u, 0u);
     if (r0 + r < rows && c0 + 16 * v < lda)
-      x = *reinterpret_cast<const uint4*>(A + (size_t)(r0 + r) * lda + c0 + 16 * v);
-    *reinterpret_cast<uint4*>(&t[r][16 * v]) = x;
+      x[u] = *reinterpret_cast<const uint4*>(A + (size_t)(r0 + r) * lda + c0 + 16 * v);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    const int r = e >> 4, v = e & 15;
+    *reinterpret_cast<uint4*>(&t[r * TR_LDW + ((4 * v + 8 * (r >> 4)) & 63)]) = x[u];
   }
   __syncthreads();
-  {
-    const int c = threadIdx.x >> 2, v = threadIdx.x & 3;  // output row c0 + c, bytes 16 v ..
-    if (c0 + c < cols && r0 + 16 * v < ldt) {
-      uint32_t w[4];
+  const int lane = threadIdx.x & 31;
+  const int g = 8 * (threadIdx.x >> 5) + (lane >> 2), v = lane & 3;  // columns 4 g .., rows 16 v ..
+  const int wg = (g + 8 * v) & 63;                                    // rotated word of column group g
+  uint32_t out[4][4];  // out[k][h]: column 4 g + k, rows 16 v + 4 h .. 16 v + 4 h + 3
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        w[q] = (uint32_t)t[16 * v + 4 * q][c] | ((uint32_t)t[16 * v + 4 * q + 1][c] << 8) |
-               ((uint32_t)t[16 * v + 4 * q + 2][c] << 16) | ((uint32_t)t[16 * v + 4 * q + 3][c] << 24);
-      *reinterpret_cast<uint4*>(B + (size_t)(c0 + c) * ldt + r0 + 16 * v) = make_uint4(w[0], w[1], w[2], w[3]);
+  for (int h = 0; h < 4; ++h) {
+    uint32_t w[4], c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = t[(16 * v + 4 * h + i) * TR_LDW + wg];
+    transpose4x4(w, c);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k][h] = c[k];
+  }
+  if (r0 + 16 * v < ldt) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = c0 + 4 * g + k;
+      if (c < cols)
+        *reinterpret_cast<uint4*>(B + (size_t)c * ldt + r0 + 16 * v) =
+            make_uint4(out[k][0], out[k][1], out[k][2], out[k][3]);
     }
   }
 }
 
 void launch_u8_transpose(int rows, int cols, const uint8_t* A, int lda, uint8_t* B, int ldt, cudaStream_t st) {
   if (rows == 0 || cols == 0) return;
-  u8_transpose_kernel<<<dim3(ceil_div(cols, 64), ceil_div(rows, 64)), 256, 0, st>>>(rows, cols, A, lda, B, ldt);
+  u8_transpose_kernel<<<dim3(ceil_div(cols, TR_C), ceil_div(rows, TR_R)), 256, 0, st>>>(rows, cols, A, lda, B, ldt);
   note_launch();
 }
 

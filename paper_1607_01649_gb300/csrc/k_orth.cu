@@ -271,8 +271,18 @@ __global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__
     i = j;
     j = t;
   }
-  double s = 0.0;
-  for (int z = 0; z < splits; ++z) s += P[(size_t)z * l * l + (size_t)i * l + j];
+  // eight interleaved binary64 sums (a fixed order), so that eight loads per
+  // thread are in flight instead of one
+  const double* p = P + (size_t)i * l + j;
+  const size_t ll = (size_t)l * l;
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int z = 0;
+  for (; z + 7 < splits; z += 8) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] += p[(size_t)(z + q) * ll];
+  }
+  for (; z < splits; ++z) a[0] += p[(size_t)z * ll];
+  const double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   G[idx] = s;
   if (Gf) Gf[idx] = (float)s;
 }

@@ -429,7 +429,11 @@ def run_ours(a):
     elif prec == rs.RSVD_F32:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
 
-    # ---- e2e: host buffers in pinned memory, copies inside the timed region
+    # ---- e2e: the C-ABI call with HOST buffers (pinned).  The mixed paths read
+    # A exactly once, in the conversion pass, so A is passed as the host
+    # pointer and read over the host link inside that pass (no device copy);
+    # U, D, V are written to host memory by the kernels.  The binary32 path
+    # reads A 2q + 2 times, so there A is copied in and U, D, V copied out.
     e2e = None
     if not a.no_e2e:
         Ah = torch.empty(m, n, dtype=torch.float32, pin_memory=True)
@@ -437,17 +441,24 @@ def run_ours(a):
         Uh = torch.empty(m, k, dtype=torch.float32, pin_memory=True)
         Dh = torch.empty(k, dtype=torch.float64, pin_memory=True)
         Vh = torch.empty(n, k, dtype=torch.float32, pin_memory=True)
+        zero_copy = prec in (rs.RSVD_MIXED_BF16, rs.RSVD_MIXED_FP8)
         steps_e2e = max(1, min(a.steps, 5))
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for i in range(steps_e2e):
-            A.copy_(Ah, non_blocking=True)
-            solve(a.seed + 200 + i)
-            Uh.copy_(U, non_blocking=True)
-            Dh.copy_(D, non_blocking=True)
-            Vh.copy_(V, non_blocking=True)
+            if zero_copy:
+                prm.seed = a.seed + 200 + i
+                code = rs.rsvd_fixed_rank(h, m, n, Ah, n, prm, Uh, k, Dh, Vh, k, ws)
+                if code != rs.RSVD_OK:
+                    raise rs.RsvdError(code, rs.last_error(h))
+            else:
+                A.copy_(Ah, non_blocking=True)
+                solve(a.seed + 200 + i)
+                Uh.copy_(U, non_blocking=True)
+                Dh.copy_(D, non_blocking=True)
+                Vh.copy_(V, non_blocking=True)
         f1.record(stream)
         barrier()
         ems = f0.elapsed_time(f1)
@@ -457,7 +468,9 @@ def run_ours(a):
             ems = float(t.item())
         e2e = {"value": world * steps_e2e / (ems / 1000.0), "unit": "solves/s",
                "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": (m * k + n * k) * 4 + k * 8,
-               "steps": steps_e2e}
+               "steps": steps_e2e,
+               "mode": ("pinned host A, U, D, V passed to rsvd_fixed_rank; A read over the host link by the "
+                        "conversion pass" if zero_copy else "pinned host A copied in, U, D, V copied out")}
         del Ah
 
     # ---- comparators on the same matrix (1 timed solve each): the plain

@@ -112,6 +112,13 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
                                 size_t* bytes);
 
 /* Fixed-rank randomized SVD (Sec. 8.1, Fig. RSVDP_stabilized, + Sec. 3 Stage B).
+ *   A, U, D, V may be device memory or host memory the device can access:
+ *   pinned host memory (cudaHostAlloc / cudaHostRegister, mapped at the same
+ *   address under unified addressing), or any host memory on devices with
+ *   pageable-memory access; anything else is RSVD_E_INVALID.  The mixed
+ *   paths (RSVD_MIXED_BF16, RSVD_MIXED_FP8) read A exactly once, in the
+ *   conversion pass, so a host A costs one pass at the host link's bandwidth
+ *   and no device copy; the binary32/64 paths read A 2q + 2 times.
  *   A  : m x n, lda >= n, double (RSVD_F64) or float (others).
  *   U  : m x kk output, ldu >= kk, same type as A;  kk = k, or l with
  *        RSVD_FLAG_RETURN_FULL_L.

@@ -95,6 +95,27 @@ FixedLayout fixed_layout(void* ws, int m, int n, int l, int kk, int prec, int sm
   return L;
 }
 
+// Whether the handle's device can read and write p directly: device or
+// managed memory; host memory registered with (or allocated by) the CUDA
+// runtime and mapped at the same address; or pageable host memory on a
+// device with pageable-memory access (address translation services).
+bool device_accessible(rsvd_handle_t h, const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice) return a.device == h->device;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer == p;
+  int pageable = 0;
+  if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return pageable != 0;
+}
+
 rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda, const rsvd_params* p,
                            const void* U, int ldu, const void* D, const void* V, int ldv, int* kk_out) {
   if (!h) return RSVD_E_INVALID;
@@ -114,6 +135,15 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   if (lda < n) return fail(h, RSVD_E_INVALID, "lda %d < n %d", lda, n);
   if (ldu < kk || ldv < kk) return fail(h, RSVD_E_INVALID, "ldu/ldv smaller than the output rank %d", kk);
   if (!A || !U || !D || !V) return fail(h, RSVD_E_INVALID, "NULL matrix pointer");
+  return RSVD_OK;
+}
+
+rsvd_status check_access(rsvd_handle_t h, const void* A, const void* U, const void* D, const void* V) {
+  const void* ptrs[4] = {A, U, D, V};
+  const char* names[4] = {"A", "U", "D", "V"};
+  for (int i = 0; i < 4; ++i)
+    if (!device_accessible(h, ptrs[i]))
+      return fail(h, RSVD_E_INVALID, "%s is not memory the device can access (pin host buffers)", names[i]);
   return RSVD_OK;
 }
 
@@ -898,6 +928,7 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
   rsvd_status st = validate_fixed(handle, m, n, A, lda, params, U, ldu, D, V, ldv, &kk);
   if (st != RSVD_OK) return st;
   if (params->k == 0) return RSVD_OK;
+  if ((st = check_access(handle, A, U, D, V)) != RSVD_OK) return st;
   const int l = params->k + params->p;
   cudaStream_t s = (cudaStream_t)stream;
   size_t need = 0;

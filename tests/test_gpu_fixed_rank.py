@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import exp_decay_matrix, lowrank_np, poly_spectrum, exact_rank_matrix
+from workloads import exp_decay_matrix, lowrank_np, poly_spectrum, exact_rank_matrix, poly_decay_matrix_np
 
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
@@ -107,3 +107,35 @@ def test_deterministic_bits(lib):
     r2 = _np(*lib.fixed_rank(_t(A), 30, 10, 2, seed=9, prec=lib.RSVD_F32))
     for a, b in zip(r1, r2):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec_name", ["RSVD_MIXED_BF16", "RSVD_MIXED_FP8"])
+def test_host_buffers_zero_copy(lib, prec_name):
+    """The mixed paths read A once, in the conversion pass: a pinned host A and
+    pinned host outputs give the same bits as device buffers.  Pageable host
+    memory is either accepted (devices with pageable-memory access) with the
+    same bits, or refused before anything is launched."""
+    import torch
+    prec = getattr(lib, prec_name)
+    m, n, k, p, q, seed = 3000, 2048, 40, 24, 1, 3
+    A = torch.from_numpy(poly_decay_matrix_np(m, n, seed=5)).cuda()
+    Ud, Dd, Vd = lib.fixed_rank(A, k, p, q, seed=seed, prec=prec)
+    h = lib.handle()
+    prm = lib.make_params(k, p, q, seed=seed, prec=prec, flags=lib.RSVD_FLAG_SYNC)
+    ws = torch.empty(lib.rsvd_workspace_size(h, m, n, prm), dtype=torch.uint8, device="cuda")
+    Ah = A.cpu().pin_memory()
+    U = torch.empty(m, k).pin_memory()
+    D = torch.empty(k, dtype=torch.float64).pin_memory()
+    V = torch.empty(n, k).pin_memory()
+    assert lib.rsvd_fixed_rank(h, m, n, Ah, n, prm, U, k, D, V, k, ws) == lib.RSVD_OK
+    torch.cuda.synchronize()
+    assert torch.equal(D, Dd.cpu()) and torch.equal(U, Ud.cpu()) and torch.equal(V, Vd.cpu())
+    Ap = A.cpu()
+    D.zero_()
+    code = lib.rsvd_fixed_rank(h, m, n, Ap, n, prm, U, k, D, V, k, ws)
+    torch.cuda.synchronize()
+    assert code in (lib.RSVD_OK, lib.RSVD_E_INVALID)
+    if code == lib.RSVD_OK:
+        assert torch.equal(D, Dd.cpu())
+    else:
+        assert "not memory the device can access" in lib.last_error(h)

@@ -385,20 +385,61 @@ def run_ours(a):
             a2 += float((Ab * Ab).sum())
         return (f2 / a2) ** 0.5, a2 ** 0.5
 
+    def spectral_rel(Uo, Do, Vo, iters=30, b=4):
+        """||A - U D V^T||_2 / ||A||_2 by a randomized block power iteration
+        (b columns, `iters` steps) with the factorization applied implicitly:
+        products with A in binary32 (no TF32; A is binary32 data), everything
+        else in float64.  Returns (estimate, last relative change of the
+        estimate, ||A||_2 estimate)."""
+        g = torch.Generator(device=dev)
+        g.manual_seed(12345)
+        Ud, Vd, Dd = Uo.double(), Vo.double(), Do.double()
+        prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+
+        def apply(X, resid, trans):
+            out = (A.T @ X.float() if trans else A @ X.float()).double()
+            if resid:
+                out -= (Vd @ (Dd[:, None] * (Ud.T @ X))) if trans else (Ud @ (Dd[:, None] * (Vd.T @ X)))
+            return out
+
+        def power(resid):
+            X = torch.randn(n, b, dtype=torch.float64, device=dev, generator=g)
+            est, prev = 0.0, 0.0
+            for _ in range(iters):
+                X, _ = torch.linalg.qr(X)
+                Y = apply(X, resid, False)
+                Z = apply(Y, resid, True)
+                prev, est = est, float(torch.linalg.norm(Z, 2, dim=0).max()) ** 0.5
+                X = Z
+            return est, abs(est - prev) / est if est > 0 else 0.0
+
+        try:
+            r, conv = power(True)
+            a2, _ = power(False)
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+        return r / a2, conv, a2
+
     res_rel, fro_a = fro_rel(U, D, V)
+    spec_rel, spec_conv, spec_a = spectral_rel(U, D, V)
     if a.workload == "pca":
         # the signal's singular values (the noise moves them by about its norm)
         sig_true = torch.linspace(100.0, 1.0, 64, dtype=torch.float64, device=dev)[:k]
         nk = min(k, 48)
         d_rel = float(((D[:nk] - sig_true[:nk]).abs() / sig_true[:nk]).max())
         err = {"max_rel_err_sigma_1..48_vs_signal": d_rel, "fro_residual_rel": res_rel,
-               "noise_floor_rel": 1e-3 * (m * n) ** 0.5 / fro_a}
+               "noise_floor_rel": 1e-3 * (m * n) ** 0.5 / fro_a,
+               "spectral_residual_rel": spec_rel, "spectral_estimate_last_rel_change": spec_conv,
+               "sigma_k+1_rel(noise, sqrt(m)+sqrt(n) times 1e-3)": 1e-3 * (m ** 0.5 + n ** 0.5) / spec_a}
     else:
         sig_true = torch.arange(1, k + 1, dtype=torch.float64, device=dev).pow(-1.5)
         d_rel = float(((D - sig_true).abs() / sig_true).max())
         fro_opt = float(torch.arange(k + 1, min(m, n) + 1, dtype=torch.float64).pow(-3.0).sum().sqrt())
         err = {"max_rel_err_sigma_1..k_vs_construction": d_rel, "fro_residual_rel": res_rel,
-               "fro_residual_optimal_rel(Eckart-Young)": fro_opt / fro_a}
+               "fro_residual_optimal_rel(Eckart-Young)": fro_opt / fro_a,
+               "spectral_residual_rel": spec_rel, "spectral_estimate_last_rel_change": spec_conv,
+               "sigma_k+1_rel(Eckart-Young)": (k + 1) ** -1.5}
 
     # ---- roofline of the dominant kernel: the tcgen05 sketch product
     roof = None

@@ -934,7 +934,7 @@ void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const i
   note_launch();
 }
 
-// ------------------------------------------------------------ orth driver --
+// ------------------------------------------------------- orth entry points --
 size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize) {
   Carver c(nullptr);
   c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);  // Gram partials

@@ -152,6 +152,23 @@ def dist_setup(a):
     return world, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the process group (x itself when there
+    is none): the job's time is its slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, units_per_rank, ms):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, over the slowest rank's time `ms`."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -360,15 +377,12 @@ def run_ours(a):
     ms = e0.elapsed_time(e1)
     sk_ms, sk_n = rs.rsvd_profile_read(h, 0)
     pj_ms, pj_n = rs.rsvd_profile_read(h, 1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     st = rs.rsvd_query_status(h, ws)
     if st != rs.RSVD_OK:
         raise rs.RsvdError(st, "device status after timing")
     ms_per_step = ms / a.steps
-    value = world * a.steps / (ms / 1000.0)
+    value = replica_throughput(world, a.steps, ms)
     diag = rs.status_block(ws)
 
     # ---- accuracy of the last solve (not timed): singular values against the
@@ -502,12 +516,8 @@ def run_ours(a):
                 Vh.copy_(V, non_blocking=True)
         f1.record(stream)
         barrier()
-        ems = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * steps_e2e / (ems / 1000.0), "unit": "solves/s",
+        ems = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+        e2e = {"value": replica_throughput(world, steps_e2e, ems), "unit": "solves/s",
                "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": (m * k + n * k) * 4 + k * 8,
                "steps": steps_e2e,
                "mode": ("pinned host A, U, D, V passed to rsvd_fixed_rank; A read over the host link by the "
@@ -758,12 +768,8 @@ def run_batched(a):
     barrier()
     clk = clocks.stop()
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
-    ms = ev[0].elapsed_time(ev[-1])
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.count * a.steps / (ms / 1000.0)
+    ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dist, dev)
+    value = replica_throughput(world, a.count * a.steps, ms)
     status = plan.status[:a.count].cpu().numpy()
     ranks = plan.rank[:a.count].cpu().numpy().astype(np.int64)
     errs = plan.err[:a.count].cpu().numpy()
@@ -818,13 +824,9 @@ def run_batched(a):
                     h_.copy_(d_, non_blocking=True)
             f1.record(side)
         barrier()
-        ems = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(f0.elapsed_time(f1), dist, dev)
         nb = lambda t: t.numel() * t.element_size()
-        e2e = {"value": world * a.count * steps_e2e / (ems / 1000.0), "unit": "solves/s",
+        e2e = {"value": replica_throughput(world, a.count * steps_e2e, ems), "unit": "solves/s",
                "h2d_bytes_per_step": nb(plan.A),
                "d2h_bytes_per_step": nb(plan.U) + nb(plan.V) + nb(plan.D) + nb(plan.rank) + nb(plan.err),
                "steps": steps_e2e}

@@ -83,7 +83,7 @@ typedef enum { RSVD_DT_F64 = 0, RSVD_DT_F32 = 1, RSVD_DT_BF16 = 2 } rsvd_dtype;
 enum {
   RSVD_FLAG_RETURN_FULL_L = 1, /* return all l = k + p triplets instead of k */
   RSVD_FLAG_SYNC = 2,          /* block until the work ends; return the device status */
-  RSVD_FLAG_CERTIFY = 4,       /* reserved: a-posteriori certificate (Sec. 14) */
+  RSVD_FLAG_CERTIFY = 4,       /* reserved; the a-posteriori certificate is rsvd_certify */
   RSVD_FLAG_USE_CONTROLLER = 8 /* rsvd_adaptive_tol: learned (l, q) controller */
 };
 
@@ -365,6 +365,24 @@ rsvd_status rsvd_controller_fallback(rsvd_handle_t handle, int mode);
  * est[0] = Frobenius residual estimate / ||A||_F, est[1] = spectral bound /
  * ||A||_F (Lemma thm:aposteriori).  info: 5 ints, est: 2 doubles (host). */
 rsvd_status rsvd_controller_last(rsvd_handle_t handle, int* info, double* est);
+
+/* A-posteriori certificate (Sec. 14: eq. infomm and Lemma thm:aposteriori)
+ * for any rank-r factorization A ~= U diag(D) V^T in binary32: with G = 16
+ * columns of the Philox stream 2 under `seed` (rsvd_gaussian stream_id 2),
+ * E = A G - U (D (V^T G)) and
+ *   out[0] = sqrt(mean_i ||E(:, i)||^2), an unbiased estimate of ||A - U D V^T||_F^2
+ *            under the square root (E ||E g||^2 = ||A - U D V^T||_F^2),
+ *   out[1] = 10 sqrt(2/pi) max_i ||E(:, i)||, a bound on ||A - U D V^T||_2 that
+ *            holds with probability at least 1 - 10^-16,
+ *   out[2] = ||A||_F  (out: 3 doubles, host).
+ * A m x n (lda >= n), U m x r (ldu >= r), D r doubles, V n x r (ldv >= r),
+ * device memory or device-accessible host memory; 0 <= r <= 1024 (r = 0
+ * certifies the zero approximation).  Reads A once.  Synchronizes `stream`.
+ * Workspace: rsvd_certify_workspace_size bytes, 256-byte aligned. */
+rsvd_status rsvd_certify_workspace_size(rsvd_handle_t handle, int m, int n, int r, size_t* bytes);
+rsvd_status rsvd_certify(rsvd_handle_t handle, int m, int n, const float* A, int lda, int r, const float* U,
+                         int ldu, const double* D, const float* V, int ldv, uint64_t seed, double* out,
+                         void* workspace, size_t ws_bytes, rsvd_stream_t stream);
 
 /* Allocation-free variant of rsvd_sketch for RSVD_MIXED_BF16 (the paper has
  * no counterpart: this is a deployment convenience).  For callers that may

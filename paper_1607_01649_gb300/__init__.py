@@ -52,7 +52,7 @@ EXPORTED = [
     "rsvd_probe_workspace_size", "rsvd_probe_features", "rsvd_mlp_workspace_size", "rsvd_mlp_forward",
     "rsvd_mlp_grad", "rsvd_mlp_train_step", "rsvd_controller_attach", "rsvd_controller_last",
     "rsvd_controller_fallback", "rsvd_batched_variants", "rsvd_batched_variant_info", "rsvd_batched_set_variant",
-    "rsvd_batched_get_variant", "rsvd_batched_autotune",
+    "rsvd_batched_get_variant", "rsvd_batched_autotune", "rsvd_certify_workspace_size", "rsvd_certify",
 ]
 
 CTRL_D_IN = 17
@@ -116,6 +116,8 @@ def load():
         "rsvd_batched_set_variant": [vp, i],
         "rsvd_batched_get_variant": [vp, ctypes.POINTER(i)],
         "rsvd_batched_autotune": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp, vp],
+        "rsvd_certify_workspace_size": [vp, i, i, i, ctypes.POINTER(sz)],
+        "rsvd_certify": [vp, i, i, vp, i, i, vp, i, vp, vp, i, u64, vp, vp, sz, vp],
         "rsvd_probe_workspace_size": [vp, i, i, ctypes.POINTER(sz)],
         "rsvd_probe_features": [vp, i, i, vp, i, u64, vp, vp, vp, sz, vp],
         "rsvd_mlp_workspace_size": [vp, i, ctypes.POINTER(sz)],
@@ -238,6 +240,23 @@ def rsvd_batched_autotune(h, count, m, n, A, lda, params, U, D, V, rank_out, err
                                         _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream), ms,
                                         ctypes.byref(var))
     return code, var.value, list(ms)
+
+
+def certify(A, U, D, V, seed=0, stream=None):
+    """rsvd_certify: (Frobenius estimate, spectral bound, ||A||_F) of
+    A - U diag(D) V^T from 16 Gaussian columns of Philox stream 2 (Sec. 14).
+    A, U, V float32 and D float64, CUDA or pinned host tensors."""
+    h = handle(A.device.index if A.is_cuda else 0)
+    m, n = A.shape
+    r = 0 if U is None else U.shape[1]
+    sz = ctypes.c_size_t()
+    _check(load().rsvd_certify_workspace_size(h, m, n, r, ctypes.byref(sz)), h)
+    ws = _empty_ws(sz.value, A.device if A.is_cuda else "cuda")
+    out = (ctypes.c_double * 3)()
+    _check(load().rsvd_certify(h, m, n, _ptr(A), A.stride(0), r, _ptr(U), U.stride(0) if r else 1, _ptr(D),
+                               _ptr(V), V.stride(0) if r else 1, int(seed), out, _ptr(ws), ws.numel(),
+                               _stream(stream)), h)
+    return out[0], out[1], out[2]
 
 
 def rsvd_query_status(h, ws, stream=None):

@@ -634,6 +634,19 @@ void launch_ctrl_features(int m, int n, const double* Gram, int nfro, const doub
   note_launch();
 }
 
+// ||A||_F^2 from the thin sketch's partial sums, in a fixed order.
+__global__ void fro2_reduce_kernel(int nfro, const double* __restrict__ fro2p, RsvdCtrlBlock* blk) {
+  if (threadIdx.x != 0) return;
+  double f2 = 0.0;
+  for (int p = 0; p < nfro; ++p) f2 += fro2p[p];
+  blk->fro2 = f2;
+}
+
+void launch_fro2_reduce(int nfro, const double* fro2p, RsvdCtrlBlock* blk, cudaStream_t s) {
+  fro2_reduce_kernel<<<1, 32, 0, s>>>(nfro, fro2p, blk);
+  note_launch();
+}
+
 void launch_ctrl_decide(RsvdCtrlBlock* blk, float quantile, int lmax, cudaStream_t s) {
   ctrl_decide_kernel<<<1, 32, 0, s>>>(blk, quantile, lmax);
   note_launch();

@@ -108,6 +108,7 @@ int launch_thin_sketch(int m, int n, const float* A, int lda, const float* G, fl
 void launch_ctrl_features(int m, int n, const double* Gram, int nfro, const double* fro2p, RsvdCtrlBlock* blk,
                           cudaStream_t s);
 void launch_ctrl_decide(RsvdCtrlBlock* blk, float quantile, int lmax, cudaStream_t s);
+void launch_fro2_reduce(int nfro, const double* fro2p, RsvdCtrlBlock* blk, cudaStream_t s);
 size_t mlp_workspace_bytes(int batch);
 // mode -1: logits only (no workspace); 0: gradient into grad; 1: Adam step on th
 cudaError_t launch_mlp(int mode, int batch, const float* X, const int* yl, const int* yq, float lam,

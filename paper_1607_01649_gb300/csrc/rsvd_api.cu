@@ -1435,4 +1435,48 @@ rsvd_status rsvd_controller_last(rsvd_handle_t handle, int* info, double* est) {
   return RSVD_OK;
 }
 
+rsvd_status rsvd_certify_workspace_size(rsvd_handle_t handle, int m, int n, int r, size_t* bytes) {
+  if (!handle || !bytes) return RSVD_E_INVALID;
+  if (m < 1 || n < 1 || r < 0 || r > 1024) return fail(handle, RSVD_E_INVALID, "need m, n >= 1 and 0 <= r <= 1024");
+  *bytes = ctrl_layout(nullptr, m, n, r > 0 ? r : 1, handle->sms, 0).bytes;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_certify(rsvd_handle_t handle, int m, int n, const float* A, int lda, int r, const float* U, int ldu,
+                         const double* D, const float* V, int ldv, uint64_t seed, double* out, void* workspace,
+                         size_t ws_bytes, rsvd_stream_t stream) {
+  size_t need = 0;
+  rsvd_status st = rsvd_certify_workspace_size(handle, m, n, r, &need);
+  if (st != RSVD_OK) return st;
+  if (!A || !out || (r > 0 && (!U || !D || !V))) return fail(handle, RSVD_E_INVALID, "NULL argument");
+  if (lda < n || (r > 0 && (ldu < r || ldv < r))) return fail(handle, RSVD_E_INVALID, "leading dimension too small");
+  if (!workspace || ws_bytes < need)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  if (!device_accessible(handle, A) || (r > 0 && (!device_accessible(handle, U) || !device_accessible(handle, D) ||
+                                                  !device_accessible(handle, V))))
+    return fail(handle, RSVD_E_INVALID, "an input is not memory the device can access (pin host buffers)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int sms = handle->sms;
+  const CtrlLayout L = ctrl_layout(workspace, m, n, r > 0 ? r : 1, sms, 0);
+  cudaMemsetAsync(L.blk, 0, sizeof(RsvdCtrlBlock), s);
+  // E = A G - U (D (V^T G)), G = 16 columns of Philox stream 2
+  launch_gaussian(n, CTRL_NC, seed, 2u, 0, RSVD_DT_F32, L.G, CTRL_NC, s);
+  const int nfro = launch_thin_sketch(m, n, A, lda, L.G, L.Yp, L.Y, L.fro2p, sms, s);
+  launch_fro2_reduce(nfro, L.fro2p, L.blk, s);
+  if (r > 0) launch_gemm_simt<float>(true, r, CTRL_NC, n, V, ldv, L.G, CTRL_NC, L.T, CTRL_NC, L.Tpart, sms, s);
+  launch_judge(m, r, L.Y, U, ldu, D, L.T, L.rpart, 0.0, 1.0, L.blk, sms, s);
+  st = check_launch(handle, "rsvd_certify");
+  if (st != RSVD_OK) return st;
+  RsvdCtrlBlock hb;
+  cudaError_t e = cudaMemcpyAsync(&hb, L.blk, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "certificate read: %s", cudaGetErrorString(e));
+  out[0] = sqrt(hb.est2 > 0.0 ? hb.est2 : 0.0);
+  out[1] = hb.spec_bound;
+  out[2] = sqrt(hb.fro2 > 0.0 ? hb.fro2 : 0.0);
+  if (!isfinite(out[0]) || !isfinite(out[2])) return fail(handle, RSVD_E_NONFINITE, "non-finite certificate");
+  return RSVD_OK;
+}
+
 }  // extern "C"

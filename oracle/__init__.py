@@ -27,6 +27,10 @@ Parity status per function:
   products): pinned (the value set and all 256 codes from the format's
   definition, round trip, ties to even at every midpoint, saturation, brute
   force over 8000 values, exact products on representable operands).
+* nystrom (Fig. nystrom): pinned (exact recovery when rank(A) = k + p, the
+  Loewner order F F* <= A, the closed form A^1/2 (I - P) A^1/2 of the
+  residual, the explicit-inverse form of eq. spd_nystrom, the accuracy gain
+  over eq. spd_standard across seeds).
 """
 from .philox import (philox4x32_10, gaussian, omega_words, box_muller, seed_key,
                      STREAM_SKETCH, STREAM_ADAPTIVE, STREAM_CERTIFY, STREAM_ADAPTIVE2, STREAM_NORM)
@@ -36,3 +40,4 @@ from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_fi
                        adaptive_range_finder)
 from . import controller
 from . import fp8
+from .nystrom import nystrom

@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="poly", choices=["poly", "pca", "controller", "batched"],
+    ap.add_argument("--workload", default="poly", choices=["poly", "pca", "controller", "batched", "nystrom"],
                     help="poly: 32768^2 polynomial decay (bf16); pca: 2^20 x 4096 PCA matrix (e4m3); "
                          "controller: a stream of square matrices solved to tol 1e-4 (learned controller); "
                          "batched: 4096 kernel-matrix blocks to tol 1e-6 in one persistent launch")
@@ -68,7 +68,8 @@ def parse():
     dflt = {"poly": dict(prec="bf16", m=32768, n=32768, k=200, p=56, q=2, seed=2001, sample=8192),
             "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768),
             "controller": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=60000, sample=0),
-            "batched": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=4001, sample=0)}[a.workload]
+            "batched": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=4001, sample=0),
+            "nystrom": dict(prec="f32", m=16384, n=16384, k=200, p=56, q=0, seed=5001, sample=4096)}[a.workload]
     for key, val in dflt.items():
         if getattr(a, key) is None:
             setattr(a, key, val)
@@ -674,6 +675,128 @@ def run_controller(a):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------- nystrom -------
+def run_nystrom(a):
+    """rsvd_nystrom (Fig. nystrom) on a 16384^2 SPD matrix V diag(j^-1.5) V^T,
+    binary32; beside it the fixed-rank RSVD with the same two passes over A
+    (q = 0) and with one power step (q = 1), their spectral residuals, and the
+    float64 oracle on a sample."""
+    import numpy as np
+    import torch
+    import paper_1607_01649_gb300 as rs
+    from workloads import spd_matrix, spd_matrix_np
+    import oracle
+    dev = torch.device("cuda", 0)
+    n, k, p = a.n, a.k, a.p
+    l = k + p
+    A = spd_matrix(n, seed=a.seed, device=dev)
+    h = rs.handle(0)
+    prm = rs.make_params(k, p, 0, seed=a.seed, prec=rs.RSVD_F32, flags=0)
+    ws = torch.empty(rs.rsvd_workspace_size(h, n, n, prm), dtype=torch.uint8, device=dev)
+    U = torch.empty(n, k, device=dev)
+    L = torch.empty(k, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve(seed):
+        prm.seed = seed
+        code = rs.rsvd_nystrom(h, n, A, n, prm, U, k, L, ws)
+        if code != rs.RSVD_OK:
+            raise rs.RsvdError(code, rs.last_error(h))
+
+    for i in range(a.warmup):
+        solve(a.seed + i)
+    torch.cuda.synchronize()
+    launches0 = rs.rsvd_kernel_launches(h)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(a.steps):
+        solve(a.seed + 100 + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = rs.rsvd_kernel_launches(h) - launches0
+    st = rs.rsvd_query_status(h, ws)
+    if st != rs.RSVD_OK:
+        raise rs.RsvdError(st, "device status after timing")
+
+    def spectral(apply_resid, iters=30, b=4):
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        X = torch.randn(n, b, dtype=torch.float64, device=dev, generator=g)
+        est = prev = 0.0
+        for _ in range(iters):
+            X, _ = torch.linalg.qr(X)
+            Z = apply_resid(apply_resid(X))
+            prev, est = est, float(torch.linalg.norm(Z, 2, dim=0).max()) ** 0.5
+            X = Z
+        return est, abs(est - prev) / est if est > 0 else 0.0
+
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        Ud, Ld = U.double(), L.double()
+        ny, ny_conv = spectral(lambda X: (A @ X.float()).double() - Ud @ (Ld[:, None] * (Ud.T @ X)))
+        comps = {}
+        for q in (0, 1):
+            Ur, Dr, Vr = rs.fixed_rank(A, k, p, q, seed=a.seed + 100, prec=rs.RSVD_F32)
+            torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            Ur, Dr, Vr = rs.fixed_rank(A, k, p, q, seed=a.seed + 100, prec=rs.RSVD_F32)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            Urd, Drd, Vrd = Ur.double(), Dr.double(), Vr.double()
+            # A symmetric: A - U D V^T applied to X, and its transpose, alternate in the power iteration
+            est, conv = spectral(lambda X: (A @ X.float()).double() - 0.5 * (
+                Urd @ (Drd[:, None] * (Vrd.T @ X)) + Vrd @ (Drd[:, None] * (Urd.T @ X))))
+            comps["rsvd_fixed_rank_q%d" % q] = {"value": 1000.0 / g0.elapsed_time(g1), "unit": "solves/s",
+                                                "spectral_residual_rel_of_symmetrized": est}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+    fma = 2.0 * n * n * l + n * l * l
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    per_ms = ms / a.steps
+    achieved = 2.0 * fma / (per_ms / 1000.0) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+            "traffic": None, "algorithmic_flops": 2.0 * fma,
+            "kernel": "gemm_simt_kernel (A G and A Q, binary32 SIMT)",
+            "peak_source": "152 SMs x 128 binary32 lanes x 2 flops x 2.07 GHz",
+            "note": "whole solve time over the two products' FLOPs"}
+    cpu = None
+    if not a.no_cpu:
+        ns = min(a.sample, n)
+        As = spd_matrix_np(ns, seed=a.seed)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0 and reps < 20:
+            oracle.nystrom(As, k, p, a.seed)
+            reps += 1
+        t = (time.perf_counter() - t0) / reps
+        scale = (n / ns) ** 2
+        cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "float64 oracle nystrom on a %dx%d SPD matrix of the same family (k=%d p=%d), %d solve(s), "
+                         "%.3f s each, scaled by the n^2 ratio %.1f" % (ns, ns, k, p, reps, t, scale)}
+    line = {"metric": METRIC, "value": a.steps / (ms / 1000.0), "unit": "solves/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Nystrom EVD (Fig. nystrom), SPD %dx%d fp32 = V diag(j^-1.5) V^T, Haar V; "
+                                   "k=%d p=%d (l=%d)" % (n, n, k, p, l),
+                       "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB)" % (n * n * 4 / 1e9)},
+            "roofline": roof, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk,
+            "error": {"spectral_residual_rel": ny, "spectral_estimate_last_rel_change": ny_conv,
+                      "lambda_k+1_rel(Eckart-Young)": (k + 1) ** -1.5,
+                      "max_rel_err_lambda_1..k_vs_construction": float(
+                          ((L.cpu() - torch.arange(1, k + 1, dtype=torch.float64).pow(-1.5)).abs()
+                           / torch.arange(1, k + 1, dtype=torch.float64).pow(-1.5)).max())},
+            "comparators": comps}
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------- batched -------
 BATCH_TOL = 1e-6
 BATCH_R = 64
@@ -912,6 +1035,8 @@ def main():
     a = parse()
     if a.workload == "batched":
         (run_reference_batched if a.impl == "reference" else run_batched)(a)
+    elif a.workload == "nystrom":
+        run_nystrom(a)
     elif a.workload == "controller":
         run_controller(a)
     elif a.impl == "reference":

@@ -133,6 +133,27 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
                             const rsvd_params* params, void* U, int ldu, double* D, void* V,
                             int ldv, void* workspace, size_t ws_bytes, rsvd_stream_t stream);
 
+/* Eigenvalue decomposition of a symmetric positive semi-definite matrix by the
+ * Nystrom method (Fig. nystrom): G = randn(n, l) (the Omega stream of
+ * rsvd_fixed_rank), Y = A G, Q = orth(Y) (CholeskyQR2), B1 = A Q,
+ * B2 = Q^T B1 (symmetrized), B2 = C^T C (Cholesky), F = B1 C^-1,
+ * [U, Sigma, ~] = svd(F), Lambda = Sigma^2; A ~ U diag(Lambda) U^T =
+ * (A Q)(Q^T A Q)^-1 (A Q)^T.  Two passes over A, like the basic RSVD, with
+ * the accuracy of one more power step.  If Q^T A Q is singular to working
+ * precision (rank(A) < l) the Cholesky fails after its shifted restarts and
+ * the call reports RSVD_E_BREAKDOWN.
+ *   A   : n x n, lda >= n, symmetric (both triangles are read); double
+ *         (RSVD_F64) or float (RSVD_F32); device or device-accessible host memory.
+ *   params: k, p (l = k + p <= n), seed; q must be 0; prec RSVD_F32 or
+ *         RSVD_F64; flags RSVD_FLAG_RETURN_FULL_L (all l pairs), RSVD_FLAG_SYNC.
+ *   U   : n x kk output, ldu >= kk, same type as A; the largest-magnitude entry
+ *         of each u_i is positive.
+ *   Lam : kk doubles, descending.
+ * workspace: rsvd_workspace_size(handle, n, n, params) bytes, 256-byte aligned. */
+rsvd_status rsvd_nystrom(rsvd_handle_t handle, int n, const void* A, int lda, const rsvd_params* params,
+                         void* U, int ldu, double* Lam, void* workspace, size_t ws_bytes,
+                         rsvd_stream_t stream);
+
 /* Tolerance-driven randomized SVD (Sec. 12.3, Fig. greedy_blocked; stopping on
  * the Frobenius norm of the explicitly updated remainder, Sec. 12.4):
  * blocks of b Gaussian columns (Philox stream 1, block t = columns t*b ..)

@@ -53,6 +53,7 @@ EXPORTED = [
     "rsvd_mlp_grad", "rsvd_mlp_train_step", "rsvd_controller_attach", "rsvd_controller_last",
     "rsvd_controller_fallback", "rsvd_batched_variants", "rsvd_batched_variant_info", "rsvd_batched_set_variant",
     "rsvd_batched_get_variant", "rsvd_batched_autotune", "rsvd_certify_workspace_size", "rsvd_certify",
+    "rsvd_nystrom",
 ]
 
 CTRL_D_IN = 17
@@ -117,6 +118,7 @@ def load():
         "rsvd_batched_get_variant": [vp, ctypes.POINTER(i)],
         "rsvd_batched_autotune": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp, vp, vp],
         "rsvd_certify_workspace_size": [vp, i, i, i, ctypes.POINTER(sz)],
+        "rsvd_nystrom": [vp, i, vp, i, P, vp, i, dp, vp, sz, vp],
         "rsvd_certify": [vp, i, i, vp, i, i, vp, i, vp, vp, i, u64, vp, vp, sz, vp],
         "rsvd_probe_workspace_size": [vp, i, i, ctypes.POINTER(sz)],
         "rsvd_probe_features": [vp, i, i, vp, i, u64, vp, vp, vp, sz, vp],
@@ -240,6 +242,28 @@ def rsvd_batched_autotune(h, count, m, n, A, lda, params, U, D, V, rank_out, err
                                         _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream), ms,
                                         ctypes.byref(var))
     return code, var.value, list(ms)
+
+
+def rsvd_nystrom(h, n, A, lda, params, U, ldu, Lam, ws, stream=None):
+    return load().rsvd_nystrom(h, n, _ptr(A), lda, ctypes.byref(params), _ptr(U), ldu, _ptr(Lam), _ptr(ws),
+                               ws.numel() if ws is not None else 0, _stream(stream))
+
+
+def nystrom(A, k, p=10, seed=0, prec=RSVD_F32, full=False, sync=True):
+    """A ~= U diag(Lam) U^T by rsvd_nystrom (Fig. nystrom) for a symmetric
+    positive semi-definite CUDA tensor A (float64 for RSVD_F64, else
+    float32).  Returns (U, Lam)."""
+    import torch
+    h = handle(A.device.index)
+    n = A.shape[0]
+    flags = (RSVD_FLAG_RETURN_FULL_L if full else 0) | (RSVD_FLAG_SYNC if sync else 0)
+    prm = make_params(k, p, 0, seed, prec, flags)
+    kk = k + p if full else k
+    U = torch.empty(n, kk, dtype=_prec_dtype(prec), device=A.device)
+    Lam = torch.empty(kk, dtype=torch.float64, device=A.device)
+    ws = _empty_ws(rsvd_workspace_size(h, n, n, prm), A.device)
+    _check(rsvd_nystrom(h, n, A, A.stride(0), prm, U, U.stride(0), Lam, ws), h)
+    return U, Lam
 
 
 def certify(A, U, D, V, seed=0, stream=None):

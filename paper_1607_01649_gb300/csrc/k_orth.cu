@@ -1036,6 +1036,42 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
   }
 }
 
+// G = (B + B^T) / 2 in binary64 (and rounded to binary32 for the binary32
+// Cholesky), l x l.
+template <typename T>
+__global__ void sym_gram_kernel(int l, const T* __restrict__ B, int ldb, double* __restrict__ G,
+                                float* __restrict__ Gf) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= l * l) return;
+  const int i = idx / l, j = idx % l;
+  const double v = 0.5 * ((double)B[(size_t)i * ldb + j] + (double)B[(size_t)j * ldb + i]);
+  G[idx] = v;
+  if (Gf) Gf[idx] = (float)v;
+}
+
+// The Nystrom factor of Fig. nystrom: B = C^T C (Cholesky of the symmetrized
+// l x l matrix B, C upper triangular; the kernel's shifted restart takes a
+// B that is not numerically positive definite) and Y <- Y C^-1 in place.
+// Uses the same workspace as run_orth.
+template <typename T, typename C>
+void run_chol_solve(int rows, int l, const T* B, int ldb, T* Y, int ldy, void* ws, DevStatus* st, int sms,
+                    cudaStream_t s) {
+  Carver c(ws);
+  c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
+  double* G = c.take<double>((size_t)l * l);
+  float* Gf = c.take<float>((size_t)l * l);
+  C* Ub = c.take<C>((size_t)l * l);
+  C* dinv = c.take<C>((size_t)l);
+  sym_gram_kernel<T><<<ceil_div(l * l, 256), 256, 0, s>>>(l, B, ldb, G, sizeof(C) == 4 ? Gf : nullptr);
+  note_launch();
+  launch_chol<C>(l, G, Gf, Ub, dinv, nullptr, st, 1, nullptr, s, nullptr);
+  launch_apply<T, C>(rows, l, Y, ldy, Ub, dinv, nullptr, 0, nullptr, s, nullptr);
+}
+
+template void run_chol_solve<float, float>(int, int, const float*, int, float*, int, void*, DevStatus*, int,
+                                           cudaStream_t);
+template void run_chol_solve<double, double>(int, int, const double*, int, double*, int, void*, DevStatus*, int,
+                                             cudaStream_t);
 template void run_orth<float, float>(int, int, float*, int, double*, __nv_bfloat16*, int, void*, DevStatus*,
                                      int, cudaStream_t, const int*);
 template void run_orth<double, double>(int, int, double*, int, double*, __nv_bfloat16*, int, void*,

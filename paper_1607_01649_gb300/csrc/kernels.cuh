@@ -32,6 +32,10 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
               int sms, cudaStream_t s, const int* skip = nullptr);
 template <typename T>
 void launch_copy_bf16(int rows, int l, const T* Y, int ldy, __nv_bfloat16* Yb, int lb, cudaStream_t s);
+// Nystrom factor: B = C^T C (Cholesky of the symmetrized l x l B), Y <- Y C^-1 (run_orth's workspace)
+template <typename T, typename C>
+void run_chol_solve(int rows, int l, const T* B, int ldb, T* Y, int ldy, void* ws, DevStatus* st, int sms,
+                    cudaStream_t s);
 // CholeskyQR2 with the apply Q = Y R^-1 on tensor cores (three-term split bf16); binary32 data
 size_t orth_tc_workspace_bytes(int rows, int l, int sms);
 void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,

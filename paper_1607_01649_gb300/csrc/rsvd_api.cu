@@ -79,6 +79,9 @@ FixedLayout fixed_layout(void* ws, int m, int n, int l, int kk, int prec, int sm
   size_t pw = simt_gemm_workspace(m, l, n, sms, es);
   const size_t pw2 = simt_gemm_workspace(n, l, m, sms, es);
   if (pw2 > pw) pw = pw2;
+  // the l x l product Q^T B1 of the Nystrom path (m = n), split over K = n
+  const size_t pw3 = simt_gemm_workspace(l, l, n, sms, es);
+  if (pw3 > pw) pw = pw3;
   if (sign_workspace_bytes(n, kk) > pw) pw = sign_workspace_bytes(n, kk);
   L.part = c.take<unsigned char>(pw);
   size_t ow = orth_workspace_bytes(m, l, sms, es);
@@ -182,6 +185,50 @@ rsvd_status fixed_rank_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, 
   launch_sign_fix<T, C>(n, kk, l, V, ldv, (C*)L.Wsel, L.part, s);
   launch_gemm_simt<T>(false, m, kk, l, Y, l, (const T*)L.Wsel, kk, U, ldu, nullptr, sms, s);
   return check_launch(h, "rsvd_fixed_rank");
+}
+
+// Lambda = Sigma^2 in place (kk values).
+__global__ void square_kernel(int kk, double* __restrict__ D) {
+  for (int i = threadIdx.x; i < kk; i += blockDim.x) D[i] = D[i] * D[i];
+}
+
+// Eigenvalue decomposition of a symmetric positive semi-definite A by the
+// Nystrom method (Fig. nystrom), SIMT products:
+//   G = randn(n, l); Y = A G; Q = orth(Y); B1 = A Q; B2 = Q^T B1;
+//   B2 = C^T C; F = B1 C^-1; [U, Sigma, ~] = svd(F); Lambda = Sigma^2,
+// with the SVD of F as in Stage B: F = Q_F R_F, one-sided Jacobi on R_F^T
+// (R_F^T J = W), so U = Q_F J and Sigma = the column norms of W.
+template <typename T, typename C>
+rsvd_status nystrom_simt(rsvd_handle_t h, int n, const T* A, int lda, const rsvd_params* p, T* U, int ldu,
+                         double* Lam, const FixedLayout& L, cudaStream_t s) {
+  const int l = p->k + p->p;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
+  const int sms = h->sms;
+  T* Om = (T*)L.Om;
+  T* Y = (T*)L.Ybuf;
+  T* Z = (T*)L.Zbuf;
+  T* part = (T*)L.part;
+  const int dt = sizeof(T) == 8 ? RSVD_DT_F64 : RSVD_DT_F32;
+  launch_gaussian(n, l, p->seed, 0u, 0, dt, Om, l, s);
+  // Q = orth(A G)
+  launch_gemm_simt<T>(false, n, l, n, A, lda, Om, l, Y, l, part, sms, s);
+  run_orth<T, C>(n, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  // B1 = A Q (in Z), B2 = Q^T B1 (l x l, in the n x l buffer of G)
+  launch_gemm_simt<T>(false, n, l, n, A, lda, Y, l, Z, l, part, sms, s);
+  launch_gemm_simt<T>(true, l, l, n, Y, l, Z, l, Om, l, part, sms, s);
+  // F = B1 C^-1, B2 = C^T C
+  run_chol_solve<T, C>(n, l, Om, l, Z, l, L.orthws, L.st, sms, s);
+  // F = Q_F R_F, SVD of R_F^T
+  run_orth<T, C>(n, l, Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  cudaError_t e = launch_jacobi<C>(l, L.Rb, (C*)L.Wt, (C*)L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<C>(l, kk, L.sigma, (const C*)L.Wt, (const C*)L.Jt, Lam, (C*)L.Wsel, (C*)L.Jsel, s);
+  // U = Q_F J, truncated to kk; the largest-magnitude entry of each u_i positive
+  launch_gemm_simt<T>(false, n, kk, l, Z, l, (const T*)L.Jsel, kk, U, ldu, nullptr, sms, s);
+  launch_sign_fix<T, C>(n, kk, l, U, ldu, (C*)L.Wsel, L.part, s);
+  square_kernel<<<1, 256, 0, s>>>(kk, Lam);
+  note_launch();
+  return check_launch(h, "rsvd_nystrom");
 }
 
 inline int round8(int v) { return (v + 7) / 8 * 8; }
@@ -962,6 +1009,34 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
   else
     st = fixed_rank_simt<float, float>(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V,
                                        ldv, L, s);
+  if (st != RSVD_OK) return st;
+  return finish_sync(handle, params, L.st, s);
+}
+
+rsvd_status rsvd_nystrom(rsvd_handle_t handle, int n, const void* A, int lda, const rsvd_params* params, void* U,
+                         int ldu, double* Lam, void* workspace, size_t ws_bytes, rsvd_stream_t stream) {
+  int kk = 0;
+  rsvd_status st = validate_fixed(handle, n, n, A, lda, params, U, ldu, Lam, U, ldu, &kk);
+  if (st != RSVD_OK) return st;
+  if (params->prec != RSVD_F32 && params->prec != RSVD_F64)
+    return fail(handle, RSVD_E_UNSUPPORTED, "rsvd_nystrom supports RSVD_F32 and RSVD_F64");
+  if (params->q != 0) return fail(handle, RSVD_E_UNSUPPORTED, "rsvd_nystrom has no power steps (q must be 0)");
+  if (params->k == 0) return RSVD_OK;
+  if ((st = check_access(handle, A, U, Lam, U)) != RSVD_OK) return st;
+  size_t need = 0;
+  st = rsvd_workspace_size(handle, n, n, params, &need);
+  if (st != RSVD_OK) return st;
+  if (!workspace || ws_bytes < need)
+    return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
+  if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  const int l = params->k + params->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  const FixedLayout L = fixed_layout(workspace, n, n, l, kk, params->prec, handle->sms);
+  cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
+  if (params->prec == RSVD_F64)
+    st = nystrom_simt<double, double>(handle, n, (const double*)A, lda, params, (double*)U, ldu, Lam, L, s);
+  else
+    st = nystrom_simt<float, float>(handle, n, (const float*)A, lda, params, (float*)U, ldu, Lam, L, s);
   if (st != RSVD_OK) return st;
   return finish_sync(handle, params, L.st, s);
 }

@@ -83,6 +83,15 @@ def exact_rank_matrix(m, n, rank, seed, cond=10.0):
     return lowrank_np(m, n, s, seed)
 
 
+def spd_matrix_np(n, seed, alpha=1.5, dtype=np.float64):
+    """Symmetric positive definite A = V diag(j^-alpha) V^T, V Haar (numpy)."""
+    rng = np.random.default_rng(seed)
+    V = haar_np(rng, n, n)
+    lam = np.arange(1, n + 1, dtype=np.float64) ** (-alpha)
+    A = (V * lam[None, :]) @ V.T
+    return (0.5 * (A + A.T)).astype(dtype)
+
+
 def pca_matrix_np(m, n, seed, rank=64, noise=1e-3, dtype=np.float32):
     """Small-size (CPU) instance of the PCA family, column-centred in float64."""
     rng = np.random.default_rng(seed)
@@ -129,6 +138,26 @@ def poly_decay_matrix(m=32768, n=32768, seed=2001, alpha=1.5, device="cuda"):
         V = haar_torch(n, r, gen, device, torch.float32)
         A = U @ V.T
         del U, V
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return A.contiguous()
+
+
+def spd_matrix(n=16384, seed=5001, alpha=1.5, device="cuda"):
+    """Symmetric positive definite A = V diag(j^-alpha) V^T, float32, Haar V,
+    synthesized on `device` (products in float32 without TF32), then made
+    exactly symmetric."""
+    torch = _torch()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        V = haar_torch(n, n, gen, device, torch.float32)
+        lam = torch.arange(1, n + 1, device=device, dtype=torch.float64).pow(-alpha).to(torch.float32)
+        A = (V * lam[None, :]) @ V.T
+        del V
+        A = 0.5 * (A + A.T)
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     return A.contiguous()

@@ -53,3 +53,21 @@ def test_create_without_device_is_an_error_not_a_crash(built_lib):
     h = ctypes.c_void_p()
     built_lib.rsvd_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
     assert built_lib.rsvd_create(ctypes.byref(h), 0) != 0
+
+
+def test_batched_variant_table_without_a_device(built_lib):
+    """The launch-variant table is host data: every variant keeps a number of
+    rows in flight that divides the binary64 fold length (256 rows), so the
+    fold points, and with them the results, are the same in every variant."""
+    n = ctypes.c_int()
+    assert built_lib.rsvd_batched_variants(ctypes.byref(n)) == 0 and n.value >= 2
+    seen = set()
+    for v in range(n.value):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        assert built_lib.rsvd_batched_variant_info(v, ctypes.byref(a), ctypes.byref(b)) == 0
+        assert a.value in (4, 8, 16, 32) and 256 % a.value == 0 and 1 <= b.value <= 4
+        seen.add((a.value, b.value))
+    assert len(seen) == n.value
+    a, b = ctypes.c_int(), ctypes.c_int()
+    assert built_lib.rsvd_batched_variant_info(n.value, ctypes.byref(a), ctypes.byref(b)) != 0
+    assert built_lib.rsvd_batched_variant_info(-1, ctypes.byref(a), ctypes.byref(b)) != 0

@@ -31,9 +31,23 @@ Parity status per function:
   Loewner order F F* <= A, the closed form A^1/2 (I - P) A^1/2 of the
   residual, the explicit-inverse form of eq. spd_nystrom, the accuracy gain
   over eq. spd_standard across seeds).
+* singlepass_evd, singlepass_svd (Figs. singlepass_herm, singlepass_gen):
+  pinned (exact recovery of rank-k inputs with C = Q* A Q, both
+  least-squares fits against their stationarity conditions solved as
+  Sylvester equations, the free / constrained / symmetrized fit ordering,
+  the section's loss of accuracy against two passes).  No GPU path yet.
+* srft_omega, rsvd_srft (eq. SRFT): pinned (orthonormal columns, numpy's FFT
+  as the subsampled transform, uniformity of D and S, prefix property, exact
+  recovery, accuracy near the Gaussian sketch).  No GPU path yet.
+* rsvd_block_krylov (Sec. "Extended sampling matrix"): pinned (q = 1 is
+  Fig. RSVD, exact recovery of rank q l, span of a blockwise orthonormalized
+  Krylov basis, residual below the power scheme's by nesting).  No GPU path yet.
+* rsvd_power_centred (implicit column centring for PCA): pinned (equals the
+  fixed-rank oracle on the explicitly centred matrix; 1* U = 0).  No GPU path yet.
 """
 from .philox import (philox4x32_10, gaussian, omega_words, box_muller, seed_key,
-                     STREAM_SKETCH, STREAM_ADAPTIVE, STREAM_CERTIFY, STREAM_ADAPTIVE2, STREAM_NORM)
+                     STREAM_SKETCH, STREAM_ADAPTIVE, STREAM_CERTIFY, STREAM_ADAPTIVE2, STREAM_NORM,
+                     STREAM_ROW, STREAM_SRFT_D, STREAM_SRFT_S)
 from .rsvd import orth, sign_normalize, stage_b, rsvd_basic, rsvd_power, rsvd_power_plain
 from .norms import fro_residual, spectral_residual, certificate, theorem_bounds
 from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_finder,
@@ -41,3 +55,7 @@ from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_fi
 from . import controller
 from . import fp8
 from .nystrom import nystrom
+from .singlepass import singlepass_evd, singlepass_svd
+from .srft import srft_omega, rsvd_srft
+from .krylov import rsvd_block_krylov
+from .centred import rsvd_power_centred

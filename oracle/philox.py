@@ -41,6 +41,9 @@ STREAM_ADAPTIVE = 1     # G blocks of the blocked adaptive range finder
 STREAM_CERTIFY = 2      # thin G of the a-posteriori certificate
 STREAM_ADAPTIVE2 = 3    # g_j of the vector-at-a-time adaptive range finder
 STREAM_NORM = 4         # start block of the spectral-norm estimator
+STREAM_ROW = 5          # G_r (row-space sketch) of the single-pass SVD
+STREAM_SRFT_D = 6       # phases of the SRFT's diagonal D
+STREAM_SRFT_S = 7       # sort keys that draw the SRFT's column subset S
 
 
 def philox4x32_10(counters, key):

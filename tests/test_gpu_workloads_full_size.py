@@ -1,0 +1,115 @@
+"""The two dense workloads at full size, through rsvd_fixed_rank (the call the
+benchmark times, with the same sizes, precisions and launch configuration),
+checked by properties that hold at any size because the float64 oracle cannot
+run there:
+
+* 32768 x 32768 polynomial decay (sigma_j = j^-1.5, Haar U and V), bf16
+  tensor-core sketches, k = 200, p = 56, q = 2;
+* 2^20 x 4096 PCA matrix (rank-64 signal 100 -> 1 plus N(0, 1e-6) noise,
+  column-centred), e4m3 sketches, k = 64, p = 64, q = 1.
+
+What is checked, and why it must hold:
+* d_i <= sigma_i (1 + 1e-4): the computed values are the singular values of
+  Q^T A, a compression of A, so they cannot exceed A's (up to the split-bf16
+  projection's rounding, ~1e-8 here);
+* d_i >= sigma_i (1 - 3%) for the poly matrix: the method's approximation
+  error at l = 256, q = 2 (Sec. 8.1; 0.8% measured);
+* Eckart-Young: the Frobenius residual is at least the optimum over all
+  rank-k matrices, and the method stays within 1% of it;
+* ||(A - U D V^T) v_i|| / ||v_i|| is at most the spectral residual, about
+  sigma_{k+1} here (checked at 2 sigma_{k+1} on sampled right singular
+  vectors; for orthonormal V the vector is A v_i - d_i u_i);
+* U^T U = V^T V = I to binary32 accuracy (the lift is a binary32 product);
+* PCA: the signal's singular values move by about eta^2 (m + n) / (2 sigma)
+  under noise of entry size eta (8e-4 relative for sigma_48; the column
+  centring adds about chi^2 / (2 m), under 3e-5 at m = 2^20), and the residual
+  is the noise that the rank-64 space does not capture, just under the noise's
+  own norm eta sqrt(m n) (0.993 of it measured).
+"""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _fro_residual(A, U, D, V, rows=4096):
+    """||A - U diag(D) V^T||_F and ||A||_F, blockwise in float64 on the device."""
+    f2, a2 = 0.0, 0.0
+    Ud = U.double() * D[None, :]
+    Vd = V.double()
+    for r0 in range(0, A.shape[0], rows):
+        Ab = A[r0:r0 + rows].double()
+        R = Ab - Ud[r0:r0 + rows] @ Vd.T
+        f2 += float((R * R).sum())
+        a2 += float((Ab * Ab).sum())
+        del Ab, R
+    return f2 ** 0.5, a2 ** 0.5
+
+
+def _orth_err(X):
+    """max |X^T X - I| in float64."""
+    import torch
+    Xd = X.double()
+    G = Xd.T @ Xd
+    return float((G - torch.eye(G.shape[0], dtype=G.dtype, device=G.device)).abs().max())
+
+
+def test_poly_decay_32768_bf16_full_size(lib):
+    import torch
+    from workloads import poly_decay_matrix
+    m = n = 32768
+    k, p, q = 200, 56, 2
+    A = poly_decay_matrix(m, n, seed=2001, device="cuda")
+    U, D, V = lib.fixed_rank(A, k, p, q, seed=2101, prec=lib.RSVD_MIXED_BF16)
+    torch.cuda.synchronize()
+    sig = torch.arange(1, min(m, n) + 1, dtype=torch.float64, device="cuda").pow(-1.5)
+    d = D.double()
+    assert bool((d[:-1] >= d[1:]).all())
+    assert bool((d <= sig[:k] * (1 + 1e-4)).all()), float((d / sig[:k]).max())
+    assert bool((d >= sig[:k] * (1 - 0.03)).all()), float((1 - d / sig[:k]).max())
+    assert _orth_err(U) < 1e-4 and _orth_err(V) < 1e-4
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        idx = torch.tensor([0, 1, 49, 99, 150, 199], device="cuda")
+        Vs = V[:, idx]
+        R = A @ Vs - U @ (D.float()[:, None] * (V.T @ Vs))     # (A - U D V^T) v_i
+        r = R.double().norm(dim=0) / Vs.double().norm(dim=0)
+        assert float(r.max()) <= 2 * float(sig[k]), float(r.max() / sig[k])
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    res, fro_a = _fro_residual(A, U, D, V)
+    opt = float(sig[k:].pow(2).sum().sqrt())
+    # ||A||_F of the binary32 matrix agrees with the construction's to rounding
+    assert abs(fro_a - float(sig.pow(2).sum().sqrt())) < 1e-4 * fro_a
+    assert opt * (1 - 1e-4) <= res <= 1.01 * opt, (res, opt)
+    del A, U, D, V, R
+    torch.cuda.empty_cache()
+
+
+def test_pca_2p20x4096_e4m3_full_size(lib):
+    import torch
+    from workloads import pca_matrix
+    m, n = 1 << 20, 4096
+    k, p, q = 64, 64, 1
+    eta = 1e-3
+    A = pca_matrix(m, n, seed=3001, device="cuda")
+    U, D, V = lib.fixed_rank(A, k, p, q, seed=3101, prec=lib.RSVD_MIXED_FP8)
+    torch.cuda.synchronize()
+    d = D.double()
+    s = torch.linspace(100.0, 1.0, 64, dtype=torch.float64, device="cuda")
+    # the 48 strongest signal directions stand well clear of the noise edge
+    # eta (sqrt m + sqrt n) = 1.09
+    shift = eta * eta * (m + n) / (2 * s[:48])
+    rel = ((d[:48] - s[:48]).abs() / s[:48])
+    assert float(rel.max()) < 2e-3, float(rel.max())
+    assert float((rel - shift / s[:48]).abs().max()) < 5e-4
+    assert _orth_err(U) < 1e-4 and _orth_err(V) < 1e-4
+    res, _ = _fro_residual(A, U, D, V, rows=65536)
+    floor = eta * (m * n) ** 0.5
+    # a k-dimensional space captures at most k eta^2 (sqrt m + sqrt n)^2 of
+    # the noise's energy (Ky Fan; the noise's singular values end at
+    # eta (sqrt m + sqrt n)): 0.991 of the floor remains at this size
+    lo = (1.0 - k * (m ** 0.5 + n ** 0.5) ** 2 / (m * n)) ** 0.5 - 0.02
+    assert lo * floor <= res <= 1.01 * floor, (res / floor, lo)
+    del A, U, D, V
+    torch.cuda.empty_cache()

@@ -1,12 +1,14 @@
-"""The two dense workloads at full size, through rsvd_fixed_rank (the call the
-benchmark times, with the same sizes, precisions and launch configuration),
-checked by properties that hold at any size because the float64 oracle cannot
-run there:
+"""The dense workloads at full size, through the calls the benchmark times
+(rsvd_fixed_rank, rsvd_nystrom; the same sizes, precisions and launch
+configuration), checked by properties that hold at any size because the
+float64 oracle cannot run there:
 
 * 32768 x 32768 polynomial decay (sigma_j = j^-1.5, Haar U and V), bf16
   tensor-core sketches, k = 200, p = 56, q = 2;
 * 2^20 x 4096 PCA matrix (rank-64 signal 100 -> 1 plus N(0, 1e-6) noise,
-  column-centred), e4m3 sketches, k = 64, p = 64, q = 1.
+  column-centred), e4m3 sketches, k = 64, p = 64, q = 1;
+* 16384 x 16384 SPD matrix V diag(j^-1.5) V^T, Nystrom, binary32 (its own
+  test states its properties).
 
 What is checked, and why it must hold:
 * d_i <= sigma_i (1 + 1e-4): the computed values are the singular values of
@@ -112,4 +114,43 @@ def test_pca_2p20x4096_e4m3_full_size(lib):
     lo = (1.0 - k * (m ** 0.5 + n ** 0.5) ** 2 / (m * n)) ** 0.5 - 0.02
     assert lo * floor <= res <= 1.01 * floor, (res / floor, lo)
     del A, U, D, V
+    torch.cuda.empty_cache()
+
+
+def test_nystrom_16384_f32_full_size(lib):
+    """Fig. nystrom on the 16384^2 SPD workload (A = V diag(j^-1.5) V^T, Haar
+    V), binary32, k = 200, p = 56, the benchmark's call.  The Nystrom
+    approximation F F* lies below A in the Loewner order, so (i) each
+    lambda_hat_i <= lambda_i and (ii) each Rayleigh quotient u_i^T A u_i >=
+    lambda_hat_i, both up to binary32 rounding (1e-6 and 2e-5 of lambda_1
+    allowed; the same steps in binary32 on the CPU at 4096^2 give -4e-9 for
+    the second); without a power step the 200th value is 16% low (0.83 of
+    lambda_200 from the float64 oracle at 4096^2), so 0.7 lambda_i is the
+    lower bound; the residual on sampled u_i is at most the spectral residual
+    (1.27 lambda_{k+1} from the oracle, 1.29 measured here)."""
+    import torch
+    from workloads import spd_matrix
+    n, k, p = 16384, 200, 56
+    A = spd_matrix(n, seed=5001, device="cuda")
+    U, L = lib.nystrom(A, k, p, seed=5101, prec=lib.RSVD_F32)
+    torch.cuda.synchronize()
+    lam = torch.arange(1, n + 1, dtype=torch.float64, device="cuda").pow(-1.5)
+    assert bool((L[:-1] >= L[1:]).all()) and bool((L > 0).all())
+    assert bool((L <= lam[:k] * (1 + 1e-3) + 1e-6).all()), float((L / lam[:k]).max())
+    assert bool((L >= 0.7 * lam[:k]).all()), float((L / lam[:k]).min())
+    assert _orth_err(U) < 1e-4
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        AU = (A @ U).double()
+        rho = (U.double() * AU).sum(dim=0)
+        assert float((rho - L).min()) >= -2e-5, float((rho - L).min())
+        idx = torch.tensor([0, 1, 49, 99, 150, 199], device="cuda")
+        Ud = U.double()
+        R = AU[:, idx] - Ud @ (L[:, None] * (Ud.T @ Ud[:, idx]))    # (A - U Lam U^T) u_i
+        r = R.norm(dim=0) / Ud[:, idx].norm(dim=0)
+        assert float(r.max()) <= 2 * float(lam[k]), float(r.max() / lam[k])
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    del A, U, L, AU, R
     torch.cuda.empty_cache()

@@ -18,10 +18,17 @@ graph; one step = the whole batch, `value` = blocks solved per second.
 ``--workload controller``: a stream of square matrices solved to tolerance
 1e-4 with the learned (l, q) controller (trained first, on the GPU).
 
+``--workload nystrom``: the Nystrom EVD (Fig. nystrom) of a 16384^2 SPD
+matrix V diag(j^-1.5) V^T in binary32, beside the fixed-rank RSVD with the
+same passes over A.
+
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own
 matrix (replicas; there is no exchange step), and `value` is the total over
 ranks.  ``--impl reference`` times the float64 CPU oracle instead, on a
-bounded sample of the same workload.
+bounded sample of the same workload: rsvd_power on a smaller matrix of the
+same family (poly, pca), nystrom on a smaller SPD matrix, adaptive_blocked on
+the first blocks of the batch, and adaptive_blocked on size-capped stand-ins
+of the controller stream's matrices, each scaled to the full size by m n.
 """
 import argparse
 import json
@@ -666,16 +673,130 @@ def run_controller(a):
     line = {"metric": METRIC, "value": out["controller"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["controller"][0] / max(res["controller"][1], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "controller stream: %d held-out square fp32 matrices, n log-uniform in [%d, %d], "
-                                   "spectra exp / poly / step, tol 1e-4 relative Frobenius" % (a.steps, a.lo, a.hi),
+            "config": {"workload": controller_name(a, a.steps),
                        "training": "%d matrices, labels from the adaptive finder (q = 0..3), 3000 Adam steps, "
                                    "final loss %.3f, %.0f s" % (a.train, loss, t_train)},
             "controller": out["controller"], "controller_escalating": out["escalate"],
-            "adaptive_only": out["adaptive"], "fixed_l256_q2": out["fixed"], "fallbacks": falls}
+            "adaptive_only": out["adaptive"], "fixed_l256_q2": out["fixed"], "fallbacks": falls,
+            "cpu_baseline": None if a.no_cpu else controller_cpu_baseline(a, 20.0)}
+    print(json.dumps(line))
+
+
+CONTROLLER_TOL = 1e-4
+CONTROLLER_CAP = 1024
+
+
+def controller_oracle_solve(a, i):
+    """Matrix i of the held-out stream (seed a.seed + i: its size n and its
+    spectrum) solved to the stream's tolerance by the float64 oracle's blocked
+    adaptive range finder -- the method without the learned part -- on an
+    n' x n' stand-in, n' = min(n, 1024), with the spectrum's first n' values
+    and Haar factors.  Returns (time scaled to n x n by (n / n')^2, n)."""
+    import oracle
+    from workloads import controller_case, lowrank_np
+    s = a.seed + i
+    n, sig, _, _ = controller_case(s, a.lo, a.hi)
+    ns = min(n, CONTROLLER_CAP)
+    A = lowrank_np(ns, ns, sig[:ns], s)
+    t0 = time.perf_counter()
+    oracle.adaptive_blocked(A, CONTROLLER_TOL, b=16, seed=s, max_rank=min(ns, 256))
+    return (time.perf_counter() - t0) * (n / float(ns)) ** 2, n
+
+
+def controller_sample_text(count, mean_n):
+    return ("float64 oracle adaptive_blocked (b=16, tol %.0e, max rank 256) on the first %d timed matrices of the "
+            "held-out stream (mean n %.0f), each on a stand-in with n capped at %d (same spectrum, Haar factors), "
+            "time scaled by (n / n')^2" % (CONTROLLER_TOL, count, mean_n, CONTROLLER_CAP))
+
+
+def controller_name(a, steps):
+    return ("controller stream: %d held-out square fp32 matrices, n log-uniform in [%d, %d], spectra exp / poly / "
+            "step, tol 1e-4 relative Frobenius" % (steps, a.lo, a.hi))
+
+
+def controller_cpu_baseline(a, seconds):
+    """The oracle timed on the stream's timed matrices (a.warmup, a.warmup +
+    1, ...), one after another, for about `seconds`; returns the cpu_baseline
+    dict."""
+    t0 = time.perf_counter()
+    scaled, ns = 0.0, []
+    while time.perf_counter() - t0 < seconds and len(ns) < a.steps:
+        t, n = controller_oracle_solve(a, a.warmup + len(ns))
+        scaled += t
+        ns.append(n)
+    return {"value": len(ns) / scaled, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": controller_sample_text(len(ns), sum(ns) / float(len(ns)))}
+
+
+def run_reference_controller(a):
+    """The oracle arm for the controller stream: the same matrices as the
+    GPU arm, warm-up steps on the first a.warmup, step i on a.warmup + i."""
+    world, rank, local = dist_setup(a)
+    if rank != 0:
+        return
+    for w in range(a.warmup):
+        controller_oracle_solve(a, w)
+    scaled, ns = 0.0, []
+    for i in range(a.steps):
+        t, n = controller_oracle_solve(a, a.warmup + i)
+        scaled += t
+        ns.append(n)
+    value = a.steps / scaled
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * scaled / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": controller_name(a, a.steps)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": controller_sample_text(a.steps, sum(ns) / float(a.steps))},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ----------------------------------------------------------- nystrom -------
+def nystrom_oracle_solve(a, As, seed):
+    """One float64 oracle Nystrom solve on the ns x ns sample As; returns its
+    time scaled to the n x n workload by the n^2 ratio."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.nystrom(As, a.k, a.p, seed)
+    return (time.perf_counter() - t0) * (a.n / float(As.shape[0])) ** 2
+
+
+def nystrom_sample_text(a, ns, reps, scaled_s):
+    return ("float64 oracle nystrom on a %dx%d SPD matrix of the same family (k=%d p=%d), %d solve(s), %.3f s "
+            "each, scaled by the n^2 ratio %.1f" % (ns, ns, a.k, a.p, reps,
+                                                    scaled_s / (a.n / float(ns)) ** 2, (a.n / float(ns)) ** 2))
+
+
+def run_reference_nystrom(a):
+    """The oracle arm for the Nystrom workload: each step is one float64
+    oracle solve on an a.sample x a.sample matrix of the same SPD family,
+    timed on the host cores and scaled by the n^2 ratio."""
+    world, rank, local = dist_setup(a)
+    if rank != 0:
+        return
+    from workloads import spd_matrix_np
+    ns = min(a.sample, a.n)
+    As = spd_matrix_np(ns, seed=a.seed)
+    for i in range(a.warmup):
+        nystrom_oracle_solve(a, As, a.seed + i)
+    scaled = sum(nystrom_oracle_solve(a, As, a.seed + 100 + i) for i in range(a.steps))
+    value = a.steps / scaled
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * scaled / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": nystrom_name(a)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": nystrom_sample_text(a, ns, a.steps, scaled / a.steps)},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def nystrom_name(a):
+    return ("Nystrom EVD (Fig. nystrom), SPD %dx%d fp32 = V diag(j^-1.5) V^T, Haar V; k=%d p=%d (l=%d)"
+            % (a.n, a.n, a.k, a.p, a.k + a.p))
+
+
 def run_nystrom(a):
     """rsvd_nystrom (Fig. nystrom) on a 16384^2 SPD matrix V diag(j^-1.5) V^T,
     binary32; beside it the fixed-rank RSVD with the same two passes over A
@@ -685,7 +806,6 @@ def run_nystrom(a):
     import torch
     import paper_1607_01649_gb300 as rs
     from workloads import spd_matrix, spd_matrix_np
-    import oracle
     dev = torch.device("cuda", 0)
     n, k, p = a.n, a.k, a.p
     l = k + p
@@ -772,20 +892,16 @@ def run_nystrom(a):
         ns = min(a.sample, n)
         As = spd_matrix_np(ns, seed=a.seed)
         t0 = time.perf_counter()
-        reps = 0
+        scaled, reps = 0.0, 0
         while time.perf_counter() - t0 < 10.0 and reps < 20:
-            oracle.nystrom(As, k, p, a.seed)
+            scaled += nystrom_oracle_solve(a, As, a.seed)
             reps += 1
-        t = (time.perf_counter() - t0) / reps
-        scale = (n / ns) ** 2
-        cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": "float64 oracle nystrom on a %dx%d SPD matrix of the same family (k=%d p=%d), %d solve(s), "
-                         "%.3f s each, scaled by the n^2 ratio %.1f" % (ns, ns, k, p, reps, t, scale)}
+        cpu = {"value": reps / scaled, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": nystrom_sample_text(a, ns, reps, scaled / reps)}
     line = {"metric": METRIC, "value": a.steps / (ms / 1000.0), "unit": "solves/s", "n_gpus": 1, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "Nystrom EVD (Fig. nystrom), SPD %dx%d fp32 = V diag(j^-1.5) V^T, Haar V; "
-                                   "k=%d p=%d (l=%d)" % (n, n, k, p, l),
+            "config": {"workload": nystrom_name(a),
                        "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB)" % (n * n * 4 / 1e9)},
             "roofline": roof, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk,
             "error": {"spectral_residual_rel": ny, "spectral_estimate_last_rel_change": ny_conv,
@@ -1036,9 +1152,9 @@ def main():
     if a.workload == "batched":
         (run_reference_batched if a.impl == "reference" else run_batched)(a)
     elif a.workload == "nystrom":
-        run_nystrom(a)
+        (run_reference_nystrom if a.impl == "reference" else run_nystrom)(a)
     elif a.workload == "controller":
-        run_controller(a)
+        (run_reference_controller if a.impl == "reference" else run_controller)(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

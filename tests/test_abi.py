@@ -71,3 +71,15 @@ def test_batched_variant_table_without_a_device(built_lib):
     a, b = ctypes.c_int(), ctypes.c_int()
     assert built_lib.rsvd_batched_variant_info(n.value, ctypes.byref(a), ctypes.byref(b)) != 0
     assert built_lib.rsvd_batched_variant_info(-1, ctypes.byref(a), ctypes.byref(b)) != 0
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No fallback: with librsvd.so absent the binding raises instead of
+    computing anything another way."""
+    import paper_1607_01649_gb300 as rs
+    monkeypatch.setattr(rs, "_lib", None)
+    monkeypatch.setattr(rs, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "librsvd.so"))
+    with pytest.raises(ImportError, match="librsvd.so not found"):
+        rs.load()
+    with pytest.raises(ImportError):
+        rs.handle(0)

@@ -56,10 +56,23 @@ def _sign_by_largest(X):
     return s
 
 
+# The fits below write the least-squares system out in full: k(k+1)/2 or k^2
+# unknowns over k l or 2 k l equations.  That is the definition, meant for the
+# small cases an oracle serves; past this many matrix entries they refuse.
+MAX_SYSTEM_ENTRIES = 1 << 27
+
+
+def _check_system(rows, cols):
+    if rows * cols > MAX_SYSTEM_ENTRIES:
+        raise ValueError("least-squares system of %d x %d entries is beyond the oracle's "
+                         "small-case limit" % (rows, cols))
+
+
 def symmetric_lsq(M, N):
     """argmin over symmetric C (k x k) of ||C M - N||_F, M and N k x l."""
     k = M.shape[0]
     pairs = [(i, j) for i in range(k) for j in range(i, k)]
+    _check_system(N.size, len(pairs))
     K = np.zeros((N.size, len(pairs)))
     for t, (i, j) in enumerate(pairs):
         E = np.zeros((k, k))
@@ -77,6 +90,7 @@ def symmetric_lsq(M, N):
 def joint_lsq(P, R1, M, R2):
     """argmin over C (k x k) of ||P C - R1||_F^2 + ||C M - R2||_F^2."""
     k = P.shape[1]
+    _check_system(P.shape[0] * k + M.shape[1] * k, k * k)
     # column-major vec: vec(P C) = (I kron P) vec(C), vec(C M) = (M^T kron I) vec(C)
     K = np.vstack([np.kron(np.eye(k), P), np.kron(M.T, np.eye(k))])
     rhs = np.concatenate([R1.ravel(order="F"), R2.ravel(order="F")])

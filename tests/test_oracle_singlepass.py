@@ -121,3 +121,12 @@ def test_one_pass_loses_accuracy_against_two(kind):
     assert np.mean(one) > 1.2 * np.mean(two)
     assert np.all(two >= sig[k] * (1 - 1e-12))
     assert np.all(one < 10.0 * sig[k])
+
+
+def test_fits_refuse_systems_beyond_small_cases():
+    from oracle.singlepass import joint_lsq, symmetric_lsq
+    k, l = 200, 400
+    with pytest.raises(ValueError):
+        joint_lsq(np.zeros((l, k)), np.zeros((l, k)), np.zeros((k, l)), np.zeros((k, l)))
+    with pytest.raises(ValueError):
+        symmetric_lsq(np.zeros((k, 3 * l)), np.zeros((k, 3 * l)))

@@ -42,6 +42,11 @@ Parity status per function:
 * rsvd_block_krylov (Sec. "Extended sampling matrix"): pinned (q = 1 is
   Fig. RSVD, exact recovery of rank q l, span of a blockwise orthonormalized
   Krylov basis, residual below the power scheme's by nesting).  No GPU path yet.
+* adaptive_blocked_spectral (the blocked scheme with Fig. adaptive2's
+  spectral stopping test, the GPU form planned for that row): pinned (the
+  blocked scheme's basis bit for bit, spectral error below eps on every seed,
+  rank between the spectral eps-rank and the Frobenius rank at a quarter of
+  the threshold plus two blocks).  No GPU path yet.
 * rsvd_power_centred (implicit column centring for PCA): pinned (equals the
   fixed-rank oracle on the explicitly centred matrix; 1* U = 0).  No GPU path yet.
 """
@@ -50,8 +55,8 @@ from .philox import (philox4x32_10, gaussian, omega_words, box_muller, seed_key,
                      STREAM_ROW, STREAM_SRFT_D, STREAM_SRFT_S)
 from .rsvd import orth, sign_normalize, stage_b, rsvd_basic, rsvd_power, rsvd_power_plain
 from .norms import fro_residual, spectral_residual, certificate, theorem_bounds
-from .adaptive import (adaptive_blocked, truncate_to_tol, single_vector_range_finder,
-                       adaptive_range_finder)
+from .adaptive import (adaptive_blocked, adaptive_blocked_spectral, truncate_to_tol,
+                       single_vector_range_finder, adaptive_range_finder)
 from . import controller
 from . import fp8
 from .nystrom import nystrom

@@ -11,6 +11,9 @@ TEST INFRASTRUCTURE ONLY (oracle); nothing in the product path may import it.
 * ``single_vector_range_finder``  Sec. 13, Fig. "singlevecrangefinder".
 * ``adaptive_range_finder``  Sec. 13, Fig. "adaptive2" with the threshold
   eps / (10 sqrt(2/pi)) and an r-vector window.
+* ``adaptive_blocked_spectral``  the blocked scheme with Fig. adaptive2's
+  spectral-norm stopping test applied to each fresh block (its b samples are
+  the test's r = b probes).
 
 Readings taken where the paper is silent:
 * the relative tolerance: eps = tol * ||A||_Fro;
@@ -73,6 +76,49 @@ def adaptive_blocked(A, tol, b=16, seed=0, q=0, max_rank=None):
     return dict(Q=Q, B=B, U=U, D=D, V=V, rank=Q.shape[1], converged=converged,
                 norms_direct=np.array(norms_direct), norms_downdate=np.array(norms_downdate),
                 eps=eps, steps=t)
+
+
+def adaptive_blocked_spectral(A, eps, b=16, seed=0, max_rank=None):
+    """The blocked scheme of Fig. greedy_blocked (q = 0) stopped by the
+    spectral-norm test of Fig. adaptive2 and Lemma thm:aposteriori instead of
+    the Frobenius norm: at the start of step t the fresh block G_t (drawn
+    independently of the current Q) gives Y = A_j G_t = (I - Q Q*) A G_t; if
+    every column of Y has norm at most eps / (10 sqrt(2/pi)), then
+    ||A - Q B||_2 <= eps except with probability 10^-b, and the step stops
+    without appending; otherwise the step goes on exactly as in
+    adaptive_blocked with the same block.  eps is absolute."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    rmax = min(m, n) if max_rank is None else min(max_rank, m, n)
+    thresh = eps / (10.0 * np.sqrt(2.0 / np.pi))
+    Aj = A.copy()
+    Q = np.zeros((m, 0))
+    B = np.zeros((0, n))
+    probes = []
+    t = 0
+    converged = False
+    while Q.shape[1] < rmax:
+        bb = min(b, rmax - Q.shape[1])
+        G = gaussian(n, bb, seed, STREAM_ADAPTIVE, col0=t * b)
+        Y = Aj @ G
+        probes.append(float(np.max(np.linalg.norm(Y, axis=0))))
+        if probes[-1] <= thresh:
+            converged = True
+            break
+        Y = Y - Q @ (Q.T @ Y)
+        Qn, _ = orth(Y)
+        Bn = Qn.T @ Aj
+        Aj = Aj - Qn @ Bn
+        B2 = Qn.T @ Aj
+        Aj = Aj - Qn @ B2
+        Bn = Bn + B2
+        Q = np.hstack([Q, Qn])
+        B = np.vstack([B, Bn])
+        t += 1
+    Uhat, D, Vt = np.linalg.svd(B, full_matrices=False)
+    U, V = sign_normalize(Q @ Uhat, Vt.T)
+    return dict(Q=Q, B=B, U=U, D=D, V=V, rank=Q.shape[1], converged=converged,
+                probes=np.array(probes), thresh=thresh, steps=t)
 
 
 def truncate_to_tol(D, resid_fro, tol_abs):

@@ -101,3 +101,35 @@ def test_certificate_bounds_the_error():
         bound, cn = oracle.certificate(A, r["U"], r["D"], r["V"], seed=1000 + s)
         assert bound >= true
         assert len(cn) == 10
+
+
+def test_blocked_with_spectral_stop():
+    """adaptive_blocked_spectral: the blocked scheme with Fig. adaptive2's test
+    on each fresh block.  Its basis is the blocked scheme's own (same blocks,
+    same steps, bit for bit); where it stops, the spectral error is below eps
+    on every seed (Lemma thm:aposteriori, failure probability 10^-16 per
+    test), so its rank is at least the spectral eps-rank; and it stops within
+    two blocks of the rank where the Frobenius tail falls below a quarter of
+    the threshold (a Gaussian probe of a remainder that small stays under the
+    threshold)."""
+    import numpy as np
+    from oracle.adaptive import adaptive_blocked_spectral, adaptive_blocked
+    from workloads import lowrank_np, exp_spectrum
+    sig = exp_spectrum(200)
+    A = lowrank_np(300, 200, sig, seed=1)
+    tail = np.sqrt(np.concatenate([np.cumsum((sig ** 2)[::-1])[::-1], [0.0]]))    # tail[r] = ||A - A_r||_F
+    for eps in (1e-2, 1e-3, 1e-4):
+        th = eps / (10.0 * np.sqrt(2.0 / np.pi))
+        lo, hi = int(np.sum(sig > eps)), int(np.argmax(tail <= th / 4)) + 32
+        for seed in range(8):
+            r = adaptive_blocked_spectral(A, eps, b=16, seed=seed)
+            assert r["converged"] and r["probes"][-1] <= th < r["probes"][:-1].min()
+            assert np.linalg.norm(A - r["Q"] @ r["B"], 2) <= eps
+            assert lo <= r["rank"] <= hi, (eps, seed, r["rank"], lo, hi)
+            if seed < 2:
+                ref = adaptive_blocked(A, 1e-300, b=16, seed=seed, max_rank=r["rank"])
+                assert np.array_equal(ref["Q"], r["Q"]) and np.array_equal(ref["B"], r["B"])
+    z = adaptive_blocked_spectral(np.zeros((40, 30)), 1e-6, seed=0)
+    assert z["rank"] == 0 and z["converged"]
+    capped = adaptive_blocked_spectral(A, 1e-12, b=16, seed=0, max_rank=48)
+    assert capped["rank"] == 48 and not capped["converged"]

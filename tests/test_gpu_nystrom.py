@@ -56,8 +56,8 @@ def test_nystrom_rank_deficient_input_is_reported(lib):
     """rank(A) = 12 < l = 24: Q^T A Q is singular to working precision.  Its
     unit-diagonal scaling turns the null block into rounding noise of order
     one, which no small shift makes positive definite, so the call reports
-    RSVD_E_BREAKDOWN instead of returning a wrong factor (the shifted Nystrom
-    variant, A + nu I with nu subtracted from Lambda, is not built)."""
+    RSVD_E_BREAKDOWN instead of returning a wrong factor (a shifted variant,
+    A + nu I with nu subtracted from Lambda, is not part of Fig. nystrom)."""
     import torch
     h = lib.handle()
     n, k, p, seed = 300, 16, 8, 4

@@ -421,10 +421,17 @@ rsvd_status rsvd_certify(rsvd_handle_t handle, int m, int n, const float* A, int
  * scratch limit").  No cudaMalloc, cudaFree or other allocating call is made.
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before capturing a stream.
- * Every call reuses the same array: calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialized. */
+ * The current device must be the handle's device (RSVD_E_INVALID otherwise).
+ * status_out (optional, may be NULL): an int in device memory or mapped host
+ * memory owned by the caller; it receives the device status word of this
+ * call (RSVD_OK, or RSVD_E_TIMEOUT if a bounded wait in the kernel gave up
+ * and Y is incomplete), copied in stream order after the product.
+ * Every call reuses the same array, status word included: calls that overlap
+ * on the GPU (other streams, other host threads) race on it and must be
+ * serialized. */
 rsvd_status rsvd_sketch_noalloc(rsvd_handle_t handle, int trans, int m, int n, int l, const void* A, int lda,
-                                const void* X, int ldx, float* Y, int ldy, rsvd_stream_t stream);
+                                const void* X, int ldx, float* Y, int ldy, int* status_out,
+                                rsvd_stream_t stream);
 
 /* Orthonormalization (Sec. 2.3, "orth", unpivoted): Q = Y R^-1 with R upper
  * triangular, diag(R) > 0, by CholeskyQR2 (a shifted first pass is added when

@@ -17,15 +17,17 @@ TEST INFRASTRUCTURE ONLY (oracle); nothing in the product path may import it.
 
 Readings taken where the paper is silent:
 * the relative tolerance: eps = tol * ||A||_Fro;
-* before qr(A_j G) the sample is projected once against the current Q
-  ((I - Q Q*) A_j G).  In exact arithmetic A_j already has range orthogonal to
-  Q, so this changes nothing but round-off (the caption of Fig. adaptive2 makes
-  the same point about its own redundant projection);
-* the deflation A_j <- A_j - Q_new B_new is applied twice (B2 = Q_new* A_j,
-  A_j <- A_j - Q_new B2, B_new <- B_new + B2).  In exact arithmetic the second
-  pass is zero; in floating point it removes what a not-quite-orthonormal
-  Q_new leaves of A_j inside span(Q_new), which the projection of later
-  samples would otherwise hide from every later step;
+* the step follows Fig. greedy_blocked with one deflation, A_j <- A_j -
+  Q_new B_new, and one addition: before qr(A_j G) the sample is projected
+  against the current Q, (I - Q Q*) A_j G, as Fig. adaptive2 does with its
+  own samples.  In exact arithmetic A_j G already lies in the orthogonal
+  complement of Q, so this changes only round-off; without it the float64
+  basis loses orthogonality (1e-10 at tol = 1e-6: near the end A_j is small
+  and its sample carries rounding components along Q of relative size
+  u ||A|| / ||A_j||).  (A binary32 implementation also deflates twice: there
+  a CholeskyQR2 block is orthonormal only to about 1e-6, and a single
+  deflation leaves that much of A_j inside span(Q_new), hidden from every
+  later sample by the projection.);
 * Gaussian blocks come from STREAM_ADAPTIVE, block t holding columns
   t b .. t b + b - 1 of that stream;
 * the loop stops with converged=False at max_rank or min(m, n).
@@ -61,9 +63,6 @@ def adaptive_blocked(A, tol, b=16, seed=0, q=0, max_rank=None):
         Qn, _ = orth(Y)
         Bn = Qn.T @ Aj
         Aj = Aj - Qn @ Bn
-        B2 = Qn.T @ Aj
-        Aj = Aj - Qn @ B2
-        Bn = Bn + B2
         Q = np.hstack([Q, Qn])
         B = np.vstack([B, Bn])
         nd = float(np.sqrt(np.sum(Aj * Aj)))
@@ -109,9 +108,6 @@ def adaptive_blocked_spectral(A, eps, b=16, seed=0, max_rank=None):
         Qn, _ = orth(Y)
         Bn = Qn.T @ Aj
         Aj = Aj - Qn @ Bn
-        B2 = Qn.T @ Aj
-        Aj = Aj - Qn @ B2
-        Bn = Bn + B2
         Q = np.hstack([Q, Qn])
         B = np.vstack([B, Bn])
         t += 1

@@ -109,7 +109,7 @@ def load():
         "rsvd_kernel_launches": [vp, ctypes.POINTER(ctypes.c_longlong)],
         "rsvd_profile": [vp, i],
         "rsvd_profile_read": [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
-        "rsvd_sketch_noalloc": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp],
+        "rsvd_sketch_noalloc": [vp, i, i, i, i, vp, i, vp, i, vp, i, vp, vp],
         "rsvd_batched_workspace_size": [vp, i, P, ctypes.POINTER(sz)],
         "rsvd_batched": [vp, i, vp, vp, vp, vp, P, vp, vp, vp, vp, vp, vp, vp, sz, vp],
         "rsvd_batched_variants": [ctypes.POINTER(i)],
@@ -339,9 +339,12 @@ def rsvd_project(h, prec, m, n, l, A, lda, Q, ldq, Bt, ldb, ws, stream=None):
                                ws.numel() if ws is not None else 0, _stream(stream))
 
 
-def rsvd_sketch_noalloc(h, trans, m, n, l, A, lda, X, ldx, Y, ldy, stream=None):
-    """bf16 tensor-core sketch product with library-owned scratch (no workspace argument)."""
-    return load().rsvd_sketch_noalloc(h, trans, m, n, l, _ptr(A), lda, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream))
+def rsvd_sketch_noalloc(h, trans, m, n, l, A, lda, X, ldx, Y, ldy, status=None, stream=None):
+    """bf16 tensor-core sketch product with library-owned scratch (no workspace
+    argument); `status` (optional) is a one-element int32 device tensor that
+    receives the call's device status word."""
+    return load().rsvd_sketch_noalloc(h, trans, m, n, l, _ptr(A), lda, _ptr(X), ldx, _ptr(Y), ldy,
+                                      _ptr(status) if status is not None else None, _stream(stream))
 
 
 def rsvd_probe_workspace_size(h, m, n):

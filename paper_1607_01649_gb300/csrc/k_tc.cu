@@ -45,6 +45,7 @@ struct TcArgs {
   int NA;        // TMEM columns per accumulator (power of 2 >= 32)
   int nchunk;    // 64-column TMA boxes per B tile
   int nbuf;      // TMEM accumulator sets (2: one tile's epilogue overlaps the next tile's MMAs)
+  int seg;       // k-blocks per TMEM accumulation segment (see seg_end)
   float* Y;
   int ldy;
   float* part;   // [G][2][BM][Npad]
@@ -55,6 +56,18 @@ struct TcArgs {
 };
 
 __host__ __device__ inline long long su0(long long c, long long W, int G) { return (c * W) / G; }
+
+// The tensor core adds each MMA's products into its fp32 accumulator with
+// truncation, not round-to-nearest, so a sum over many k-blocks kept in TMEM
+// drifts toward zero by about half an ulp per MMA (measured: 7.9e-4 relative
+// on the 2^20-row projection B^T = A^T Q, about 41k accumulating MMAs per
+// CTA).  The k-blocks of a tile are therefore cut into segments that end at
+// multiples of g.seg; each segment starts a fresh accumulator, and the
+// epilogue adds the segments together in fp32 with round-to-nearest.
+__device__ __forceinline__ int seg_end(int kb, int kb_hi, int seg) {
+  const int e = (kb / seg + 1) * seg;
+  return e < kb_hi ? e : kb_hi;
+}
 
 constexpr int TC_THREADS = 192;
 constexpr int TC_MAX_CTAS = 256;  // persistent grid cap (>= #SMs of the part)
@@ -165,53 +178,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t idesc = F8 ? idesc_e4m3(128, g.Npad) : idesc_bf16(128, g.Npad, TRANS ? 1 : 0, 1);
     int it = 0, j = 0;
     bool ok = true;
-    for (int t = t_first; t <= t_last && ok; ++t, ++j) {
+    for (int t = t_first; t <= t_last && ok; ++t) {
       const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
       const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
-      const int acc = j % g.nbuf;
-      const uint32_t aph = (uint32_t)(j / g.nbuf) & 1u;
-      if (!mbar_wait(&tempty[acc], aph ^ 1u)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t dtm = tbase + (uint32_t)(acc * SUB * g.NA);
-      for (int kb = kb_lo; kb < kb_hi; ++kb, ++it) {
-        const int s = it % stages;
-        const uint32_t ph = (uint32_t)(it / stages) & 1u;
-        if (!mbar_wait(&full[s], ph)) {
+      for (int sg = kb_lo; sg < kb_hi && ok; ++j) {
+        const int se = seg_end(sg, kb_hi, g.seg);
+        const int acc = j % g.nbuf;
+        const uint32_t aph = (uint32_t)(j / g.nbuf) & 1u;
+        if (!mbar_wait(&tempty[acc], aph ^ 1u)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t aA = smem_u32(sm + (size_t)s * stage_bytes);
-        const uint32_t aB = aA + NT * SUB * A_TILE;
+        const uint32_t dtm = tbase + (uint32_t)(acc * SUB * g.NA);
+        for (int kb = sg; kb < se; ++kb, ++it) {
+          const int s = it % stages;
+          const uint32_t ph = (uint32_t)(it / stages) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aA = smem_u32(sm + (size_t)s * stage_bytes);
+          const uint32_t aB = aA + NT * SUB * A_TILE;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          // bf16: 16 K-elements (32 bytes) per MMA; e4m3: 32 K-elements (32 bytes)
-          const uint64_t bd = F8 ? umma_desc(aB + 32 * k, 16, 1024) : umma_desc(aB + 2048 * k, 8192, 1024);
-          const uint32_t accum = (kb > kb_lo || k > 0) ? 1u : 0u;
+          for (int k = 0; k < 4; ++k) {
+            // bf16: 16 K-elements (32 bytes) per MMA; e4m3: 32 K-elements (32 bytes)
+            const uint64_t bd = F8 ? umma_desc(aB + 32 * k, 16, 1024) : umma_desc(aB + 2048 * k, 8192, 1024);
+            const uint32_t accum = (kb > sg || k > 0) ? 1u : 0u;
 #pragma unroll
-          for (int sb = 0; sb < SUB; ++sb) {
-            const uint32_t aAs = aA + sb * A_TILE;
-            const uint64_t ad = TRANS ? umma_desc(aAs + 2048 * k, 8192, 1024) : umma_desc(aAs + 32 * k, 16, 1024);
-            if (F8)
-              mma_e4m3(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
-            else
-              mma_bf16(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
-            if (SPLIT3) {
-              const uint64_t ad2 = TRANS ? umma_desc(aAs + A_TILE + 2048 * k, 8192, 1024)
-                                         : umma_desc(aAs + A_TILE + 32 * k, 16, 1024);
-              const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
-              mma_bf16(dtm, ad, bd2, idesc, 1u);   // Ah^T Xl
-              mma_bf16(dtm, ad2, bd, idesc, 1u);   // Al^T Xh
+            for (int sb = 0; sb < SUB; ++sb) {
+              const uint32_t aAs = aA + sb * A_TILE;
+              const uint64_t ad = TRANS ? umma_desc(aAs + 2048 * k, 8192, 1024) : umma_desc(aAs + 32 * k, 16, 1024);
+              if (F8)
+                mma_e4m3(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
+              else
+                mma_bf16(dtm + (uint32_t)(sb * g.NA), ad, bd, idesc, accum);
+              if (SPLIT3) {
+                const uint64_t ad2 = TRANS ? umma_desc(aAs + A_TILE + 2048 * k, 8192, 1024)
+                                           : umma_desc(aAs + A_TILE + 32 * k, 16, 1024);
+                const uint64_t bd2 = umma_desc(aB + b_bytes + 2048 * k, 8192, 1024);
+                mma_bf16(dtm, ad, bd2, idesc, 1u);   // Ah^T Xl
+                mma_bf16(dtm, ad2, bd, idesc, 1u);   // Al^T Xh
+              }
             }
           }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+        sg = se;
       }
-      if (!ok) break;
-      mma_commit(&tfull[acc]);
     }
     if (!ok) {
       set_status(g.st, RSVD_E_TIMEOUT);
@@ -223,67 +240,77 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int r = 32 * q + lane;
     const bool yvec = (g.ldy % 4) == 0 && (((uintptr_t)g.Y) & 15) == 0;
     int j = 0;
-    for (int t = t_first; t <= t_last; ++t, ++j) {
+    bool alive = true;
+    for (int t = t_first; t <= t_last && alive; ++t) {
       const int kb_lo = (int)((t == t_first) ? u0 - (long long)t * g.KB : 0);
       const int kb_hi = (int)((t == t_last) ? u1 - (long long)t * g.KB : g.KB);
-      const int acc = j % g.nbuf;
-      const uint32_t aph = (uint32_t)(j / g.nbuf) & 1u;
-      if (!mbar_wait(&tfull[acc], aph)) {
-        set_status(g.st, RSVD_E_TIMEOUT);
-        abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
       const bool whole = (kb_lo == 0 && kb_hi == g.KB);
+      for (int sg = kb_lo; sg < kb_hi; ++j) {
+        const int se = seg_end(sg, kb_hi, g.seg);
+        const bool first = (sg == kb_lo);  // later segments add to what the earlier ones stored
+        const int acc = j % g.nbuf;
+        const uint32_t aph = (uint32_t)(j / g.nbuf) & 1u;
+        if (!mbar_wait(&tfull[acc], aph)) {
+          set_status(g.st, RSVD_E_TIMEOUT);
+          abort_flag = 1;
+          alive = false;
+          break;
+        }
+        tc_fence_after();
 #pragma unroll 1
-      for (int sb = 0; sb < SUB; ++sb) {
-      const int row = t * BM + 128 * sb + r;
-      float* dst;
-      bool store = true;
-      if (whole) {
-        dst = g.Y + (size_t)row * g.ldy;
-        store = row < g.M;
-      } else {
-        const int slot = (t == t_first) ? 0 : 1;
-        dst = g.part + (((size_t)c * 2 + slot) * BM + 128 * sb + r) * g.Npad;
-      }
-      const uint32_t taddr = tbase + (uint32_t)((acc * SUB + sb) * g.NA) + ((uint32_t)(32 * q) << 16);
-      const float rsc = (F8 && g.rs && row < g.M) ? g.rs[row] : 1.0f;
-      for (int c16 = 0; c16 < g.Npad; c16 += 16) {
-        uint32_t v[16];
-        tmem_ld16(taddr + c16, v);
-        tmem_wait_ld();
-        if (F8) {
-          // scales are linear, so partial tiles can be scaled before the fix-up adds them
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float cv = (c16 + e < g.N) ? g.cs[c16 + e] : 0.0f;
-            v[e] = __float_as_uint(__uint_as_float(v[e]) * rsc * cv);
-          }
-        }
-        if (store) {
-          if (whole && yvec && c16 + 16 <= g.N) {
-            // 16-byte stores: a quarter of the store instructions (each still
-            // touches the 32 rows of the warp)
-#pragma unroll
-            for (int e = 0; e < 16; e += 4)
-              *reinterpret_cast<float4*>(dst + c16 + e) = make_float4(
-                  __uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
-          } else if (whole) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (c16 + e < g.N) dst[c16 + e] = __uint_as_float(v[e]);
+        for (int sb = 0; sb < SUB; ++sb) {
+          const int row = t * BM + 128 * sb + r;
+          float* dst;
+          bool store = true;
+          if (whole) {
+            dst = g.Y + (size_t)row * g.ldy;
+            store = row < g.M;
           } else {
+            const int slot = (t == t_first) ? 0 : 1;
+            dst = g.part + (((size_t)c * 2 + slot) * BM + 128 * sb + r) * g.Npad;
+          }
+          const uint32_t taddr = tbase + (uint32_t)((acc * SUB + sb) * g.NA) + ((uint32_t)(32 * q) << 16);
+          const float rsc = (F8 && g.rs && row < g.M) ? g.rs[row] : 1.0f;
+          for (int c16 = 0; c16 < g.Npad; c16 += 16) {
+            uint32_t v[16];
+            tmem_ld16(taddr + c16, v);
+            tmem_wait_ld();
+            if (F8) {
+              // scales are linear, so partial tiles can be scaled before the fix-up adds them
 #pragma unroll
-            for (int e = 0; e < 16; e += 4)
-              *reinterpret_cast<float4*>(dst + c16 + e) = make_float4(
-                  __uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+              for (int e = 0; e < 16; ++e) {
+                const float cv = (c16 + e < g.N) ? g.cs[c16 + e] : 0.0f;
+                v[e] = __float_as_uint(__uint_as_float(v[e]) * rsc * cv);
+              }
+            }
+            const bool vec = !whole || (yvec && c16 + 16 <= g.N);
+            if (!store) {
+            } else if (vec) {
+              // 16-byte accesses (each instruction still touches the 32 rows of the warp)
+#pragma unroll
+              for (int e = 0; e < 16; e += 4) {
+                float4 o = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                                       __uint_as_float(v[e + 3]));
+                if (!first) {
+                  const float4 p = *reinterpret_cast<const float4*>(dst + c16 + e);
+                  o.x += p.x;
+                  o.y += p.y;
+                  o.z += p.z;
+                  o.w += p.w;
+                }
+                *reinterpret_cast<float4*>(dst + c16 + e) = o;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c16 + e < g.N) dst[c16 + e] = __uint_as_float(v[e]) + (first ? 0.0f : dst[c16 + e]);
+            }
           }
         }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);
+        sg = se;
       }
-      }
-      tc_fence_before();
-      mbar_arrive(&tempty[acc]);
     }
   }
   __syncthreads();
@@ -428,6 +455,10 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   g.NA = pow2_at_least(g.Npad);
   g.nchunk = ceil_div(N, 64);
   g.nbuf = (2 * SUBT * g.NA <= 512) ? 2 : 1;
+  // TMEM segments: 1024 K for the three-term projection (192 accumulating
+  // MMAs, truncation drift about 4e-6 relative), 8192 K for the plain
+  // sketches (whose bf16 inputs carry 2^-9 relative rounding anyway)
+  g.seg = split3 ? 16 : 128;
   g.Y = Y;
   g.ldy = ldy;
   g.part = part;
@@ -530,6 +561,7 @@ cudaError_t launch_tc_gemm_e4m3(int M, int N, int K, const uint8_t* A8, int lda,
   g.NA = pow2_at_least(g.Npad);
   g.nchunk = 1;
   g.nbuf = (2 * SUBT * g.NA <= 512) ? 2 : 1;
+  g.seg = 64;  // 8192 K per TMEM segment
   g.Y = Y;
   g.ldy = ldy;
   g.part = part;

@@ -10,8 +10,9 @@
 // 160 x 2 x 128 x 128 fp32 partial tiles, 20 MiB, plus 256 bytes of status);
 // every GPU that loads the library holds the array until the process exits.
 // The array is shared by every call: calls that overlap on the GPU (on
-// different streams, or from different host threads) race on it and must be
-// serialized by the caller.
+// different streams, or from different host threads) race on it, status word
+// included, and must be serialized by the caller.  The call runs on the
+// current device, which must be the handle's.
 #include <mutex>
 
 #include "common.cuh"
@@ -64,7 +65,8 @@ rsvd_status handle_fail(rsvd_handle_t h, rsvd_status code, const char* msg);
 using namespace rsvd;
 
 extern "C" rsvd_status rsvd_sketch_noalloc(rsvd_handle_t handle, int trans, int m, int n, int l, const void* A,
-                                           int lda, const void* X, int ldx, float* Y, int ldy, rsvd_stream_t stream) {
+                                           int lda, const void* X, int ldx, float* Y, int ldy, int* status_out,
+                                           rsvd_stream_t stream) {
   if (!handle) return RSVD_E_INVALID;
   if (m < 0 || n < 0 || l < 0) return handle_fail(handle, RSVD_E_INVALID, "rsvd_sketch_noalloc: negative size");
   if (l > NOALLOC_MAX_L)
@@ -77,6 +79,12 @@ extern "C" rsvd_status rsvd_sketch_noalloc(rsvd_handle_t handle, int trans, int 
   if ((lda % 8) || (ldx % 8) || (((uintptr_t)A | (uintptr_t)X) & 15))
     return handle_fail(handle, RSVD_E_INVALID,
                        "rsvd_sketch_noalloc: bf16 operands need 16-byte aligned rows (lda, ldx multiples of 8)");
+  // the scratch array exists once per device; the kernel must run on the
+  // device whose copy it writes
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: cudaGetDevice failed");
+  if (cur != handle_device(handle))
+    return handle_fail(handle, RSVD_E_INVALID, "rsvd_sketch_noalloc: the current device is not the handle's device");
   void* base = nullptr;
   rsvd_status st = scratch_for(handle_device(handle), &base);
   if (st != RSVD_OK) return handle_fail(handle, st, "rsvd_sketch_noalloc: cudaGetSymbolAddress failed");
@@ -94,5 +102,9 @@ extern "C" rsvd_status rsvd_sketch_noalloc(rsvd_handle_t handle, int trans, int 
                                        (const __nv_bfloat16*)X, ldx, nullptr, Y, ldy, part, sms, dst, s, 128);
   if (e != cudaSuccess) return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: launch failed");
   if (cudaGetLastError() != cudaSuccess) return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: launch failed");
+  // the device status word (RSVD_E_TIMEOUT if a bounded wait gave up) is
+  // private to the library's array: copy it out for the caller, in stream order
+  if (status_out && cudaMemcpyAsync(status_out, &dst->code, sizeof(int), cudaMemcpyDefault, s) != cudaSuccess)
+    return handle_fail(handle, RSVD_E_CUDA, "rsvd_sketch_noalloc: status copy failed");
   return RSVD_OK;
 }

@@ -22,11 +22,9 @@ What is checked, and why it must hold:
   sigma_{k+1} here (checked at 2 sigma_{k+1} on sampled right singular
   vectors; for orthonormal V the vector is A v_i - d_i u_i);
 * U^T U = V^T V = I to binary32 accuracy (the lift is a binary32 product);
-* PCA: the signal's singular values move by about eta^2 (m + n) / (2 sigma)
-  under noise of entry size eta (8e-4 relative for sigma_48; the column
-  centring adds about chi^2 / (2 m), under 3e-5 at m = 2^20), and the residual
-  is the noise that the rank-64 space does not capture, just under the noise's
-  own norm eta sqrt(m n) (0.993 of it measured).
+* PCA: against the exact singular values of the generated matrix (float64
+  A^T A and its eigenvalues), for the e4m3, bf16 and binary32 paths alike;
+  its own docstring states the bounds.
 """
 import pytest
 
@@ -88,32 +86,71 @@ def test_poly_decay_32768_bf16_full_size(lib):
     torch.cuda.empty_cache()
 
 
+def _exact_sigma(A, rows=65536):
+    """Singular values of A (float32 on the device) from A^T A formed in
+    float64 blockwise and eigvalsh, descending: exact to about 1e-16 ||A||^2
+    in the squares, far below every tolerance checked here."""
+    import torch
+    n = A.shape[1]
+    G = torch.zeros(n, n, dtype=torch.float64, device=A.device)
+    for r0 in range(0, A.shape[0], rows):
+        Ab = A[r0:r0 + rows].double()
+        G.addmm_(Ab.T, Ab)
+        del Ab
+    lam = torch.linalg.eigvalsh(G).flip(0).clamp_min(0)
+    del G
+    return lam.sqrt(), lam
+
+
 def test_pca_2p20x4096_e4m3_full_size(lib):
+    """The PCA workload through the benchmark's call, e4m3 sketches, with the
+    bf16 and binary32 paths on the same matrix beside it, against the exact
+    singular values of the generated A (not its construction values: the noise
+    moves those by about eta^2 (m + n) / (2 sigma)).
+
+    * d_i <= sigma_i (interlacing: the d_i are the singular values of Q^T A,
+      Sec. 3 Remark 3.2), up to the projection's rounding;
+    * for the 48 strongest directions the method's own error is second order
+      in the angle between the signal direction and range(Q), sin^2 theta <=
+      (1.09 / 26)^(2 (2q + 1)) < 1e-8 (the noise's singular values end at
+      eta (sqrt m + sqrt n) = 1.09, the 48th signal value is 26), so what
+      remains is rounding: on the binary32 path |d_i - sigma_i| <= 1e-5
+      sigma_i (the tolerance stated for that path; 7.7e-6 measured); on the
+      mixed paths the split-bf16 projection perturbs B = Q^T A by about 2^-16
+      of ||A||_2 (pair representation 2^-17 per operand, the dropped Al^T Ql
+      term 2^-18, the tensor core's truncating accumulation bounded by
+      1024-element segments), so |d_i - sigma_i| <= 5e-5 sigma_1 (1.5e-5
+      sigma_1 measured);
+    * Eckart-Young: the Frobenius residual is at least the optimum
+      sqrt(sum_{i > k} lambda_i) over rank-k matrices and within 0.5% of it
+      (the weakest signal directions, sigma ~ 1.4 .. 5.8, lie at the noise
+      edge, which q = 1 separates only partly);
+    * U^T U = V^T V = I to binary32 accuracy.
+    """
     import torch
     from workloads import pca_matrix
     m, n = 1 << 20, 4096
     k, p, q = 64, 64, 1
-    eta = 1e-3
     A = pca_matrix(m, n, seed=3001, device="cuda")
-    U, D, V = lib.fixed_rank(A, k, p, q, seed=3101, prec=lib.RSVD_MIXED_FP8)
-    torch.cuda.synchronize()
-    d = D.double()
-    s = torch.linspace(100.0, 1.0, 64, dtype=torch.float64, device="cuda")
-    # the 48 strongest signal directions stand well clear of the noise edge
-    # eta (sqrt m + sqrt n) = 1.09
-    shift = eta * eta * (m + n) / (2 * s[:48])
-    rel = ((d[:48] - s[:48]).abs() / s[:48])
-    assert float(rel.max()) < 2e-3, float(rel.max())
-    assert float((rel - shift / s[:48]).abs().max()) < 5e-4
-    assert _orth_err(U) < 1e-4 and _orth_err(V) < 1e-4
-    res, _ = _fro_residual(A, U, D, V, rows=65536)
-    floor = eta * (m * n) ** 0.5
-    # a k-dimensional space captures at most k eta^2 (sqrt m + sqrt n)^2 of
-    # the noise's energy (Ky Fan; the noise's singular values end at
-    # eta (sqrt m + sqrt n)): 0.991 of the floor remains at this size
-    lo = (1.0 - k * (m ** 0.5 + n ** 0.5) ** 2 / (m * n)) ** 0.5 - 0.02
-    assert lo * floor <= res <= 1.01 * floor, (res / floor, lo)
-    del A, U, D, V
+    sig, lam = _exact_sigma(A)
+    opt = float(lam[k:].sum().sqrt())
+    for prec in (lib.RSVD_MIXED_FP8, lib.RSVD_MIXED_BF16, lib.RSVD_F32):
+        U, D, V = lib.fixed_rank(A, k, p, q, seed=3101, prec=prec)
+        torch.cuda.synchronize()
+        d = D.double()
+        assert bool((d[:-1] >= d[1:]).all())
+        assert bool((d <= sig[:k] * (1 + 1e-5)).all()), (prec, float((d / sig[:k]).max()))
+        err = (d[:48] - sig[:48]).abs()
+        if prec == lib.RSVD_F32:
+            assert float((err / sig[:48]).max()) <= 1e-5, (prec, float((err / sig[:48]).max()))
+        else:
+            assert float(err.max()) <= 5e-5 * float(sig[0]), (prec, float(err.max() / sig[0]))
+        assert _orth_err(U) < 1e-4 and _orth_err(V) < 1e-4, prec
+        res, _ = _fro_residual(A, U, D, V, rows=65536)
+        assert opt * (1 - 1e-6) <= res <= 1.005 * opt, (prec, res / opt)
+        del U, D, V
+        torch.cuda.empty_cache()
+    del A
     torch.cuda.empty_cache()
 
 

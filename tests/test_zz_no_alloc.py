@@ -1,10 +1,19 @@
 """rsvd_sketch_noalloc: the bf16 tensor-core sketch product for callers that
-cannot allocate device memory (no workspace argument; the scratch is a fixed
-array in the library).  Checked against rsvd_sketch, the entry point that takes
-a caller workspace, on two calls in a row (the second call reuses the scratch
-the first one left behind).  This file is collected last on purpose."""
-import ctypes
+cannot allocate device memory -- code running inside another framework's
+memory pool, an allocation-free real-time loop, or a plugin that is handed only
+its input and output buffers.  It takes no workspace: its scratch is a fixed
+array inside the library.
 
+Each case runs the call twice in a row (the second call reuses the scratch the
+first one left behind) and checks every element of Y against the exact
+float64 product of the same bf16 operands, within the binary32 accumulation
+bound the other tensor-core tests use, and against rsvd_sketch (the entry
+point with a caller workspace) within the same bound.  The cases cover both
+operand layouts, a ragged M, K long enough that every tile is split between
+many CTAs (partial tiles in the fixed array, added by the fix-up kernel) and a
+K long enough that one CTA adds several TMEM segments of a tile.  This file is
+collected last on purpose: a failure here leaves every other test already run.
+"""
 import numpy as np
 import pytest
 
@@ -14,7 +23,7 @@ U32 = 2.0 ** -24
 
 def _bf16(rng, shape):
     import torch
-    x = torch.from_numpy(rng.standard_normal(shape)).to(torch.float32).to(torch.bfloat16).cuda()
+    x = torch.from_numpy(rng.standard_normal(shape, dtype=np.float32)).to(torch.bfloat16).cuda()
     r, c = shape
     c8 = (c + 7) // 8 * 8
     buf = torch.zeros(r, c8, dtype=torch.bfloat16, device="cuda")
@@ -22,8 +31,13 @@ def _bf16(rng, shape):
     return buf[:, :c]
 
 
-@pytest.mark.parametrize("trans,m,n,l", [(False, 3000, 2000, 128), (True, 5000, 700, 96), (False, 256, 20000, 64)])
-def test_noalloc_matches_workspace_entry_point(lib, trans, m, n, l):
+@pytest.mark.parametrize("trans,m,n,l", [
+    (False, 3000, 2000, 128),     # NN, ragged M (3000 = 23 x 128 + 56)
+    (True, 5000, 700, 96),        # TN (A^T X), ragged M = 700
+    (False, 256, 20000, 64),      # two tiles, each split between ~76 CTAs
+    (False, 128, 1 << 21, 16),    # one tile, ~215 k-blocks per CTA: two TMEM segments each
+])
+def test_noalloc_matches_exact_product_and_workspace_entry_point(lib, trans, m, n, l):
     import torch
     h = lib.handle()
     rng = np.random.default_rng(m + n + l)
@@ -34,14 +48,22 @@ def test_noalloc_matches_workspace_entry_point(lib, trans, m, n, l):
     A64 = A.float().cpu().numpy().astype(np.float64)
     X64 = X.float().cpu().numpy().astype(np.float64)
     Aop = A64.T if trans else A64
+    exact = Aop @ X64
     bound = 2 * K * U32 * (np.abs(Aop) @ np.abs(X64)) + 1e-30
+    del A64, Aop
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
     for call in range(2):
-        ref = lib.sketch(A, X, trans=trans, prec=lib.RSVD_MIXED_BF16).cpu().numpy().astype(np.float64)
         Y = torch.full((M, l), float("nan"), dtype=torch.float32, device="cuda")
-        code = lib.rsvd_sketch_noalloc(h, int(trans), m, n, l, A, A.stride(0), X, X.stride(0), Y, Y.stride(0))
+        code = lib.rsvd_sketch_noalloc(h, int(trans), m, n, l, A, A.stride(0), X, X.stride(0), Y, Y.stride(0),
+                                       status=status)
         assert code == lib.RSVD_OK, lib.last_error(h)
+        torch.cuda.synchronize()
+        assert int(status.item()) == lib.RSVD_OK
         got = Y.cpu().numpy().astype(np.float64)
-        assert np.all(np.isfinite(got))
+        assert np.all(np.isfinite(got)), call
+        err = np.abs(got - exact)
+        assert np.all(err <= bound), (call, float(np.max(err / bound)))
+        ref = lib.sketch(A, X, trans=trans, prec=lib.RSVD_MIXED_BF16).cpu().numpy().astype(np.float64)
         assert np.all(np.abs(got - ref) <= bound), (call, float(np.max(np.abs(got - ref) / bound)))
 
 

@@ -84,7 +84,10 @@ enum {
   RSVD_FLAG_RETURN_FULL_L = 1, /* return all l = k + p triplets instead of k */
   RSVD_FLAG_SYNC = 2,          /* block until the work ends; return the device status */
   RSVD_FLAG_CERTIFY = 4,       /* reserved; the a-posteriori certificate is rsvd_certify */
-  RSVD_FLAG_USE_CONTROLLER = 8 /* rsvd_adaptive_tol: learned (l, q) controller */
+  RSVD_FLAG_USE_CONTROLLER = 8, /* rsvd_adaptive_tol: learned (l, q) controller */
+  RSVD_FLAG_SPECTRAL = 16,      /* rsvd_adaptive_tol: spectral-norm stopping test (Sec. 13) */
+  RSVD_FLAG_CENTER = 32,        /* rsvd_fixed_rank: factor the column-centred A - 1 mu^T (PCA) */
+  RSVD_FLAG_KRYLOV = 64         /* rsvd_fixed_rank: block Krylov basis, q counts blocks */
 };
 
 typedef struct {
@@ -94,7 +97,8 @@ typedef struct {
   int block;      /* adaptive block size b (0 -> 16) */
   int max_rank;   /* adaptive cap on the rank (0 -> min(m, n)) */
   int probe_cols; /* reserved (controller probe width) */
-  double tol;     /* adaptive: relative Frobenius tolerance, eps = tol ||A||_Fro */
+  double tol;     /* adaptive: relative Frobenius tolerance, eps = tol ||A||_Fro
+                     (RSVD_FLAG_SPECTRAL: the absolute spectral tolerance eps) */
   uint64_t seed;  /* key of the Philox4x32-10 Gaussian stream */
   int prec;       /* rsvd_precision */
   int flags;      /* RSVD_FLAG_* */
@@ -128,7 +132,20 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
  *   is positive (lowest index on ties).
  * The random test matrix is the Philox4x32-10 stream keyed by params->seed:
  * G(i, j) comes from counter (i / 4, j, 0, 0) through a 24-bit Box-Muller map
- * (see rsvd_gaussian). */
+ * (see rsvd_gaussian).
+ * RSVD_FLAG_CENTER (PCA, Sec. 1): factor the column-centred Abar = A - 1 mu^T,
+ * mu = A^T 1 / m, without forming it: mu is one more read of A (binary64
+ * sums), and every product carries its rank-one correction, Abar X = A X -
+ * 1 (mu^T X) and Abar^T Y = A^T Y - mu (1^T Y).  Workspace grows by a few
+ * vectors (rsvd_workspace_size with the flag set).
+ * RSVD_FLAG_KRYLOV (Sec. "Extended sampling matrix"): params->q >= 1 counts
+ * blocks; Q spans [A G, (A A^T) A G, ..., (A A^T)^(q-1) A G], w = q (k + p)
+ * columns (w <= 256, 128 for RSVD_F64), Stage B on the w x n matrix B = Q^T A
+ * (RSVD_FLAG_RETURN_FULL_L returns all w triplets).  Each block is formed
+ * from the previous block's orthonormal basis and projected against the
+ * blocks before it, which spans the same space in exact arithmetic.  Passes
+ * over A: 2q.  Precisions RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16 (k + p a
+ * multiple of 8); not combined with RSVD_FLAG_CENTER. */
 rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, int lda,
                             const rsvd_params* params, void* U, int ldu, double* D, void* V,
                             int ldv, void* workspace, size_t ws_bytes, rsvd_stream_t stream);
@@ -171,8 +188,18 @@ rsvd_status rsvd_nystrom(rsvd_handle_t handle, int n, const void* A, int lda, co
  * That path synchronizes the stream twice (to read the choice and the judge's
  * verdict).
  *   U, V : capacity max_rank columns (ldu, ldv >= max_rank).
+ * With RSVD_FLAG_SPECTRAL (Sec. 13: the stopping test of Fig. adaptive2 and
+ * Lemma thm:aposteriori with alpha = 1/10; q must be 0): tol is an ABSOLUTE
+ * spectral-norm tolerance eps > 0.  Before block t is appended, its fresh
+ * samples A_j G_t = (I - Q Q^T) A G_t are the b probes; if each has norm at
+ * most eps / (10 sqrt(2/pi)), the loop stops without appending them, and then
+ * ||A - Q B||_2 <= eps with probability at least 1 - 10^-b.  Otherwise the
+ * block is appended exactly as in the Frobenius mode.
  *   rank_out : DEVICE int, receives the rank r (a multiple of b, or max_rank).
- *   err_out  : DEVICE double, receives ||A - Q B||_Fro / ||A||_Fro.
+ *   err_out  : DEVICE double, receives ||A - Q B||_Fro / ||A||_Fro; in the
+ *              spectral mode an absolute bound on ||A - Q B||_2 instead: the
+ *              probe bound 10 sqrt(2/pi) max_i ||A_j g_i|| of the block that
+ *              stopped the loop, or ||A - Q B||_Fro if the cap came first.
  * Entries of D, U, V beyond r are set to zero.  If the cap is hit first the
  * status is RSVD_E_NOT_CONVERGED and the outputs hold the rank-max_rank
  * factorization. */

@@ -38,6 +38,9 @@ RSVD_FLAG_RETURN_FULL_L = 1
 RSVD_FLAG_SYNC = 2
 RSVD_FLAG_CERTIFY = 4
 RSVD_FLAG_USE_CONTROLLER = 8
+RSVD_FLAG_SPECTRAL = 16
+RSVD_FLAG_CENTER = 32
+RSVD_FLAG_KRYLOV = 64
 
 STATUS_NAMES = {0: "RSVD_OK", 1: "RSVD_E_INVALID", 2: "RSVD_E_NOMEM", 3: "RSVD_E_CUDA", 4: "RSVD_E_BREAKDOWN",
                 5: "RSVD_E_NOT_CONVERGED", 6: "RSVD_E_NONFINITE", 7: "RSVD_E_TIMEOUT", 8: "RSVD_E_UNSUPPORTED"}
@@ -423,15 +426,20 @@ def _prec_dtype(prec):
     return torch.float64 if prec == RSVD_F64 else torch.float32
 
 
-def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws=None, out=None):
+def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws=None, out=None, centre=False,
+               krylov=False):
     """A ~= U diag(D) V^T by rsvd_fixed_rank.  A: (m, n) row-major CUDA tensor
-    (float64 for RSVD_F64, else float32).  Returns (U, D, V)."""
+    (float64 for RSVD_F64, else float32).  centre=True factors the
+    column-centred matrix without forming it (RSVD_FLAG_CENTER);
+    krylov=True takes the block Krylov basis of q blocks (RSVD_FLAG_KRYLOV).
+    Returns (U, D, V)."""
     import torch
     h = handle(A.device.index)
     m, n = A.shape
     flags = (RSVD_FLAG_RETURN_FULL_L if full else 0) | (RSVD_FLAG_SYNC if sync else 0)
+    flags |= (RSVD_FLAG_CENTER if centre else 0) | (RSVD_FLAG_KRYLOV if krylov else 0)
     prm = make_params(k, p, q, seed, prec, flags)
-    kk = k + p if full else k
+    kk = ((k + p) * (q if krylov else 1)) if full else k
     dt = _prec_dtype(prec)
     if out is None:
         U = torch.empty(m, kk, dtype=dt, device=A.device)
@@ -445,16 +453,17 @@ def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws
     return U, D, V
 
 
-def adaptive_tol(A, tol, block=16, max_rank=0, seed=0, prec=RSVD_F32, q=0, controller=False):
+def adaptive_tol(A, tol, block=16, max_rank=0, seed=0, prec=RSVD_F32, q=0, controller=False, spectral=False):
     """Tolerance-driven randomized SVD by rsvd_adaptive_tol (q power steps per
     block; with controller=True the learned controller attached to the
-    device's handle chooses (l, q)).  Returns (U, D, V, rank, err, status):
-    U, V have max_rank columns, the first `rank` valid; status is RSVD_OK or
-    RSVD_E_NOT_CONVERGED (other failures raise)."""
+    device's handle chooses (l, q); with spectral=True tol is an absolute
+    spectral-norm tolerance, RSVD_FLAG_SPECTRAL).  Returns (U, D, V, rank,
+    err, status): U, V have max_rank columns, the first `rank` valid; status
+    is RSVD_OK or RSVD_E_NOT_CONVERGED (other failures raise)."""
     import torch
     h = handle(A.device.index)
     m, n = A.shape
-    flags = RSVD_FLAG_USE_CONTROLLER if controller else 0
+    flags = (RSVD_FLAG_USE_CONTROLLER if controller else 0) | (RSVD_FLAG_SPECTRAL if spectral else 0)
     prm = make_params(0, 0, q, seed, prec, flags, tol=tol, block=block, max_rank=max_rank)
     R = max_rank if max_rank > 0 else min(m, n, 128 if prec == RSVD_F64 else 256)
     dt = _prec_dtype(prec)

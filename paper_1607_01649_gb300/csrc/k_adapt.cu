@@ -20,6 +20,11 @@
 // from every later step (the residual would stall near tol = 1e-6); the second
 // pass leaves only the square of that.
 //   stop when ||A_j||_F <= tol ||A||_F, or the rank reaches max_rank.
+// Spectral mode (Sec. 13, Fig. adaptive2 and Lemma thm:aposteriori): before
+// a block is appended, its fresh samples A_j G_t = (I - Q Q^T) A G_t serve as
+// the b probes; if each has norm at most eps / (10 sqrt(2/pi)), then
+// ||A - Q B||_2 <= eps with probability at least 1 - 10^-b and the loop stops
+// without appending (no power steps in this mode).
 // Every kernel of a step returns at once when the device flag `done` is set,
 // so the host enqueues ceil(max_rank / b) steps without synchronizing.
 #include "common.cuh"
@@ -241,9 +246,10 @@ __global__ void adapt_update_kernel(int m, int n, int bb, T* __restrict__ Aj, co
 }
 
 // Stopping test after step t: rank = tb + bb; ||A_j||_F^2 = sum of the update
-// partials (fixed order); done when <= eps^2 or the rank reaches max_rank.
+// partials (fixed order); done when <= eps^2 (Frobenius mode only) or the
+// rank reaches max_rank.
 __global__ void adapt_check_kernel(int nparts, const double* __restrict__ pnorm, int new_rank, int max_rank,
-                                   DevStatus* st) {
+                                   int spectral, DevStatus* st) {
   if (threadIdx.x != 0 || st->done) return;
   double r2 = 0.0;
   for (int p = 0; p < nparts; ++p) r2 += pnorm[p];
@@ -252,11 +258,64 @@ __global__ void adapt_check_kernel(int nparts, const double* __restrict__ pnorm,
   if (!isfinite(r2)) {
     set_status(st, RSVD_E_NONFINITE);
     st->done = 1;
-  } else if (r2 <= st->scratch[0]) {
+  } else if (!spectral && r2 <= st->scratch[0]) {
     st->done = 1;
   } else if (new_rank >= max_rank) {
     set_status(st, RSVD_E_NOT_CONVERGED);
     st->done = 1;
+  }
+}
+
+// Spectral-norm stopping test (Fig. adaptive2 with Lemma thm:aposteriori,
+// alpha = 1/10): the fresh block Y = A_j G_t, drawn independently of the
+// current Q, holds b samples (I - Q Q^T) A g_i.  Partial column sums of
+// squares in binary64 over row slices, then the test.
+constexpr int PROBE_ROWS = 2048;
+template <typename T>
+__global__ void __launch_bounds__(256) adapt_probe_partial_kernel(int m, int bb, const T* __restrict__ Y, int ldy,
+                                                                  double* __restrict__ pp, const int* done) {
+  if (*done) return;
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int r0 = blockIdx.x * PROBE_ROWS, r1 = min(m, r0 + PROBE_ROWS);
+  double acc = 0.0;
+  if (lane < bb)
+    for (int i = r0 + warp; i < r1; i += 8) {
+      const double v = (double)Y[(size_t)i * ldy + lane];
+      acc = fma(v, v, acc);
+    }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w][lane];
+    pp[(size_t)blockIdx.x * 32 + lane] = s;
+  }
+}
+
+// Sums the partials in a fixed order; stops the loop (rank unchanged) when
+// every probe norm is at most thresh = eps / (10 sqrt(2/pi)).  The largest
+// probe norm is kept in scratch[1].
+__global__ void adapt_probe_check_kernel(int parts, int bb, const double* __restrict__ pp, double thresh,
+                                         DevStatus* st) {
+  if (st->done) return;
+  const int lane = threadIdx.x;
+  double s = 0.0;
+  if (lane < bb)
+    for (int p = 0; p < parts; ++p) s += pp[(size_t)p * 32 + lane];
+  double mx = lane < bb ? s : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    const double nrm = sqrt(mx);
+    st->scratch[1] = nrm;
+    if (!isfinite(nrm)) {
+      set_status(st, RSVD_E_NONFINITE);
+      st->done = 1;
+    } else if (nrm <= thresh) {
+      st->scratch[2] = 1.0;  // converged on the spectral test
+      st->done = 1;
+    }
   }
 }
 
@@ -273,6 +332,7 @@ size_t adapt_workspace_bytes(int m, int n, int R, int b, int sms, size_t es) {
   c.take<double>((size_t)splits * n * 32);                   // Bt partials (binary64)
   const size_t np = (size_t)ceil_div(m, 32) * ceil_div(n, 32);
   c.take<double>(np > 4096 ? np : 4096);                     // norm partials
+  c.take<double>((size_t)ceil_div(m, PROBE_ROWS) * 32);       // probe partials
   (void)sms;
   return c.size();
 }
@@ -282,6 +342,7 @@ struct AdaptBufs {
   T *Aj, *Q, *Bt, *B2, *G, *Cp;
   double* Btp;
   double* pn;
+  double* pp;
 };
 
 template <typename T>
@@ -297,6 +358,7 @@ AdaptBufs<T> adapt_carve(void* ws, int m, int n, int R, int b) {
   B.Btp = c.take<double>((size_t)64 * n * 32);
   const size_t np = (size_t)ceil_div(m, 32) * ceil_div(n, 32);
   B.pn = c.take<double>(np > 4096 ? np : 4096);
+  B.pp = c.take<double>((size_t)ceil_div(m, PROBE_ROWS) * 32);
   return B;
 }
 
@@ -306,7 +368,8 @@ AdaptBufs<T> adapt_carve(void* ws, int m, int n, int R, int b) {
 // squared norms.
 template <typename T, typename C>
 void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, int q, uint64_t seed, void* ws,
-                  void* orthws, DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout) {
+                  void* orthws, DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout, double spectral_eps) {
+  const bool spectral = spectral_eps > 0.0;
   AdaptBufs<T> B = adapt_carve<T>(ws, m, n, R, b);
   *Qout = B.Q;
   *Btout = B.Bt;
@@ -324,6 +387,15 @@ void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, i
     launch_gaussian(n, bb, seed, 1u, tb, dt, B.G, b, s);
     adapt_sketch_kernel<T><<<ceil_div(m, 8), 256, 0, s>>>(m, n, bb, B.Aj, B.G, b, Y, R, done);
     note_launch();
+    if (spectral) {
+      // the fresh samples are the probes: stop before appending them if
+      // max_i ||A_j g_i|| <= eps / (10 sqrt(2/pi))
+      const int parts = ceil_div(m, PROBE_ROWS);
+      adapt_probe_partial_kernel<T><<<parts, 256, 0, s>>>(m, bb, Y, R, B.pp, done);
+      note_launch();
+      adapt_probe_check_kernel<<<1, 32, 0, s>>>(parts, bb, B.pp, spectral_eps / (10.0 * sqrt(2.0 / M_PI)), st);
+      note_launch();
+    }
     for (int j = 0; j < q; ++j) {
       // Y = orth(Y); Z = orth(A_j^T Y) (into the G buffer, binary64 row sums);
       // Y = A_j Z
@@ -365,14 +437,14 @@ void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, i
       adapt_update_kernel<T><<<ug, 256, 0, s>>>(m, n, bb, B.Aj, Y, R, dst, R, B.pn, done);
       note_launch();
     }
-    adapt_check_kernel<<<1, 32, 0, s>>>((int)(ug.x * ug.y), B.pn, tb + bb, R, st);
+    adapt_check_kernel<<<1, 32, 0, s>>>((int)(ug.x * ug.y), B.pn, tb + bb, R, spectral ? 1 : 0, st);
     note_launch();
   }
 }
 
 template void run_adaptive<float, float>(int, int, const float*, int, double, int, int, int, uint64_t, void*,
-                                         void*, DevStatus*, int, cudaStream_t, float**, float**);
+                                         void*, DevStatus*, int, cudaStream_t, float**, float**, double);
 template void run_adaptive<double, double>(int, int, const double*, int, double, int, int, int, uint64_t, void*,
-                                           void*, DevStatus*, int, cudaStream_t, double**, double**);
+                                           void*, DevStatus*, int, cudaStream_t, double**, double**, double);
 
 }  // namespace rsvd

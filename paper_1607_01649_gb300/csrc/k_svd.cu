@@ -323,9 +323,19 @@ __global__ void __launch_bounds__(512)
       ss = (double)part;
       const double sg = sqrt(ss);
       const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
+      // J is orthogonal in exact arithmetic; each binary32 rotation scales its
+      // two columns by 1 + O(u) (the hardware reciprocal square root is not
+      // correctly rounded), and over a few thousand rotations per column the
+      // norms drift by up to ~1e-4 while the columns stay orthogonal, so each
+      // column is rescaled to unit norm
+      C jp = C(0);
+      for (int i = lane; i < l; i += 32) jp = fma(jv[i], jv[i], jp);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) jp += __shfl_xor_sync(0xffffffffu, jp, o);
+      const double jinv = jp > C(0) ? 1.0 / sqrt((double)jp) : 1.0;
       for (int i = lane; i < l; i += 32) {
         Wt[(size_t)col * l + i] = (C)((double)x[i] * inv);
-        Jt[(size_t)col * l + i] = jv[i];
+        Jt[(size_t)col * l + i] = (C)((double)jv[i] * jinv);
       }
       if (lane == 0) sigma[col] = sg;
     }

@@ -271,39 +271,65 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           const uint32_t taddr = tbase + (uint32_t)((acc * SUB + sb) * g.NA) + ((uint32_t)(32 * q) << 16);
           const float rsc = (F8 && g.rs && row < g.M) ? g.rs[row] : 1.0f;
-          for (int c16 = 0; c16 < g.Npad; c16 += 16) {
-            uint32_t v[16];
-            tmem_ld16(taddr + c16, v);
-            tmem_wait_ld();
-            if (F8) {
-              // scales are linear, so partial tiles can be scaled before the fix-up adds them
+          // columns this thread may write: Y's N, or the partial row's Npad
+          const int lim = whole ? g.N : g.Npad;
+          const bool v4 = !whole || yvec;  // 16-byte accesses allowed where 4 columns fit
+#pragma unroll 1
+          for (int c0 = 0; c0 < g.Npad; c0 += 64) {
+            // what the earlier segments stored, loaded for 64 columns at once
+            // before the TMEM reads, so one L2 latency covers the group
+            float old[64];
+            if (!first && store) {
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const float cv = (c16 + e < g.N) ? g.cs[c16 + e] : 0.0f;
-                v[e] = __float_as_uint(__uint_as_float(v[e]) * rsc * cv);
-              }
-            }
-            const bool vec = !whole || (yvec && c16 + 16 <= g.N);
-            if (!store) {
-            } else if (vec) {
-              // 16-byte accesses (each instruction still touches the 32 rows of the warp)
+              for (int e = 0; e < 64; e += 4) {
+                const int cc = c0 + e;
+                if (v4 && cc + 4 <= lim) {
+                  const float4 p = *reinterpret_cast<const float4*>(dst + cc);
+                  old[e] = p.x;
+                  old[e + 1] = p.y;
+                  old[e + 2] = p.z;
+                  old[e + 3] = p.w;
+                } else {
 #pragma unroll
-              for (int e = 0; e < 16; e += 4) {
-                float4 o = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
-                                       __uint_as_float(v[e + 3]));
-                if (!first) {
-                  const float4 p = *reinterpret_cast<const float4*>(dst + c16 + e);
-                  o.x += p.x;
-                  o.y += p.y;
-                  o.z += p.z;
-                  o.w += p.w;
+                  for (int x = 0; x < 4; ++x) old[e + x] = (cc + x < lim) ? dst[cc + x] : 0.0f;
                 }
-                *reinterpret_cast<float4*>(dst + c16 + e) = o;
               }
             } else {
 #pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (c16 + e < g.N) dst[c16 + e] = __uint_as_float(v[e]) + (first ? 0.0f : dst[c16 + e]);
+              for (int e = 0; e < 64; ++e) old[e] = 0.0f;
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int c16 = c0 + 16 * h;
+              if (c16 >= g.Npad) break;  // uniform over the warp
+              uint32_t v[16];
+              tmem_ld16(taddr + c16, v);
+              tmem_wait_ld();
+              float o[16];
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                float x = __uint_as_float(v[e]);
+                if (F8) {
+                  // scales are linear, so partial tiles can be scaled before the fix-up adds them
+                  const float cv = (c16 + e < g.N) ? g.cs[c16 + e] : 0.0f;
+                  x = x * rsc * cv;
+                }
+                o[e] = x + old[16 * h + e];
+              }
+              if (store) {
+#pragma unroll
+                for (int e = 0; e < 16; e += 4) {
+                  const int cc = c16 + e;
+                  if (v4 && cc + 4 <= lim) {
+                    // 16-byte stores (each instruction still touches the 32 rows of the warp)
+                    *reinterpret_cast<float4*>(dst + cc) = make_float4(o[e], o[e + 1], o[e + 2], o[e + 3]);
+                  } else {
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                      if (cc + x < lim) dst[cc + x] = o[e + x];
+                  }
+                }
+              }
             }
           }
         }
@@ -456,9 +482,10 @@ cudaError_t launch_tc_gemm(bool trans, bool split3, int M, int N, int K, const _
   g.nchunk = ceil_div(N, 64);
   g.nbuf = (2 * SUBT * g.NA <= 512) ? 2 : 1;
   // TMEM segments: 1024 K for the three-term projection (192 accumulating
-  // MMAs, truncation drift about 4e-6 relative), 8192 K for the plain
-  // sketches (whose bf16 inputs carry 2^-9 relative rounding anyway)
-  g.seg = split3 ? 16 : 128;
+  // MMAs, truncation drift about 4e-6 relative); 65536 K for the plain
+  // sketches, whose bf16 inputs carry 2^-9 relative rounding anyway (one
+  // segment per tile up to K = 65536, drift under 1e-4 beyond)
+  g.seg = split3 ? 16 : 1024;
   g.Y = Y;
   g.ldy = ldy;
   g.part = part;
@@ -561,7 +588,7 @@ cudaError_t launch_tc_gemm_e4m3(int M, int N, int K, const uint8_t* A8, int lda,
   g.NA = pow2_at_least(g.Npad);
   g.nchunk = 1;
   g.nbuf = (2 * SUBT * g.NA <= 512) ? 2 : 1;
-  g.seg = 64;  // 8192 K per TMEM segment
+  g.seg = 512;  // 65536 K per TMEM segment, as for the bf16 sketches
   g.Y = Y;
   g.ldy = ldy;
   g.part = part;

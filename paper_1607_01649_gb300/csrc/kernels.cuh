@@ -90,7 +90,25 @@ void launch_fp8_cols(int rows, int cols, const float* X, int ldx, const float* r
 size_t adapt_workspace_bytes(int m, int n, int R, int b, int sms, size_t es);
 template <typename T, typename C>
 void run_adaptive(int m, int n, const T* A, int lda, double tol, int R, int b, int q, uint64_t seed, void* ws,
-                  void* orthws, DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout);
+                  void* orthws, DevStatus* st, int sms, cudaStream_t s, T** Qout, T** Btout,
+                  double spectral_eps = 0.0);  // > 0: spectral-norm stopping test with this absolute eps
+
+// k_centre.cu (implicit column centring, RSVD_FLAG_CENTER)
+struct CentreBufs {
+  double* mu;    // n column means
+  double* vec;   // l: mu^T X or 1^T Q
+  double* part;  // per-slice partial sums
+};
+size_t centre_workspace_bytes(int m, int n, int l, int sms);
+CentreBufs centre_carve(void* ws, int m, int n, int l, int sms);
+template <typename T>
+void centre_means(int m, int n, const T* A, int lda, const CentreBufs& B, int sms, cudaStream_t s);
+template <typename T, typename X>
+void centre_forward(int m, int n, int l, const X* Xop, int ldx, T* Y, int ldy, const CentreBufs& B, int sms,
+                    cudaStream_t s);
+template <typename T, typename Q>
+void centre_adjoint(int m, int n, int l, const Q* Qm, int ldq, T* Z, int ldz, const CentreBufs& B, int sms,
+                    cudaStream_t s);
 
 // k_batched.cu
 int batched_max_rank();

@@ -127,14 +127,21 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   if (p->k < 0 || p->p < 0 || p->q < 0) return fail(h, RSVD_E_INVALID, "k, p, q must be >= 0");
   if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16 && p->prec != RSVD_MIXED_FP8)
     return fail(h, RSVD_E_UNSUPPORTED, "precision %d is not implemented", p->prec);
-  const int l = p->k + p->p;
+  const int l0 = p->k + p->p;
+  const bool krylov = (p->flags & RSVD_FLAG_KRYLOV) != 0;
+  if (krylov && p->q < 1) return fail(h, RSVD_E_INVALID, "block Krylov: q (the number of blocks) must be >= 1");
+  const int l = krylov ? l0 * p->q : l0;  // the basis width
   const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
   *kk_out = kk;
   if (p->k == 0) return RSVD_OK;
   const int mn = m < n ? m : n;
-  if (l > mn) return fail(h, RSVD_E_INVALID, "l = k + p = %d exceeds min(m, n) = %d", l, mn);
+  if (l > mn) return fail(h, RSVD_E_INVALID, "basis width %d exceeds min(m, n) = %d", l, mn);
   if (l > max_l_for(p->prec))
-    return fail(h, RSVD_E_UNSUPPORTED, "l = %d exceeds the supported maximum %d", l, max_l_for(p->prec));
+    return fail(h, RSVD_E_UNSUPPORTED, "basis width %d exceeds the supported maximum %d", l, max_l_for(p->prec));
+  if (krylov && p->prec == RSVD_MIXED_FP8)
+    return fail(h, RSVD_E_UNSUPPORTED, "block Krylov runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
+  if (krylov && p->prec == RSVD_MIXED_BF16 && (l0 % 8) != 0)
+    return fail(h, RSVD_E_INVALID, "block Krylov in RSVD_MIXED_BF16 needs k + p a multiple of 8");
   if (lda < n) return fail(h, RSVD_E_INVALID, "lda %d < n %d", lda, n);
   if (ldu < kk || ldv < kk) return fail(h, RSVD_E_INVALID, "ldu/ldv smaller than the output rank %d", kk);
   if (!A || !U || !D || !V) return fail(h, RSVD_E_INVALID, "NULL matrix pointer");
@@ -152,7 +159,8 @@ rsvd_status check_access(rsvd_handle_t h, const void* A, const void* U, const vo
 
 template <typename T, typename C>
 rsvd_status fixed_rank_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, const rsvd_params* p, T* U,
-                            int ldu, double* D, T* V, int ldv, const FixedLayout& L, cudaStream_t s) {
+                            int ldu, double* D, T* V, int ldv, const FixedLayout& L, cudaStream_t s,
+                            const CentreBufs* cb = nullptr) {
   const int l = p->k + p->p;
   const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
   const int sms = h->sms;
@@ -163,18 +171,24 @@ rsvd_status fixed_rank_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, 
   const int dt = sizeof(T) == 8 ? RSVD_DT_F64 : RSVD_DT_F32;
   // G = randn(n, l)
   launch_gaussian(n, l, p->seed, 0u, 0, dt, Om, l, s);
+  // implicit centring: column means, then a rank-one correction per product
+  if (cb) centre_means<T>(m, n, A, lda, *cb, sms, s);
   // Q = orth(A G)
   launch_gemm_simt<T>(false, m, l, n, A, lda, Om, l, Y, l, part, sms, s);
+  if (cb) centre_forward<T, T>(m, n, l, Om, l, Y, l, *cb, sms, s);
   run_orth<T, C>(m, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   // q power steps with orth after every product
   for (int j = 0; j < p->q; ++j) {
     launch_gemm_simt<T>(true, n, l, m, A, lda, Y, l, Z, l, part, sms, s);
+    if (cb) centre_adjoint<T, T>(m, n, l, Y, l, Z, l, *cb, sms, s);
     run_orth<T, C>(n, l, Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
     launch_gemm_simt<T>(false, m, l, n, A, lda, Z, l, Y, l, part, sms, s);
+    if (cb) centre_forward<T, T>(m, n, l, Z, l, Y, l, *cb, sms, s);
     run_orth<T, C>(m, l, Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   }
   // B^T = A^T Q, then B^T = Q_B R_B
   launch_gemm_simt<T>(true, n, l, m, A, lda, Y, l, Z, l, part, sms, s);
+  if (cb) centre_adjoint<T, T>(m, n, l, Y, l, Z, l, *cb, sms, s);
   run_orth<T, C>(n, l, Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
   // SVD of R_B^T by one-sided Jacobi
   cudaError_t e = launch_jacobi<C>(l, L.Rb, (C*)L.Wt, (C*)L.Jt, L.sigma, L.st, s);
@@ -330,7 +344,8 @@ rsvd_status tc_call(rsvd_handle_t h, cudaError_t e, const char* what) {
 // accumulation, binary64-accumulated Gram matrices, three-term split-bf16
 // projection B^T = A^T Q.
 rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int lda, const rsvd_params* p, float* U,
-                             int ldu, double* D, float* V, int ldv, const MixedLayout& L, cudaStream_t s) {
+                             int ldu, double* D, float* V, int ldv, const MixedLayout& L, cudaStream_t s,
+                             const CentreBufs* cb = nullptr) {
   const int l = p->k + p->p;
   const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
   const int sms = h->sms;
@@ -340,6 +355,8 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
   launch_split_bf16(m, n, A, lda, L.Ah, L.Al, n8, sms, s);
   // G = randn(n, l), bf16
   launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_BF16, L.Omb, l8, s);
+  // implicit centring: column means of A, then a rank-one correction per product
+  if (cb) centre_means<float>(m, n, A, lda, *cb, sms, s);
   // Q = orth(A G)
   {
     ProfScope ps(h, 0, s);
@@ -347,6 +364,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                         sms, L.st, s), "sketch A G")) != RSVD_OK)
       return st;
   }
+  if (cb) centre_forward<float, __nv_bfloat16>(m, n, l, L.Omb, l8, L.Y, l, *cb, sms, s);
   run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
   // power steps
   for (int j = 0; j < p->q; ++j) {
@@ -356,6 +374,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                           L.part, sms, L.st, s), "sketch A^T Q")) != RSVD_OK)
         return st;
     }
+    if (cb) centre_adjoint<float, __nv_bfloat16>(m, n, l, L.Yb, l8, L.Z, l, *cb, sms, s);
     run_orth_tc(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s);
     {
       ProfScope ps(h, 0, s);
@@ -363,6 +382,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                           L.part, sms, L.st, s), "sketch A W")) != RSVD_OK)
         return st;
     }
+    if (cb) centre_forward<float, __nv_bfloat16>(m, n, l, L.Zb, l8, L.Y, l, *cb, sms, s);
     run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
   }
   // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
@@ -373,6 +393,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
                                         L.st, s), "projection")) != RSVD_OK)
       return st;
   }
+  if (cb) centre_adjoint<float, float>(m, n, l, L.Y, l, L.Z, l, *cb, sms, s);
   run_orth_tc(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
   // SVD of R_B^T
   cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
@@ -450,7 +471,7 @@ SketchFp8 sketch_fp8_layout(void* ws, int trans, int m, int n, int l, int sms) {
 // and lift as the bf16 path.
 rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int lda, const rsvd_params* p, float* U,
                            int ldu, double* D, float* V, int ldv, const MixedLayout& L, const Fp8Extra& E,
-                           cudaStream_t s) {
+                           cudaStream_t s, const CentreBufs* cb = nullptr) {
   const int l = p->k + p->p;
   const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? l : p->k;
   const int sms = h->sms;
@@ -461,6 +482,8 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
   launch_u8_transpose(m, n, E.A8, n16, E.A8T, m16, s);
   // G = randn(n, l); Y = A G
   launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_F32, E.Om, l, s);
+  // implicit centring: column means of A, then a rank-one correction per product
+  if (cb) centre_means<float>(m, n, A, lda, *cb, sms, s);
   launch_fp8_cols(n, l, E.Om, l, nullptr, E.X8t, n16, E.cvec, E.colws, s);
   {
     ProfScope ps(h, 0, s);
@@ -468,6 +491,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                              s), "e4m3 sketch A G")) != RSVD_OK)
       return st;
   }
+  if (cb) centre_forward<float, float>(m, n, l, E.Om, l, L.Y, l, *cb, sms, s);
   run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   for (int j = 0; j < p->q; ++j) {
     // Z = A^T Q = A8^T (S Q)
@@ -478,6 +502,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                                L.st, s), "e4m3 sketch A^T Q")) != RSVD_OK)
         return st;
     }
+    if (cb) centre_adjoint<float, float>(m, n, l, L.Y, l, L.Z, l, *cb, sms, s);
     run_orth_tc(n, l, L.Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
     launch_fp8_cols(n, l, L.Z, l, nullptr, E.X8t, n16, E.cvec, E.colws, s);
     {
@@ -486,6 +511,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                                L.st, s), "e4m3 sketch A W")) != RSVD_OK)
         return st;
     }
+    if (cb) centre_forward<float, float>(m, n, l, L.Z, l, L.Y, l, *cb, sms, s);
     run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
   }
   // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
@@ -496,6 +522,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
                                         L.st, s), "projection")) != RSVD_OK)
       return st;
   }
+  if (cb) centre_adjoint<float, float>(m, n, l, L.Y, l, L.Z, l, *cb, sms, s);
   run_orth_tc(n, l, L.Z, l, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
   cudaError_t e = launch_jacobi<float>(l, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
   if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
@@ -504,6 +531,156 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
   launch_sign_fix<float, float>(n, kk, l, V, ldv, L.Wsel, L.part, s);
   launch_gemm_simt<float>(false, m, kk, l, L.Y, l, L.Wsel, kk, U, ldu, nullptr, sms, s);
   return check_launch(h, "rsvd_fixed_rank (e4m3)");
+}
+
+// ------------------------------------------------------------ block Krylov --
+// Randomized SVD on the extended sampling matrix (Sec. "Extended sampling
+// matrix"): the basis spans [A G, (A A^T) A G, ..., (A A^T)^(q-1) A G], q
+// blocks of l = k + p columns, w = q l in all; then Stage B on B = Q^T A.
+// The section forms the blocks by plain repeated products; in binary32 their
+// scales drift apart as sigma^(2j) and the last blocks lose what the first
+// ones hold, so here each new block is taken from the previous block's
+// orthonormal basis (Z = orth(A^T Q_(j-1)), Y_j = A Z: the same span, as in
+// Fig. RSVDP_stabilized), projected twice against the blocks before it and
+// orthonormalized.  In exact arithmetic Q spans the same Krylov space, so U,
+// D and V are those of the section's method.
+template <typename T>
+__global__ void sub_inplace_kernel(int rows, int cols, T* __restrict__ Y, int ldy, const T* __restrict__ X, int ldx) {
+  const long long total = (long long)rows * cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), j = (int)(e % cols);
+    Y[(size_t)i * ldy + j] -= X[(size_t)i * ldx + j];
+  }
+}
+
+template <typename T>
+void launch_sub_inplace(int rows, int cols, T* Y, int ldy, const T* X, int ldx, int sms, cudaStream_t s) {
+  const long long total = (long long)rows * cols;
+  if (total == 0) return;
+  long long want = (total + 1023) / 1024;
+  const int blocks = (int)(want < sms * 8 ? want : sms * 8);
+  sub_inplace_kernel<T><<<blocks, 256, 0, s>>>(rows, cols, Y, ldy, X, ldx);
+  note_launch();
+}
+
+struct KrylovExtra {
+  void* C;     // w x l coefficients
+  void* T;     // m x l product Q_prev C
+  void* part;  // split-K partials of Q_prev^T Y_j
+  size_t bytes;
+};
+
+KrylovExtra krylov_extra(void* ws, int m, int w, int l, size_t es, int sms) {
+  Carver c(ws);
+  KrylovExtra K;
+  K.C = c.take<unsigned char>((size_t)w * l * es);
+  K.T = c.take<unsigned char>((size_t)m * l * es);
+  size_t pw = simt_gemm_workspace(w, l, m, sms, es);
+  const size_t pw2 = simt_gemm_workspace(m, l, w, sms, es);
+  if (pw2 > pw) pw = pw2;
+  K.part = c.take<unsigned char>(pw + 256);
+  K.bytes = c.size();
+  return K;
+}
+
+// Y_j (m x l, ld w) -= Q_prev (Q_prev^T Y_j), Q_prev = the jl columns before it; twice.
+template <typename T>
+void krylov_project(int m, int w, int l, int j, T* Y, const KrylovExtra& K, int sms, cudaStream_t s) {
+  T* Yj = Y + (size_t)j * l;
+  for (int rep = 0; rep < 2; ++rep) {
+    launch_gemm_simt<T>(true, j * l, l, m, Y, w, Yj, w, (T*)K.C, l, (T*)K.part, sms, s);
+    launch_gemm_simt<T>(false, m, l, j * l, Y, w, (const T*)K.C, l, (T*)K.T, l, (T*)K.part, sms, s);
+    launch_sub_inplace<T>(m, l, Yj, w, (const T*)K.T, l, sms, s);
+  }
+}
+
+template <typename T, typename C>
+rsvd_status fixed_rank_krylov_simt(rsvd_handle_t h, int m, int n, const T* A, int lda, const rsvd_params* p, T* U,
+                                   int ldu, double* D, T* V, int ldv, const FixedLayout& L, const KrylovExtra& K,
+                                   cudaStream_t s) {
+  const int l = p->k + p->p, qb = p->q, w = l * qb;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? w : p->k;
+  const int sms = h->sms;
+  T* Om = (T*)L.Om;
+  T* Y = (T*)L.Ybuf;  // m x w
+  T* Z = (T*)L.Zbuf;  // n x l per block, then B^T n x w
+  T* part = (T*)L.part;
+  const int dt = sizeof(T) == 8 ? RSVD_DT_F64 : RSVD_DT_F32;
+  launch_gaussian(n, l, p->seed, 0u, 0, dt, Om, l, s);
+  launch_gemm_simt<T>(false, m, l, n, A, lda, Om, l, Y, w, part, sms, s);
+  run_orth<T, C>(m, l, Y, w, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  for (int j = 1; j < qb; ++j) {
+    launch_gemm_simt<T>(true, n, l, m, A, lda, Y + (size_t)(j - 1) * l, w, Z, l, part, sms, s);
+    run_orth<T, C>(n, l, Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    launch_gemm_simt<T>(false, m, l, n, A, lda, Z, l, Y + (size_t)j * l, w, part, sms, s);
+    krylov_project<T>(m, w, l, j, Y, K, sms, s);
+    run_orth<T, C>(m, l, Y + (size_t)j * l, w, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  }
+  // B^T = A^T Q (n x w), B^T = Q_B R_B, SVD of R_B^T, lift
+  launch_gemm_simt<T>(true, n, w, m, A, lda, Y, w, Z, w, part, sms, s);
+  run_orth<T, C>(n, w, Z, w, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  cudaError_t e = launch_jacobi<C>(w, L.Rb, (C*)L.Wt, (C*)L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<C>(w, kk, L.sigma, (const C*)L.Wt, (const C*)L.Jt, D, (C*)L.Wsel, (C*)L.Jsel, s);
+  launch_gemm_simt<T>(false, n, kk, w, Z, w, (const T*)L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_sign_fix<T, C>(n, kk, w, V, ldv, (C*)L.Wsel, L.part, s);
+  launch_gemm_simt<T>(false, m, kk, w, Y, w, (const T*)L.Wsel, kk, U, ldu, nullptr, sms, s);
+  return check_launch(h, "rsvd_fixed_rank (block Krylov)");
+}
+
+// The same on tensor cores (RSVD_MIXED_BF16): bf16 products for the blocks,
+// the three-term split-bf16 projection for B^T = A^T Q (w <= 256 columns);
+// the projections of the blocks against each other run in binary32.
+rsvd_status fixed_rank_krylov_mixed(rsvd_handle_t h, int m, int n, const float* A, int lda, const rsvd_params* p,
+                                    float* U, int ldu, double* D, float* V, int ldv, const MixedLayout& L,
+                                    const KrylovExtra& K, cudaStream_t s) {
+  const int l = p->k + p->p, qb = p->q, w = l * qb;
+  const int kk = (p->flags & RSVD_FLAG_RETURN_FULL_L) ? w : p->k;
+  const int sms = h->sms;
+  const int n8 = round8(n), l8 = round8(l);  // l % 8 == 0, so w8 == w
+  rsvd_status st;
+  launch_split_bf16(m, n, A, lda, L.Ah, L.Al, n8, sms, s);
+  launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_BF16, L.Omb, l8, s);
+  {
+    ProfScope ps(h, 0, s);
+    if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Omb, l8, nullptr, L.Y, w, L.part,
+                                        sms, L.st, s), "Krylov block 0")) != RSVD_OK)
+      return st;
+  }
+  run_orth_tc(m, l, L.Y, w, nullptr, L.Yb, w, L.orthws, L.st, sms, s);
+  for (int j = 1; j < qb; ++j) {
+    {
+      ProfScope ps(h, 0, s);
+      if ((st = tc_call(h, launch_tc_gemm(true, false, n, l, m, L.Ah, n8, nullptr, L.Yb + (size_t)(j - 1) * l, w,
+                                          nullptr, L.Z, l, L.part, sms, L.st, s), "Krylov A^T Q")) != RSVD_OK)
+        return st;
+    }
+    run_orth_tc(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s);
+    {
+      ProfScope ps(h, 0, s);
+      if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Zb, l8, nullptr,
+                                          L.Y + (size_t)j * l, w, L.part, sms, L.st, s), "Krylov A W")) != RSVD_OK)
+        return st;
+    }
+    krylov_project<float>(m, w, l, j, L.Y, K, sms, s);
+    run_orth_tc(m, l, L.Y + (size_t)j * l, w, nullptr, L.Yb + (size_t)j * l, w, L.orthws, L.st, sms, s);
+  }
+  launch_split_bf16(m, w, L.Y, w, L.Yb, L.Yl, w, sms, s);
+  {
+    ProfScope ps(h, 1, s);
+    if ((st = tc_call(h, launch_tc_gemm(true, true, n, w, m, L.Ah, n8, L.Al, L.Yb, w, L.Yl, L.Z, w, L.part, sms,
+                                        L.st, s), "projection")) != RSVD_OK)
+      return st;
+  }
+  run_orth_tc(n, w, L.Z, w, L.Rb, nullptr, 0, L.orthws, L.st, sms, s);
+  cudaError_t e = launch_jacobi<float>(w, L.Rb, L.Wt, L.Jt, L.sigma, L.st, s);
+  if (e != cudaSuccess) return fail(h, RSVD_E_CUDA, "jacobi launch: %s", cudaGetErrorString(e));
+  launch_sort_gather<float>(w, kk, L.sigma, L.Wt, L.Jt, D, L.Wsel, L.Jsel, s);
+  launch_gemm_simt<float>(false, n, kk, w, L.Z, w, L.Jsel, kk, V, ldv, nullptr, sms, s);
+  launch_sign_fix<float, float>(n, kk, w, V, ldv, L.Wsel, L.part, s);
+  launch_gemm_simt<float>(false, m, kk, w, L.Y, w, L.Wsel, kk, U, ldu, nullptr, sms, s);
+  return check_launch(h, "rsvd_fixed_rank (block Krylov, mixed)");
 }
 
 // ---------------------------------------------------------- adaptive path --
@@ -527,7 +704,13 @@ rsvd_status validate_adaptive(rsvd_handle_t h, int m, int n, const void* A, int 
   if (m < 1 || n < 1) return fail(h, RSVD_E_INVALID, "m and n must be >= 1");
   if (p->prec != RSVD_F64 && p->prec != RSVD_F32)
     return fail(h, RSVD_E_UNSUPPORTED, "rsvd_adaptive_tol supports RSVD_F64 and RSVD_F32");
-  if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  if (p->flags & RSVD_FLAG_SPECTRAL) {
+    if (!(p->tol > 0.0) || !isfinite(p->tol))
+      return fail(h, RSVD_E_INVALID, "spectral mode: tol (absolute eps) must be positive and finite");
+    if (p->q != 0) return fail(h, RSVD_E_INVALID, "spectral mode takes no power steps (q must be 0)");
+  } else if (!(p->tol > 0.0) || !(p->tol < 1.0)) {
+    return fail(h, RSVD_E_INVALID, "tol must lie in (0, 1)");
+  }
   if (p->q < 0 || p->q > 8) return fail(h, RSVD_E_INVALID, "q must lie in [0, 8]");
   const AdaptParams a = adapt_params(m, n, p);
   if (a.b < 1 || a.b > 32) return fail(h, RSVD_E_INVALID, "block must lie in [1, 32]");
@@ -598,7 +781,9 @@ rsvd_status adaptive_impl(rsvd_handle_t h, int m, int n, const T* A, int lda, co
   const AdaptParams a = adapt_params(m, n, p);
   T *Q = nullptr, *Bt = nullptr;
   cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
-  run_adaptive<T, C>(m, n, A, lda, p->tol, a.R, a.b, p->q, p->seed, L.abufs, L.orthws, L.st, h->sms, s, &Q, &Bt);
+  const bool spectral = (p->flags & RSVD_FLAG_SPECTRAL) != 0;
+  run_adaptive<T, C>(m, n, A, lda, spectral ? 0.5 : p->tol, a.R, a.b, p->q, p->seed, L.abufs, L.orthws, L.st,
+                     h->sms, s, &Q, &Bt, spectral ? p->tol : 0.0);
   rsvd_status st = check_launch(h, "rsvd_adaptive_tol");
   if (st != RSVD_OK) return st;
   // one synchronization: the rank sizes Stage B
@@ -617,7 +802,13 @@ rsvd_status adaptive_impl(rsvd_handle_t h, int m, int n, const T* A, int lda, co
     cudaMemset2DAsync(U + rank, (size_t)ldu * sizeof(T), 0, (size_t)(a.R - rank) * sizeof(T), m, s);
     cudaMemset2DAsync(V + rank, (size_t)ldv * sizeof(T), 0, (size_t)(a.R - rank) * sizeof(T), n, s);
   }
-  const double err = hs.fro2_a > 0.0 ? sqrt(hs.fro2_res > 0.0 ? hs.fro2_res / hs.fro2_a : 0.0) : 0.0;
+  double err = hs.fro2_a > 0.0 ? sqrt(hs.fro2_res > 0.0 ? hs.fro2_res / hs.fro2_a : 0.0) : 0.0;
+  if (spectral) {
+    // absolute bounds on ||A - Q B||_2: the probe bound of the block that
+    // stopped the loop (Lemma thm:aposteriori), else ||A - Q B||_Fro
+    err = hs.scratch[2] != 0.0 ? 10.0 * sqrt(2.0 / M_PI) * hs.scratch[1]
+                               : sqrt(hs.fro2_res > 0.0 ? hs.fro2_res : 0.0);
+  }
   if (rank_out) cudaMemcpyAsync(rank_out, &L.st->rank, sizeof(int), cudaMemcpyDeviceToDevice, s);
   if (err_out) cudaMemcpyAsync(err_out, &err, sizeof(double), cudaMemcpyHostToDevice, s);
   e = cudaStreamSynchronize(s);
@@ -958,13 +1149,24 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
   rsvd_status st = validate_fixed(handle, m, n, (const void*)1, n, params, (const void*)1, 1 << 30,
                                   (const void*)1, (const void*)1, 1 << 30, &kk);
   if (st != RSVD_OK) return st;
-  const int l = params->k + params->p;
+  int l = params->k + params->p;
+  if (params->flags & RSVD_FLAG_KRYLOV) {
+    const int l0 = l;
+    l *= params->q;
+    const size_t es = params->prec == RSVD_F64 ? 8 : 4;
+    const size_t base = params->prec == RSVD_MIXED_BF16 ? mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes
+                                                        : fixed_layout(nullptr, m, n, l, kk, params->prec, handle->sms).bytes;
+    *bytes = base + krylov_extra(nullptr, m, l, l0, es, handle->sms).bytes;
+    if (params->flags & RSVD_FLAG_CENTER) return fail(handle, RSVD_E_UNSUPPORTED, "block Krylov does not centre");
+    return RSVD_OK;
+  }
   if (params->prec == RSVD_MIXED_BF16)
     *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes;
   else if (params->prec == RSVD_MIXED_FP8)
     *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes + fp8_extra(nullptr, m, n, l, handle->sms).bytes;
   else
     *bytes = fixed_layout(nullptr, m, n, l, kk, params->prec, handle->sms).bytes;
+  if (params->flags & RSVD_FLAG_CENTER) *bytes += centre_workspace_bytes(m, n, l, handle->sms);
   return RSVD_OK;
 }
 
@@ -984,11 +1186,46 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
   if (!workspace || ws_bytes < need)
     return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
   if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  if (params->flags & RSVD_FLAG_KRYLOV) {
+    const int w = l * params->q;
+    const size_t es = params->prec == RSVD_F64 ? 8 : 4;
+    if (params->prec == RSVD_MIXED_BF16) {
+      if (((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
+      const MixedLayout M = mixed_layout(workspace, m, n, w, kk, handle->sms);
+      const KrylovExtra K = krylov_extra((char*)workspace + M.bytes, m, w, l, es, handle->sms);
+      cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
+      st = fixed_rank_krylov_mixed(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M,
+                                   K, s);
+      if (st != RSVD_OK) return st;
+      return finish_sync(handle, params, M.st, s);
+    }
+    const FixedLayout L = fixed_layout(workspace, m, n, w, kk, params->prec, handle->sms);
+    const KrylovExtra K = krylov_extra((char*)workspace + L.bytes, m, w, l, es, handle->sms);
+    cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
+    if (params->prec == RSVD_F64)
+      st = fixed_rank_krylov_simt<double, double>(handle, m, n, (const double*)A, lda, params, (double*)U, ldu, D,
+                                                  (double*)V, ldv, L, K, s);
+    else
+      st = fixed_rank_krylov_simt<float, float>(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D,
+                                                (float*)V, ldv, L, K, s);
+    if (st != RSVD_OK) return st;
+    return finish_sync(handle, params, L.st, s);
+  }
+  // implicit centring buffers sit after the path's own layout
+  const bool centre = (params->flags & RSVD_FLAG_CENTER) != 0;
+  CentreBufs cbuf;
+  const CentreBufs* cb = nullptr;
+  auto carve_centre = [&](size_t off) {
+    if (!centre) return;
+    cbuf = centre_carve((char*)workspace + off, m, n, l, handle->sms);
+    cb = &cbuf;
+  };
   if (params->prec == RSVD_MIXED_BF16) {
     if (((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
     const MixedLayout M = mixed_layout(workspace, m, n, l, kk, handle->sms);
+    carve_centre(M.bytes);
     cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
-    st = fixed_rank_mixed(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, s);
+    st = fixed_rank_mixed(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, s, cb);
     if (st != RSVD_OK) return st;
     return finish_sync(handle, params, M.st, s);
   }
@@ -996,19 +1233,21 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
     if (((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
     const MixedLayout M = mixed_layout(workspace, m, n, l, kk, handle->sms);
     const Fp8Extra E = fp8_extra((char*)workspace + M.bytes, m, n, l, handle->sms);
+    carve_centre(M.bytes + E.bytes);
     cudaMemsetAsync(M.st, 0, sizeof(DevStatus), s);
-    st = fixed_rank_fp8(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, E, s);
+    st = fixed_rank_fp8(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V, ldv, M, E, s, cb);
     if (st != RSVD_OK) return st;
     return finish_sync(handle, params, M.st, s);
   }
   const FixedLayout L = fixed_layout(workspace, m, n, l, kk, params->prec, handle->sms);
+  carve_centre(L.bytes);
   cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
   if (params->prec == RSVD_F64)
     st = fixed_rank_simt<double, double>(handle, m, n, (const double*)A, lda, params, (double*)U, ldu, D,
-                                         (double*)V, ldv, L, s);
+                                         (double*)V, ldv, L, s, cb);
   else
     st = fixed_rank_simt<float, float>(handle, m, n, (const float*)A, lda, params, (float*)U, ldu, D, (float*)V,
-                                       ldv, L, s);
+                                       ldv, L, s, cb);
   if (st != RSVD_OK) return st;
   return finish_sync(handle, params, L.st, s);
 }

@@ -87,7 +87,9 @@ enum {
   RSVD_FLAG_USE_CONTROLLER = 8, /* rsvd_adaptive_tol: learned (l, q) controller */
   RSVD_FLAG_SPECTRAL = 16,      /* rsvd_adaptive_tol: spectral-norm stopping test (Sec. 13) */
   RSVD_FLAG_CENTER = 32,        /* rsvd_fixed_rank: factor the column-centred A - 1 mu^T (PCA) */
-  RSVD_FLAG_KRYLOV = 64         /* rsvd_fixed_rank: block Krylov basis, q counts blocks */
+  RSVD_FLAG_KRYLOV = 64,        /* rsvd_fixed_rank: block Krylov basis, q counts blocks */
+  RSVD_FLAG_SINGLE_PASS = 128,  /* rsvd_fixed_rank: single-pass SVD (sketches only, fitted core) */
+  RSVD_FLAG_SYMMETRIC = 256     /* with RSVD_FLAG_SINGLE_PASS: single-pass EVD of a symmetric A */
 };
 
 typedef struct {
@@ -145,7 +147,22 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
  * from the previous block's orthonormal basis and projected against the
  * blocks before it, which spans the same space in exact arithmetic.  Passes
  * over A: 2q.  Precisions RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16 (k + p a
- * multiple of 8); not combined with RSVD_FLAG_CENTER. */
+ * multiple of 8); not combined with RSVD_FLAG_CENTER.
+ * RSVD_FLAG_SINGLE_PASS (Sec. "Single pass algorithms", Fig. singlepass_gen):
+ * the sketches Yc = A Gc and Yr = A^T Gr (Gc the Omega stream, Gr Philox
+ * stream 5) are the only products with A; Qc, Qr = the k dominant left
+ * singular vectors of Yc, Yr; the k x k core C minimizes ||P C - R1||_F^2 +
+ * ||C M - R2||_F^2 (P = Gr^T Qc, R1 = Yr^T Qr, M = Qr^T Gc, R2 = Qc^T Yc),
+ * solved in binary64 as the Sylvester equation of its normal equations;
+ * U = Qc Uhat, V = Qr Vhat from C = Uhat D Vhat^T.  q must be 0, k <= 128,
+ * outputs k triplets.  The two sketches are separate launches (A is read
+ * twice; nothing depends on a basis).  With RSVD_FLAG_SYMMETRIC (Fig.
+ * singlepass_herm; A symmetric, m = n): Y = A G only, the symmetric core
+ * minimizing ||C (Q^T G) - Q^T Y||_F (a Lyapunov equation), D receives the k
+ * eigenvalues ordered by decreasing magnitude (signed), U the eigenvectors
+ * (largest-magnitude entry positive) and V a copy of U.  Precisions RSVD_F64,
+ * RSVD_F32, RSVD_MIXED_BF16 (bf16 tensor-core sketches, the rest binary32
+ * and binary64). */
 rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, int lda,
                             const rsvd_params* params, void* U, int ldu, double* D, void* V,
                             int ldv, void* workspace, size_t ws_bytes, rsvd_stream_t stream);

@@ -41,6 +41,8 @@ RSVD_FLAG_USE_CONTROLLER = 8
 RSVD_FLAG_SPECTRAL = 16
 RSVD_FLAG_CENTER = 32
 RSVD_FLAG_KRYLOV = 64
+RSVD_FLAG_SINGLE_PASS = 128
+RSVD_FLAG_SYMMETRIC = 256
 
 STATUS_NAMES = {0: "RSVD_OK", 1: "RSVD_E_INVALID", 2: "RSVD_E_NOMEM", 3: "RSVD_E_CUDA", 4: "RSVD_E_BREAKDOWN",
                 5: "RSVD_E_NOT_CONVERGED", 6: "RSVD_E_NONFINITE", 7: "RSVD_E_TIMEOUT", 8: "RSVD_E_UNSUPPORTED"}
@@ -427,17 +429,19 @@ def _prec_dtype(prec):
 
 
 def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws=None, out=None, centre=False,
-               krylov=False):
+               krylov=False, single_pass=False, symmetric=False):
     """A ~= U diag(D) V^T by rsvd_fixed_rank.  A: (m, n) row-major CUDA tensor
     (float64 for RSVD_F64, else float32).  centre=True factors the
     column-centred matrix without forming it (RSVD_FLAG_CENTER);
-    krylov=True takes the block Krylov basis of q blocks (RSVD_FLAG_KRYLOV).
-    Returns (U, D, V)."""
+    krylov=True takes the block Krylov basis of q blocks (RSVD_FLAG_KRYLOV);
+    single_pass=True is the single-pass SVD (q must be 0), with
+    symmetric=True the single-pass EVD (D signed, V = U).  Returns (U, D, V)."""
     import torch
     h = handle(A.device.index)
     m, n = A.shape
     flags = (RSVD_FLAG_RETURN_FULL_L if full else 0) | (RSVD_FLAG_SYNC if sync else 0)
     flags |= (RSVD_FLAG_CENTER if centre else 0) | (RSVD_FLAG_KRYLOV if krylov else 0)
+    flags |= (RSVD_FLAG_SINGLE_PASS if single_pass else 0) | (RSVD_FLAG_SYMMETRIC if symmetric else 0)
     prm = make_params(k, p, q, seed, prec, flags)
     kk = ((k + p) * (q if krylov else 1)) if full else k
     dt = _prec_dtype(prec)

@@ -110,6 +110,32 @@ template <typename T, typename Q>
 void centre_adjoint(int m, int n, int l, const Q* Qm, int ldq, T* Z, int ldz, const CentreBufs& B, int sms,
                     cudaStream_t s);
 
+// singlepass.cu (Figs. singlepass_gen, singlepass_herm)
+struct SinglePassLayout {
+  DevStatus* st;
+  void *Gc, *Gr, *Yc, *Yr, *orthws;
+  double *Rc, *Rr;
+  void *Wt, *Jt;
+  double *sig, *sigs;
+  void *Wsel, *Jc, *Jr, *Qc, *Qr, *Pt, *Mt, *part;
+  double *Jd, *Rd, *P, *MT, *X1, *X2;
+  double* K[6];
+  double *s1, *s2;
+  void* orth64;
+  double *Rb64, *Wt64, *Jt64, *sig64, *part64;
+  void *Uh, *Vh;
+  __nv_bfloat16 *Ah, *Gcb, *Grb;
+  float* tcpart;
+  size_t bytes;
+};
+SinglePassLayout single_pass_layout(void* ws, int m, int n, int k, int l, size_t es, int sms, bool mixed);
+template <typename T>
+void run_single_pass_svd(int m, int n, const T* A, int lda, int k, int p, uint64_t seed, T* U, int ldu, double* D,
+                         T* V, int ldv, const SinglePassLayout& L, int sms, bool mixed, cudaStream_t s);
+template <typename T>
+void run_single_pass_evd(int n, const T* A, int lda, int k, int p, uint64_t seed, T* U, int ldu, double* D, T* V,
+                         int ldv, const SinglePassLayout& L, int sms, bool mixed, cudaStream_t s);
+
 // k_batched.cu
 int batched_max_rank();
 int batched_max_dim();

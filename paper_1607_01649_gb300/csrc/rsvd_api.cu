@@ -138,6 +138,16 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   if (l > mn) return fail(h, RSVD_E_INVALID, "basis width %d exceeds min(m, n) = %d", l, mn);
   if (l > max_l_for(p->prec))
     return fail(h, RSVD_E_UNSUPPORTED, "basis width %d exceeds the supported maximum %d", l, max_l_for(p->prec));
+  if (p->flags & RSVD_FLAG_SINGLE_PASS) {
+    if (p->q != 0) return fail(h, RSVD_E_INVALID, "single pass: q must be 0 (A is read once per sketch)");
+    if (p->k > 128) return fail(h, RSVD_E_UNSUPPORTED, "single pass: k must be <= 128 (binary64 fit)");
+    if (p->prec == RSVD_MIXED_FP8)
+      return fail(h, RSVD_E_UNSUPPORTED, "single pass runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
+    if (p->flags & (RSVD_FLAG_KRYLOV | RSVD_FLAG_CENTER | RSVD_FLAG_RETURN_FULL_L))
+      return fail(h, RSVD_E_INVALID, "single pass takes neither Krylov blocks, centring nor RETURN_FULL_L");
+    if ((p->flags & RSVD_FLAG_SYMMETRIC) && m != n)
+      return fail(h, RSVD_E_INVALID, "single-pass EVD: A must be square (m = %d, n = %d)", m, n);
+  }
   if (krylov && p->prec == RSVD_MIXED_FP8)
     return fail(h, RSVD_E_UNSUPPORTED, "block Krylov runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
   if (krylov && p->prec == RSVD_MIXED_BF16 && (l0 % 8) != 0)
@@ -1150,6 +1160,11 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
                                   (const void*)1, (const void*)1, 1 << 30, &kk);
   if (st != RSVD_OK) return st;
   int l = params->k + params->p;
+  if (params->flags & RSVD_FLAG_SINGLE_PASS) {
+    const size_t es = params->prec == RSVD_F64 ? 8 : 4;
+    *bytes = single_pass_layout(nullptr, m, n, params->k, l, es, handle->sms, params->prec == RSVD_MIXED_BF16).bytes;
+    return RSVD_OK;
+  }
   if (params->flags & RSVD_FLAG_KRYLOV) {
     const int l0 = l;
     l *= params->q;
@@ -1186,6 +1201,32 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
   if (!workspace || ws_bytes < need)
     return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
   if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  if (params->flags & RSVD_FLAG_SINGLE_PASS) {
+    const bool mixed = params->prec == RSVD_MIXED_BF16;
+    const size_t es = params->prec == RSVD_F64 ? 8 : 4;
+    if (mixed && ((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
+    const SinglePassLayout L = single_pass_layout(workspace, m, n, params->k, l, es, handle->sms, mixed);
+    cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
+    const bool sym = (params->flags & RSVD_FLAG_SYMMETRIC) != 0;
+    if (params->prec == RSVD_F64) {
+      if (sym)
+        run_single_pass_evd<double>(n, (const double*)A, lda, params->k, params->p, params->seed, (double*)U, ldu, D,
+                                    (double*)V, ldv, L, handle->sms, false, s);
+      else
+        run_single_pass_svd<double>(m, n, (const double*)A, lda, params->k, params->p, params->seed, (double*)U, ldu,
+                                    D, (double*)V, ldv, L, handle->sms, false, s);
+    } else {
+      if (sym)
+        run_single_pass_evd<float>(n, (const float*)A, lda, params->k, params->p, params->seed, (float*)U, ldu, D,
+                                   (float*)V, ldv, L, handle->sms, mixed, s);
+      else
+        run_single_pass_svd<float>(m, n, (const float*)A, lda, params->k, params->p, params->seed, (float*)U, ldu, D,
+                                   (float*)V, ldv, L, handle->sms, mixed, s);
+    }
+    st = check_launch(handle, "rsvd_fixed_rank (single pass)");
+    if (st != RSVD_OK) return st;
+    return finish_sync(handle, params, L.st, s);
+  }
   if (params->flags & RSVD_FLAG_KRYLOV) {
     const int w = l * params->q;
     const size_t es = params->prec == RSVD_F64 ? 8 : 4;

@@ -89,7 +89,8 @@ enum {
   RSVD_FLAG_CENTER = 32,        /* rsvd_fixed_rank: factor the column-centred A - 1 mu^T (PCA) */
   RSVD_FLAG_KRYLOV = 64,        /* rsvd_fixed_rank: block Krylov basis, q counts blocks */
   RSVD_FLAG_SINGLE_PASS = 128,  /* rsvd_fixed_rank: single-pass SVD (sketches only, fitted core) */
-  RSVD_FLAG_SYMMETRIC = 256     /* with RSVD_FLAG_SINGLE_PASS: single-pass EVD of a symmetric A */
+  RSVD_FLAG_SYMMETRIC = 256,    /* with RSVD_FLAG_SINGLE_PASS: single-pass EVD of a symmetric A */
+  RSVD_FLAG_SRFT = 512          /* rsvd_fixed_rank: SRFT test matrix; U, V complex */
 };
 
 typedef struct {
@@ -162,7 +163,18 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
  * eigenvalues ordered by decreasing magnitude (signed), U the eigenvectors
  * (largest-magnitude entry positive) and V a copy of U.  Precisions RSVD_F64,
  * RSVD_F32, RSVD_MIXED_BF16 (bf16 tensor-core sketches, the rest binary32
- * and binary64). */
+ * and binary64).
+ * RSVD_FLAG_SRFT (Sec. 6, eq. SRFT): Fig. RSVD (q must be 0) with Omega =
+ * D F S instead of a Gaussian: D = diag(e^{i theta_j}), theta_j = 2 pi
+ * (w >> 8) 2^-24 from word j mod 4 of Philox counter (j / 4, 0, 6, 0); F the
+ * unitary n-point DFT; S the l columns with the smallest 64-bit keys
+ * (w0 << 32 | w1 of counter (j, 0, 7, 0)), in key order.  For a real A the
+ * factors are complex: U (m x kk) and V (n x kk) are COMPLEX outputs, pairs
+ * (re, im) of A's element type, ldu and ldv counted in complex entries; D is
+ * real; each pair is phased so that the largest-magnitude entry of v_i is
+ * real and positive.  The complex steps run on the realification, so
+ * 2 (k + p) <= 256 (128 for RSVD_F64).  Precisions RSVD_F64, RSVD_F32,
+ * RSVD_MIXED_BF16. */
 rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, int lda,
                             const rsvd_params* params, void* U, int ldu, double* D, void* V,
                             int ldv, void* workspace, size_t ws_bytes, rsvd_stream_t stream);

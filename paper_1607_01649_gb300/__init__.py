@@ -43,6 +43,7 @@ RSVD_FLAG_CENTER = 32
 RSVD_FLAG_KRYLOV = 64
 RSVD_FLAG_SINGLE_PASS = 128
 RSVD_FLAG_SYMMETRIC = 256
+RSVD_FLAG_SRFT = 512
 
 STATUS_NAMES = {0: "RSVD_OK", 1: "RSVD_E_INVALID", 2: "RSVD_E_NOMEM", 3: "RSVD_E_CUDA", 4: "RSVD_E_BREAKDOWN",
                 5: "RSVD_E_NOT_CONVERGED", 6: "RSVD_E_NONFINITE", 7: "RSVD_E_TIMEOUT", 8: "RSVD_E_UNSUPPORTED"}
@@ -429,22 +430,27 @@ def _prec_dtype(prec):
 
 
 def fixed_rank(A, k, p=10, q=1, seed=0, prec=RSVD_F32, full=False, sync=True, ws=None, out=None, centre=False,
-               krylov=False, single_pass=False, symmetric=False):
+               krylov=False, single_pass=False, symmetric=False, srft=False):
     """A ~= U diag(D) V^T by rsvd_fixed_rank.  A: (m, n) row-major CUDA tensor
     (float64 for RSVD_F64, else float32).  centre=True factors the
     column-centred matrix without forming it (RSVD_FLAG_CENTER);
     krylov=True takes the block Krylov basis of q blocks (RSVD_FLAG_KRYLOV);
     single_pass=True is the single-pass SVD (q must be 0), with
-    symmetric=True the single-pass EVD (D signed, V = U).  Returns (U, D, V)."""
+    symmetric=True the single-pass EVD (D signed, V = U); srft=True takes
+    the SRFT test matrix (q must be 0; U and V come back complex).  Returns
+    (U, D, V)."""
     import torch
     h = handle(A.device.index)
     m, n = A.shape
     flags = (RSVD_FLAG_RETURN_FULL_L if full else 0) | (RSVD_FLAG_SYNC if sync else 0)
     flags |= (RSVD_FLAG_CENTER if centre else 0) | (RSVD_FLAG_KRYLOV if krylov else 0)
     flags |= (RSVD_FLAG_SINGLE_PASS if single_pass else 0) | (RSVD_FLAG_SYMMETRIC if symmetric else 0)
+    flags |= RSVD_FLAG_SRFT if srft else 0
     prm = make_params(k, p, q, seed, prec, flags)
     kk = ((k + p) * (q if krylov else 1)) if full else k
     dt = _prec_dtype(prec)
+    if srft:
+        dt = torch.complex128 if prec == RSVD_F64 else torch.complex64
     if out is None:
         U = torch.empty(m, kk, dtype=dt, device=A.device)
         D = torch.empty(kk, dtype=torch.float64, device=A.device)

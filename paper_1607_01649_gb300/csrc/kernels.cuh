@@ -136,6 +136,26 @@ template <typename T>
 void run_single_pass_evd(int n, const T* A, int lda, int k, int p, uint64_t seed, T* U, int ldu, double* D, T* V,
                          int ldv, const SinglePassLayout& L, int sms, bool mixed, cudaStream_t s);
 
+// srft.cu (eq. SRFT: Fig. RSVD with Omega = D F S, on the realification)
+struct SrftLayout {
+  DevStatus* st;
+  unsigned long long* key;
+  int* S;
+  void *Om, *Y2, *Yh, *Z, *orthws;
+  double* Rb;
+  void *Wt, *Jt;
+  double *sig, *Dall;
+  void *Wsel, *Jsel, *W2, *J2, *Uh, *Vh, *Xi, *part;
+  __nv_bfloat16 *Ah, *Al, *Omb, *Qh, *Ql;
+  float* tcpart;
+  size_t bytes;
+};
+SrftLayout srft_layout(void* ws, int m, int n, int l, int kk, size_t es, int sms, bool mixed);
+// U, V: complex outputs, interleaved (re, im), leading dimensions in complex entries
+template <typename T>
+cudaError_t run_srft(int m, int n, const T* A, int lda, int k, int p, int kk, uint64_t seed, T* U, int ldu, double* D,
+                     T* V, int ldv, const SrftLayout& L, int sms, bool mixed, cudaStream_t s);
+
 // k_batched.cu
 int batched_max_rank();
 int batched_max_dim();

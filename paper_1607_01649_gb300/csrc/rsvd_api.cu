@@ -148,6 +148,16 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
     if ((p->flags & RSVD_FLAG_SYMMETRIC) && m != n)
       return fail(h, RSVD_E_INVALID, "single-pass EVD: A must be square (m = %d, n = %d)", m, n);
   }
+  if (p->flags & RSVD_FLAG_SRFT) {
+    if (p->q != 0) return fail(h, RSVD_E_INVALID, "SRFT sketch: q must be 0 (Fig. RSVD)");
+    if (p->prec == RSVD_MIXED_FP8)
+      return fail(h, RSVD_E_UNSUPPORTED, "SRFT runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
+    if (p->flags & (RSVD_FLAG_KRYLOV | RSVD_FLAG_CENTER | RSVD_FLAG_SINGLE_PASS))
+      return fail(h, RSVD_E_INVALID, "SRFT takes neither Krylov blocks, centring nor the single-pass fit");
+    if (2 * l0 > max_l_for(p->prec))
+      return fail(h, RSVD_E_UNSUPPORTED, "SRFT: the realified basis 2 (k + p) = %d exceeds %d", 2 * l0,
+                  max_l_for(p->prec));
+  }
   if (krylov && p->prec == RSVD_MIXED_FP8)
     return fail(h, RSVD_E_UNSUPPORTED, "block Krylov runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
   if (krylov && p->prec == RSVD_MIXED_BF16 && (l0 % 8) != 0)
@@ -1160,6 +1170,11 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
                                   (const void*)1, (const void*)1, 1 << 30, &kk);
   if (st != RSVD_OK) return st;
   int l = params->k + params->p;
+  if (params->flags & RSVD_FLAG_SRFT) {
+    const size_t es = params->prec == RSVD_F64 ? 8 : 4;
+    *bytes = srft_layout(nullptr, m, n, l, kk, es, handle->sms, params->prec == RSVD_MIXED_BF16).bytes;
+    return RSVD_OK;
+  }
   if (params->flags & RSVD_FLAG_SINGLE_PASS) {
     const size_t es = params->prec == RSVD_F64 ? 8 : 4;
     *bytes = single_pass_layout(nullptr, m, n, params->k, l, es, handle->sms, params->prec == RSVD_MIXED_BF16).bytes;
@@ -1201,6 +1216,24 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
   if (!workspace || ws_bytes < need)
     return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
   if (((uintptr_t)workspace & 255) != 0) return fail(handle, RSVD_E_INVALID, "workspace not 256-byte aligned");
+  if (params->flags & RSVD_FLAG_SRFT) {
+    const bool mixed = params->prec == RSVD_MIXED_BF16;
+    const size_t es = params->prec == RSVD_F64 ? 8 : 4;
+    if (mixed && ((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
+    const SrftLayout L = srft_layout(workspace, m, n, l, kk, es, handle->sms, mixed);
+    cudaMemsetAsync(L.st, 0, sizeof(DevStatus), s);
+    cudaError_t e;
+    if (params->prec == RSVD_F64)
+      e = run_srft<double>(m, n, (const double*)A, lda, params->k, params->p, kk, params->seed, (double*)U, ldu, D,
+                           (double*)V, ldv, L, handle->sms, false, s);
+    else
+      e = run_srft<float>(m, n, (const float*)A, lda, params->k, params->p, kk, params->seed, (float*)U, ldu, D,
+                          (float*)V, ldv, L, handle->sms, mixed, s);
+    if (e != cudaSuccess) return fail(handle, RSVD_E_CUDA, "SRFT solve: %s", cudaGetErrorString(e));
+    st = check_launch(handle, "rsvd_fixed_rank (SRFT)");
+    if (st != RSVD_OK) return st;
+    return finish_sync(handle, params, L.st, s);
+  }
   if (params->flags & RSVD_FLAG_SINGLE_PASS) {
     const bool mixed = params->prec == RSVD_MIXED_BF16;
     const size_t es = params->prec == RSVD_F64 ? 8 : 4;

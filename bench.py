@@ -71,7 +71,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--sample", type=int, default=None, help="CPU oracle sample size (rows; square for poly)")
-    a = ap.parse_args()
+    ap.add_argument("--cpu-sample", action="store_true",
+                    help="poly: time the oracle on a sample scaled by m n instead of one full-size solve")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the sub-records (PCA, batched and the method variants) of the default run")
+    return apply_defaults(ap.parse_args())
+
+
+def apply_defaults(a):
     dflt = {"poly": dict(prec="bf16", m=32768, n=32768, k=200, p=56, q=2, seed=2001, sample=8192),
             "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768),
             "controller": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=60000, sample=0),
@@ -309,14 +316,46 @@ def run_reference(a):
     value = a.steps / dt / scale
     sample = ("float64 oracle rsvd_power on a %dx%d matrix of the same family (k=%d p=%d q=%d) per step, "
               "time scaled by the m*n ratio %.1f" % (sm_, sn_, a.k, a.p, a.q, scale))
+    # ms_per_step is the wall time of one step as run (one sample solve); the
+    # value is that rate scaled to the full-size workload by the m n ratio
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * dt / a.steps * scale,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 * dt / a.steps,
+            "ms_per_full_size_solve": 1000.0 * dt / a.steps * scale,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a)},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def peaks():
+    """HBM GB/s and bf16 TFLOP/s (burst, sustained): MEASURED_PEAKS.json, else
+    the profiling recipe's fallback figures."""
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return (float(pk["hbm_gbs"]), float(pk["bf16_tflops"]), float(pk.get("bf16_tflops_sustained", pk["bf16_tflops"])),
+                "measured")
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def solve_roofline(m, n, l, q, passes, bytes_per_entry, ms_per_step, fp8=False):
+    """The per-solve floor of the method: the slower of its sketch flops at the
+    tensor-core peak (sustained: the solve is timed inside a long loop; e4m3
+    at twice the bf16 rate) and its passes over A at the HBM copy bandwidth,
+    divided by the measured time per solve; beside it the compulsory floor
+    (A read once in its given fp32 form)."""
+    hbm, _, tc_s, src = peaks()
+    tc = tc_s * (2.0 if fp8 else 1.0)
+    flops = passes * 2.0 * m * n * l
+    t_flop = flops / (tc * 1e12) * 1e3
+    t_bytes = passes * bytes_per_entry * m * n / (hbm * 1e9) * 1e3
+    floor = max(t_flop, t_bytes)
+    t_comp = 4.0 * m * n / (hbm * 1e9) * 1e3
+    return {"floor_ms": floor, "frac": floor / ms_per_step, "bound": "hbm" if t_bytes >= t_flop else "tensor",
+            "passes_over_A": passes, "bytes_per_entry": bytes_per_entry, "sketch_flops": flops,
+            "compulsory_floor_ms": t_comp, "compulsory_frac": t_comp / ms_per_step, "peak_source": src}
 
 
 # ------------------------------------------------------------------- ours --
@@ -489,8 +528,28 @@ def run_ours(a):
                 "algorithmic_bytes": alg_bytes, "kernel": kname,
                 "launches": sk_n, "avg_ms": per_launch_ms, "peak_source": peak_src,
                 "projection_split3_avg_ms": (pj_ms / pj_n) if pj_n else None}
+        # the whole solve against the method's floor: 2q + 2 passes over A
+        # (q + 1 products A X, q products A^T X, the projection) at the
+        # sketch's bytes per entry
+        sr = solve_roofline(m, n, l, q, 2 * q + 2, eb, ms_per_step, fp8=(prec == rs.RSVD_MIXED_FP8))
+        roof["solve_frac"] = sr["frac"]
+        roof["solve"] = sr
+        # and against this design's own bytes: the conversion pass (fp32 A read,
+        # the bf16 pair written; e4m3 also writes A8 and its byte transpose),
+        # the 2q + 1 sketch passes and the split-bf16 projection (Ah + Al)
+        conv = (8.0 if prec == rs.RSVD_MIXED_BF16 else 11.0) * m * n
+        design_bytes = conv + (2 * q + 1) * eb * m * n + 4.0 * m * n
+        roof["solve_design_floor_ms"] = design_bytes / (hbm * 1e9) * 1e3
+        roof["solve_design_frac"] = roof["solve_design_floor_ms"] / ms_per_step
     elif prec == rs.RSVD_F32:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
+
+    variants = None
+    if not a.no_extra and world == 1:
+        if a.workload == "poly":
+            variants = poly_variants(a, rs, h, A, dev, stream, fro_rel)
+        elif a.workload == "pca":
+            variants = {"centring": pca_centring(a, rs, h, A, dev, stream, D)}
 
     # ---- e2e: the C-ABI call with HOST buffers (pinned).  The mixed paths read
     # A exactly once, in the conversion pass, so A is passed as the host
@@ -559,11 +618,14 @@ def run_ours(a):
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
-        return
+        return None
     cpu = None
     if not a.no_cpu:
-        v, detail, t, nsol = oracle_sample(a, device=dev)
-        cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": detail}
+        if a.workload == "poly" and not a.cpu_sample:
+            cpu = oracle_full(a, A, a.seed + 100 + a.steps - 1, D, res_rel, fro_rel, dev)
+        else:
+            v, detail, t, nsol = oracle_sample(a, device=dev)
+            cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": detail}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {rs.RSVD_MIXED_BF16: "bf16", rs.RSVD_MIXED_FP8: "e4m3"}.get(prec, "f32"),
@@ -576,9 +638,186 @@ def run_ours(a):
             "diagnostics": {"jacobi_sweeps_last_solve": diag["jacobi_sweeps"],
                             "shifted_cholesky_last_solve": diag["shift_count"],
                             "sketch_launches_timed": sk_n, "projection_launches_timed": pj_n}}
-    print(json.dumps(line))
+    if variants is not None:
+        line["variants"] = variants
     if dist is not None:
         dist.destroy_process_group()
+    return line
+
+
+def oracle_full(a, A, seed, D_gpu, res_gpu, fro_rel, dev):
+    """One full-size float64 oracle solve (oracle.rsvd_power, Fig.
+    RSVDP_stabilized) on the host cores, on the same binary32 A (promoted to
+    float64) and the same Omega seed as the last timed GPU solve; its own
+    error beside the GPU's."""
+    import numpy as np
+    import torch
+    import oracle
+    A64 = A.double().cpu().numpy()
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    ref = oracle.rsvd_power(A64, a.k, a.p, a.q, seed)
+    t = time.perf_counter() - t0
+    del A64
+    Ur = torch.from_numpy(ref["U"]).to(dev)
+    Vr = torch.from_numpy(ref["V"]).to(dev)
+    Dr = torch.from_numpy(ref["D"]).to(dev)
+    res_ref, _ = fro_rel(Ur, Dr, Vr)
+    sig = torch.arange(1, a.k + 1, dtype=torch.float64, device=dev).pow(-1.5)
+    d_ref = float(((Dr - sig).abs() / sig).max())
+    gpu_vs = float(((D_gpu.double() - Dr).abs() / Dr).max())
+    return {"value": 1.0 / t, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": "one full-size float64 oracle solve (rsvd_power, %dx%d, k=%d p=%d q=%d) on the same A and "
+                      "Omega seed as the last timed GPU solve: %.1f s" % (a.m, a.n, a.k, a.p, a.q, t),
+            "oracle_error": {"fro_residual_rel": res_ref, "max_rel_err_sigma_1..k_vs_construction": d_ref},
+            "gpu_error_vs_oracle": {"fro_residual_ratio": res_gpu / res_ref, "max_rel_diff_sigma_1..k": gpu_vs}}
+
+
+def _timed(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def poly_variants(a, rs, h, A, dev, stream, fro_rel):
+    """The method variants of the paper on the same poly-decay matrix (bf16
+    tensor-core sketches, one rsvd_fixed_rank call per solve, 5 timed), each
+    with its passes over A, its solve roofline fraction and its Frobenius
+    residual against the Eckart-Young optimum at its rank k:
+    * power_q1_l256 / power_q2_l256: Fig. RSVDP_stabilized, k = 120;
+    * krylov_2x128: the extended sampling matrix, 2 blocks of 128 columns
+      (the same 4 passes as q = 1 at width 256);
+    * basic_q0_l128: Fig. RSVD, k = 120, p = 8 (2 passes);
+    * single_pass_l128: Fig. singlepass_gen, k = 120, p = 8 (the two
+      sketches as separate launches: 2 reads of A);
+    * srft_l128: Fig. RSVD with the SRFT test matrix, k = 100, p = 28
+      (complex factors);
+    * adaptive_spectral_4096: rsvd_adaptive_tol in its spectral mode on a
+      4096^2 exp(-j/20)-decay matrix (binary32; a j^-1.5 tail keeps the
+      Frobenius norm of the remainder, which the probes see, far above a
+      spectral eps at any rank under 256), eps = 1e-3 ||A||_2, beside the
+      Frobenius mode at the tolerance that gives the same spectral error."""
+    import torch
+    m, n = a.m, a.n
+    out = {}
+    fro_a2 = float(torch.arange(1, min(m, n) + 1, dtype=torch.float64).pow(-3.0).sum())
+
+    def opt_rel(k):
+        return float(torch.arange(k + 1, min(m, n) + 1, dtype=torch.float64).pow(-3.0).sum().sqrt()) / fro_a2 ** 0.5
+
+    cases = [("power_q1_l256", dict(k=120, p=136, q=1), 4, 256),
+             ("power_q2_l256", dict(k=120, p=136, q=2), 6, 256),
+             ("krylov_2x128", dict(k=120, p=8, q=2, krylov=True), 4, 256),
+             ("basic_q0_l128", dict(k=120, p=8, q=0), 2, 128),
+             ("single_pass_l128", dict(k=120, p=8, q=0, single_pass=True), 2, 128),
+             ("srft_l128", dict(k=100, p=28, q=0, srft=True), 2, 256)]
+    for name, kw, passes, width in cases:
+        try:
+            kw = dict(kw)
+            k = kw.pop("k")
+            p_ = kw.pop("p")
+            q_ = kw.pop("q")
+            flags = ((rs.RSVD_FLAG_KRYLOV if kw.get("krylov") else 0) |
+                     (rs.RSVD_FLAG_SINGLE_PASS if kw.get("single_pass") else 0) |
+                     (rs.RSVD_FLAG_SRFT if kw.get("srft") else 0))
+            prm = rs.make_params(k, p_, q_, seed=a.seed, prec=rs.RSVD_MIXED_BF16, flags=flags)
+            ws = torch.empty(rs.rsvd_workspace_size(h, m, n, prm), dtype=torch.uint8, device=dev)
+            dt = torch.complex64 if kw.get("srft") else torch.float32
+            U = torch.empty(m, k, dtype=dt, device=dev)
+            D = torch.empty(k, dtype=torch.float64, device=dev)
+            V = torch.empty(n, k, dtype=dt, device=dev)
+
+            def solve():
+                code = rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm, U, k, D, V, k, ws)
+                if code != rs.RSVD_OK:
+                    raise rs.RsvdError(code, rs.last_error(h))
+
+            ms = _timed(solve, 5, stream)
+            if kw.get("srft"):
+                f2, a2 = 0.0, 0.0
+                Ud = U.to(torch.complex128) * D[None, :]
+                for r0 in range(0, m, 4096):
+                    Ab = A[r0:r0 + 4096].double()
+                    R = Ab - (Ud[r0:r0 + 4096] @ V.to(torch.complex128).conj().T).real
+                    f2 += float((R * R).sum())
+                    a2 += float((Ab * Ab).sum())
+                res = (f2 / a2) ** 0.5
+            else:
+                res = fro_rel(U, D, V)[0]
+            sr = solve_roofline(m, n, width, 0, passes, 2.0, ms)
+            out[name] = {"value": 1000.0 / ms, "unit": "solves/s", "ms": ms, "k": k, "basis_width": width,
+                         "passes_over_A": passes, "solve_frac": sr["frac"], "fro_residual_rel": res,
+                         "fro_optimal_rel": opt_rel(k), "ratio_to_optimal": res / opt_rel(k)}
+            del ws, U, D, V
+            torch.cuda.empty_cache()
+        except Exception as exc:  # a variant that fails is reported, not fatal
+            out[name] = {"error": str(exc)[:200]}
+    try:
+        from workloads import exp_decay_matrix_torch
+        As = exp_decay_matrix_torch(4096, 4096, seed=a.seed + 7, rate=20.0, device=dev)
+        eps = 1e-3 * float(torch.exp(torch.tensor(-1.0 / 20.0)))  # 1e-3 sigma_1
+        res = {}
+
+        def solve_spec():
+            res["r"] = rs.adaptive_tol(As, eps, block=16, seed=a.seed, prec=rs.RSVD_F32, spectral=True)
+
+        ms = _timed(solve_spec, 3, stream)
+        U, D, V, rank, bound, code = res["r"]
+        Ud = U[:, :rank].double() * D[:rank][None, :]
+        E = As.double() - Ud @ V[:, :rank].double().T
+        true2 = float(torch.linalg.matrix_norm(E, 2))
+        out["adaptive_spectral_4096"] = {"value": 1000.0 / ms, "unit": "solves/s", "ms": ms, "eps": eps,
+                                         "rank": rank, "status": code, "reported_bound": bound,
+                                         "true_spectral_error": true2,
+                                         "sigma_rank+1": float(torch.exp(torch.tensor(-(rank + 1) / 20.0)))}
+        del As, E
+        torch.cuda.empty_cache()
+    except Exception as exc:
+        out["adaptive_spectral_4096"] = {"error": str(exc)[:200]}
+    return out
+
+
+def pca_centring(a, rs, h, A, dev, stream, D_centred):
+    """PCA as it arrives: the same matrix with column offsets added (entry
+    scale), factored with implicit centring (RSVD_FLAG_CENTER) in the
+    benchmark's precision; its singular values against those of the solve on
+    the explicitly centred matrix, and the time beside it."""
+    import torch
+    from workloads import column_offsets
+    m, n, k, p, q = a.m, a.n, a.k, a.p, a.q
+    prec = {"bf16": rs.RSVD_MIXED_BF16, "fp8": rs.RSVD_MIXED_FP8, "f32": rs.RSVD_F32}[a.prec]
+    scale = float(A[:4096].double().pow(2).mean().sqrt())
+    mu = column_offsets(n, a.seed + 11, 2.0 * scale, device=dev)
+    A.add_(mu[None, :])
+    try:
+        prm = rs.make_params(k, p, q, seed=a.seed + 100 + a.steps - 1, prec=prec, flags=rs.RSVD_FLAG_CENTER)
+        ws = torch.empty(rs.rsvd_workspace_size(h, m, n, prm), dtype=torch.uint8, device=dev)
+        U = torch.empty(m, k, dtype=torch.float32, device=dev)
+        D = torch.empty(k, dtype=torch.float64, device=dev)
+        V = torch.empty(n, k, dtype=torch.float32, device=dev)
+
+        def solve():
+            code = rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm, U, k, D, V, k, ws)
+            if code != rs.RSVD_OK:
+                raise rs.RsvdError(code, rs.last_error(h))
+
+        ms = _timed(solve, 5, stream)
+        nk = min(k, 48)
+        diff = float(((D[:nk] - D_centred[:nk]).abs() / D_centred[:nk]).max())
+        one_u = float(U.double().sum(dim=0).abs().max() / m ** 0.5)
+        del ws, U, V
+        return {"value": 1000.0 / ms, "unit": "solves/s", "ms": ms, "offset_scale": 2.0 * scale,
+                "max_rel_diff_sigma_1..48_vs_explicitly_centred": diff, "max_abs_1^T_u_over_sqrt_m": one_u}
+    finally:
+        A.sub_(mu[None, :])
 
 
 # ------------------------------------------------------- controller stream --
@@ -1096,7 +1335,7 @@ def run_batched(a):
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
-        return
+        return None
     cpu = None
     if not a.no_cpu:
         done, t_run, mn_s = batched_oracle_sample(a, 12.0)
@@ -1117,9 +1356,9 @@ def run_batched(a):
                       "blocks_converged": int(np.sum(status == 0)), "mean_rank": float(ranks.mean()),
                       "max_rank": int(ranks.max())},
             "plain_f32": f32}
-    print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+    return line
 
 
 def run_reference_batched(a):
@@ -1147,10 +1386,36 @@ def run_reference_batched(a):
     print(json.dumps(line))
 
 
+def sub_args(a, workload, steps=5, warmup=2):
+    """Arguments of a sub-record of the default run: the workload's own
+    defaults, a few steps, no CPU oracle, no e2e, no comparators."""
+    import argparse as _ap
+    b = _ap.Namespace(**vars(a))
+    b.workload = workload
+    for key in ("prec", "m", "n", "k", "p", "q", "seed", "sample"):
+        setattr(b, key, None)
+    b = apply_defaults(b)
+    b.steps, b.warmup = steps, warmup
+    b.no_cpu = b.no_e2e = b.no_f32 = True
+    return b
+
+
+def compact(line):
+    """The figures of a sub-record's line that the default run carries."""
+    keep = ("value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "error", "clocks",
+            "gpu_launches", "variants")
+    return {k: line[k] for k in keep if k in line}
+
+
 def main():
     a = parse()
     if a.workload == "batched":
-        (run_reference_batched if a.impl == "reference" else run_batched)(a)
+        if a.impl == "reference":
+            run_reference_batched(a)
+        else:
+            line = run_batched(a)
+            if line is not None:
+                print(json.dumps(line))
     elif a.workload == "nystrom":
         (run_reference_nystrom if a.impl == "reference" else run_nystrom)(a)
     elif a.workload == "controller":
@@ -1158,7 +1423,24 @@ def main():
     elif a.impl == "reference":
         run_reference(a)
     else:
-        run_ours(a)
+        line = run_ours(a)
+        if line is None:
+            return
+        if a.workload == "poly" and not a.no_extra and line["n_gpus"] == 1:
+            # the other configurations, measured in the same run: the PCA
+            # matrix with e4m3 sketches (and implicit centring of the same
+            # matrix with column offsets), the batched kernel blocks
+            import torch
+            extra = {}
+            for wl, fn in (("pca", run_ours), ("batched", run_batched)):
+                torch.cuda.empty_cache()
+                try:
+                    sub = fn(sub_args(a, wl))
+                    extra[wl] = compact(sub) if sub is not None else None
+                except Exception as exc:
+                    extra[wl] = {"error": str(exc)[:300]}
+            line["extra"] = extra
+        print(json.dumps(line))
 
 
 if __name__ == "__main__":

@@ -143,6 +143,27 @@ def poly_decay_matrix(m=32768, n=32768, seed=2001, alpha=1.5, device="cuda"):
     return A.contiguous()
 
 
+def exp_decay_matrix_torch(m, n, seed, rate=20.0, device="cuda"):
+    """A = U diag(exp(-j / rate)) V^T, float32, Haar U, V (QR of seeded torch
+    Gaussians, sign-fixed), synthesized on `device` without TF32."""
+    torch = _torch()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    r = min(m, n)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        U = haar_torch(m, r, gen, device, torch.float32)
+        s = torch.exp(-torch.arange(1, r + 1, device=device, dtype=torch.float64) / rate).to(torch.float32)
+        U.mul_(s[None, :])
+        V = haar_torch(n, r, gen, device, torch.float32)
+        A = U @ V.T
+        del U, V
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return A.contiguous()
+
+
 def spd_matrix(n=16384, seed=5001, alpha=1.5, device="cuda"):
     """Symmetric positive definite A = V diag(j^-alpha) V^T, float32, Haar V,
     synthesized on `device` (products in float32 without TF32), then made
@@ -183,6 +204,16 @@ def pca_matrix(m=1 << 20, n=4096, seed=3001, rank=64, noise=1e-3, device="cuda")
     mean = A.sum(dim=0, dtype=torch.float64) / m
     A.sub_(mean.to(torch.float32)[None, :])
     return A
+
+
+def column_offsets(n, seed, scale, device="cuda"):
+    """Seeded column offsets mu_j ~ N(0, scale^2) (float32, length n) to add to
+    a centred matrix, so that a solver's implicit centring has means to
+    remove (PCA data is not centred when it arrives)."""
+    torch = _torch()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    return scale * torch.randn(n, generator=gen, device=device, dtype=torch.float32)
 
 
 # ------------------------------------------------------- kernel blocks ------

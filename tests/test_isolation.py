@@ -71,7 +71,7 @@ def test_generators_import_neither_side():
 
 def test_oracle_only_in_cpu_legs_and_smoke():
     allowed = {
-        "bench.py": {"oracle_sample", "run_reference", "controller_oracle_solve", "nystrom_oracle_solve",
+        "bench.py": {"oracle_sample", "oracle_full", "run_reference", "controller_oracle_solve", "nystrom_oracle_solve",
                      "batched_oracle_sample"},
         "__graft_entry__.py": {"smoke"},
     }

@@ -212,33 +212,52 @@ __global__ void __launch_bounds__(512)
           }
           C* xa = (ia < w ? top + (size_t)ia * cs : bot + (size_t)(ia - w) * cs);
           C* xb = (ib < w ? top + (size_t)ib * cs : bot + (size_t)(ib - w) * cs);
-          V* va = reinterpret_cast<V*>(xa);
-          V* vb = reinterpret_cast<V*>(xb);
-          V* ja = reinterpret_cast<V*>(xa + (size_t)w * cs);
-          V* jb = reinterpret_cast<V*>(xb + (size_t)w * cs);
-          C ga = C(0);
-          for (int v = 0; v < nv; ++v) ga = JVec<C>::dot(va[v * 32 + lane], vb[v * 32 + lane], ga);
+          V* va = reinterpret_cast<V*>(xa) + lane;
+          V* vb = reinterpret_cast<V*>(xb) + lane;
+          V* ja = reinterpret_cast<V*>(xa + (size_t)w * cs) + lane;
+          V* jb = reinterpret_cast<V*>(xb + (size_t)w * cs) + lane;
+          // the pair's X and J entries of this lane, loaded once (at most two
+          // 16-byte vectors per column: l <= 256 in binary32, 128 in binary64);
+          // the J loads and the carried norms are in flight during the dot product
+          V a[2], b[2], pa[2], pb[2];
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+            if (v < nv) {
+              a[v] = va[32 * v];
+              b[v] = vb[32 * v];
+            }
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+            if (v < nv) {
+              pa[v] = ja[32 * v];
+              pb[v] = jb[32 * v];
+            }
+          const C al = xa[lp], be = xb[lp];
+          // two independent accumulation chains
+          C g0 = C(0), g1 = C(0);
+          g0 = JVec<C>::dot(a[0], b[0], g0);
+          if (nv > 1) g1 = JVec<C>::dot(a[1], b[1], g1);
+          C ga = g0 + g1;
           // xor butterflies leave the identical sum in every lane, so the
           // rotation decision below is warp-uniform without a broadcast
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-          const C al = xa[lp], be = xb[lp];
           if (al > C(0) && be > C(0) && ga * ga > tol2 * al * be) {
             // Rutishauser's formulas: zeta = (beta - alpha) / (2 gamma),
             // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t
             C t, c;
             jac_rotation<C>(al, be, ga, t, c);
-            const C s = c * t;
-            for (int v = 0; v < nv; ++v) {
-              V a = va[v * 32 + lane], b = vb[v * 32 + lane];
-              JVec<C>::rot(a, b, c, s);
-              va[v * 32 + lane] = a;
-              vb[v * 32 + lane] = b;
-              V p = ja[v * 32 + lane], q = jb[v * 32 + lane];
-              JVec<C>::rot(p, q, c, s);
-              ja[v * 32 + lane] = p;
-              jb[v * 32 + lane] = q;
-            }
+            const C sn = c * t;
+#pragma unroll
+            for (int v = 0; v < 2; ++v)
+              if (v < nv) {
+                JVec<C>::rot(a[v], b[v], c, sn);
+                JVec<C>::rot(pa[v], pb[v], c, sn);
+                va[32 * v] = a[v];
+                vb[32 * v] = b[v];
+                ja[32 * v] = pa[v];
+                jb[32 * v] = pb[v];
+              }
             __syncwarp();
             if (lane == 0) {
               xa[lp] = al - t * ga;
@@ -358,6 +377,10 @@ size_t jacobi_smem_bytes(int l, size_t csize) {
 
 template <typename C>
 cudaError_t launch_jacobi(int l, const double* Rb, C* Wt, C* Jt, double* sigma, DevStatus* st, cudaStream_t s) {
+  // the kernel keeps a lane's share of a column pair in registers: at most two
+  // 16-byte vectors per column (l <= 256 in binary32, l <= 128 in binary64)
+  const int vw = (int)(16 / sizeof(C));
+  if (l < 1 || jac_lp(l, vw) / (32 * vw) > 2) return cudaErrorInvalidValue;
   const int nc = jacobi_cluster_size(l);
   const int w = (l + 2 * nc - 1) / (2 * nc);
   const size_t smem = jacobi_smem_bytes(l, sizeof(C));

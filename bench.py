@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--train", type=int, default=192, help="controller: training matrices")
     ap.add_argument("--lo", type=int, default=512, help="controller: smallest n")
     ap.add_argument("--hi", type=int, default=16384, help="controller: largest n")
-    ap.add_argument("--prec", default=None, choices=["bf16", "f32", "fp8"])
+    ap.add_argument("--prec", default=None, choices=["bf16", "f32", "fp8", "fp8b"],
+                    help="fp8: e4m3 with a scale per row; fp8b: one scale per 128-row block")
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--k", type=int, default=None)
@@ -80,7 +81,7 @@ def parse():
 
 def apply_defaults(a):
     dflt = {"poly": dict(prec="bf16", m=32768, n=32768, k=200, p=56, q=2, seed=2001, sample=8192),
-            "pca": dict(prec="fp8", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768),
+            "pca": dict(prec="fp8b", m=1 << 20, n=4096, k=64, p=64, q=1, seed=3001, sample=32768),
             "controller": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=60000, sample=0),
             "batched": dict(prec="f32", m=0, n=0, k=0, p=0, q=0, seed=4001, sample=0),
             "nystrom": dict(prec="f32", m=16384, n=16384, k=200, p=56, q=0, seed=5001, sample=4096)}[a.workload]
@@ -380,7 +381,9 @@ def run_ours(a):
 
     m, n, k, p, q = a.m, a.n, a.k, a.p, a.q
     l = k + p
-    prec = {"bf16": rs.RSVD_MIXED_BF16, "fp8": rs.RSVD_MIXED_FP8, "f32": rs.RSVD_F32}[a.prec]
+    prec = {"bf16": rs.RSVD_MIXED_BF16, "fp8": rs.RSVD_MIXED_FP8, "fp8b": rs.RSVD_MIXED_FP8_B128,
+            "f32": rs.RSVD_F32}[a.prec]
+    fp8 = prec in (rs.RSVD_MIXED_FP8, rs.RSVD_MIXED_FP8_B128)
     A = make_workload(a, m, n, a.seed + rank, dev)
     h = rs.handle(local)
     prm = rs.make_params(k, p, q, seed=a.seed, prec=prec, flags=0)
@@ -510,7 +513,7 @@ def run_ours(a):
         peak_src = "measured"
     except Exception:
         hbm, peak_src = 6800.0, "fallback"
-    if prec in (rs.RSVD_MIXED_BF16, rs.RSVD_MIXED_FP8) and sk_n > 0:
+    if (prec == rs.RSVD_MIXED_BF16 or fp8) and sk_n > 0:
         per_launch_ms = sk_ms / sk_n
         # algorithmic bytes of the sketch products of one solve: A once per
         # product (bf16: 2 bytes, e4m3: 1 byte per entry), the thin operand in the
@@ -531,7 +534,7 @@ def run_ours(a):
         # the whole solve against the method's floor: 2q + 2 passes over A
         # (q + 1 products A X, q products A^T X, the projection) at the
         # sketch's bytes per entry
-        sr = solve_roofline(m, n, l, q, 2 * q + 2, eb, ms_per_step, fp8=(prec == rs.RSVD_MIXED_FP8))
+        sr = solve_roofline(m, n, l, q, 2 * q + 2, eb, ms_per_step, fp8=fp8)
         roof["solve_frac"] = sr["frac"]
         roof["solve"] = sr
         # and against this design's own bytes: the conversion pass (fp32 A read,
@@ -563,7 +566,7 @@ def run_ours(a):
         Uh = torch.empty(m, k, dtype=torch.float32, pin_memory=True)
         Dh = torch.empty(k, dtype=torch.float64, pin_memory=True)
         Vh = torch.empty(n, k, dtype=torch.float32, pin_memory=True)
-        zero_copy = prec in (rs.RSVD_MIXED_BF16, rs.RSVD_MIXED_FP8)
+        zero_copy = prec == rs.RSVD_MIXED_BF16 or fp8
         steps_e2e = max(1, min(a.steps, 5))
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -613,7 +616,7 @@ def run_ours(a):
         return out
 
     f32 = comparator(rs.RSVD_F32) if (prec != rs.RSVD_F32 and not a.no_f32) else None
-    bf16 = comparator(rs.RSVD_MIXED_BF16) if (prec == rs.RSVD_MIXED_FP8 and not a.no_f32) else None
+    bf16 = comparator(rs.RSVD_MIXED_BF16) if (fp8 and not a.no_f32) else None
 
     if rank != 0:
         if dist is not None:
@@ -628,7 +631,7 @@ def run_ours(a):
             cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": detail}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {rs.RSVD_MIXED_BF16: "bf16", rs.RSVD_MIXED_FP8: "e4m3"}.get(prec, "f32"),
+            "vs_baseline": None, "dtype": "e4m3" if fp8 else ("bf16" if prec == rs.RSVD_MIXED_BF16 else "f32"),
             "data": "synthetic",
             "config": {"workload": workload_name(a), "precision": a.prec,
                        "l2": "inputs larger than L2 (A is %.2f GB; L2 129 MB)" % (m * n * 4 / 1e9),
@@ -793,7 +796,9 @@ def pca_centring(a, rs, h, A, dev, stream, D_centred):
     import torch
     from workloads import column_offsets
     m, n, k, p, q = a.m, a.n, a.k, a.p, a.q
-    prec = {"bf16": rs.RSVD_MIXED_BF16, "fp8": rs.RSVD_MIXED_FP8, "f32": rs.RSVD_F32}[a.prec]
+    prec = {"bf16": rs.RSVD_MIXED_BF16, "fp8": rs.RSVD_MIXED_FP8, "fp8b": rs.RSVD_MIXED_FP8_B128,
+            "f32": rs.RSVD_F32}[a.prec]
+    fp8 = prec in (rs.RSVD_MIXED_FP8, rs.RSVD_MIXED_FP8_B128)
     scale = float(A[:4096].double().pow(2).mean().sqrt())
     mu = column_offsets(n, a.seed + 11, 2.0 * scale, device=dev)
     A.add_(mu[None, :])

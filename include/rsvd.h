@@ -70,11 +70,15 @@ typedef enum {
                           cores with bf16 operands and fp32 accumulation; the
                           final B = Q^T A as a three-term split-bf16 product;
                           Gram matrices accumulated in binary64 */
-  RSVD_MIXED_FP8 = 3   /* A, U, V float; A*Omega, A^T Q, A W on tcgen05 tensor
+  RSVD_MIXED_FP8 = 3,  /* A, U, V float; A*Omega, A^T Q, A W on tcgen05 tensor
                           cores with e4m3 operands (A scaled per row, the thin
                           operand per column; scales applied in the epilogue)
                           and fp32 accumulation; B = Q^T A as in
                           RSVD_MIXED_BF16 (three-term split bf16) */
+  RSVD_MIXED_FP8_B128 = 4 /* as RSVD_MIXED_FP8 with one scale per block of 128
+                          rows of A: r_b = 448 / max |A| over the block's rows
+                          (binary32), found by one more read of A before the
+                          conversion pass */
 } rsvd_precision;
 
 /* Element types for the stage entry points. */

@@ -18,6 +18,9 @@ element by element:
   zero row), A8 = e4m3(binary32(A_ij r_i)), s_i = 1 / r_i, so A ~ diag(s) A8.
   (A scale per row is one instance of a diagonal row scaling A = S A8; a row
   fits in on-chip memory, so one pass over A finds the scale and converts.)
+  With block=b the maximum is taken over the b rows of i's block (rows
+  b floor(i / b) .. + b - 1), one scale for the whole block: the
+  per-128-row-block scaling, block=128.
 * A thin operand X (K x N) is scaled per column the same way:
   X ~ X8 diag(c), c_j = 1 / (448 / max_i |X_ij|).
 * Y = A X is computed as diag(s) (A8 X8) diag(c); the products of two e4m3
@@ -73,19 +76,26 @@ def e4m3_round(x):
     return np.where(np.isnan(x), np.nan, out)
 
 
-def row_scale(A):
-    """r_i = 448 / max_j |A_ij| in binary32 (1 for a zero row); returns (r, s = 1/r)."""
+def row_scale(A, block=None):
+    """r_i = 448 / max |A| in binary32 (1 for a zero maximum); returns (r, s = 1/r).
+    block=None: the maximum of row i; block=b: the maximum over the b rows of
+    i's block (rows b floor(i / b) .. + b - 1, all columns), one scale for the
+    whole block."""
     A = np.asarray(A, dtype=np.float32)
     amax = np.max(np.abs(A), axis=1).astype(np.float32)
+    if block is not None:
+        for b0 in range(0, A.shape[0], block):
+            amax[b0:b0 + block] = np.max(amax[b0:b0 + block])
     r = np.where(amax > 0, np.float32(E4M3_MAX) / np.where(amax > 0, amax, np.float32(1)), np.float32(1))
     r = r.astype(np.float32)
     return r, (np.float32(1) / r).astype(np.float32)
 
 
-def quantize_rows(A):
-    """(A8 values as float64, s) with A ~ diag(s) A8."""
+def quantize_rows(A, block=None):
+    """(A8 values as float64, s) with A ~ diag(s) A8 (per-row scales, or one
+    scale per block of `block` rows)."""
     A = np.asarray(A, dtype=np.float32)
-    r, s = row_scale(A)
+    r, s = row_scale(A, block)
     return e4m3_round((A * r[:, None]).astype(np.float32)), s
 
 
@@ -95,17 +105,17 @@ def quantize_cols(X):
     return X8t.T, c
 
 
-def sketch_fp8(A, X):
+def sketch_fp8(A, X, block=None):
     """Y = diag(s) (A8 X8) diag(c) in float64 (the exact value the e4m3
     tensor-core product approximates with binary32 accumulation)."""
-    A8, s = quantize_rows(A)
+    A8, s = quantize_rows(A, block)
     X8, c = quantize_cols(X)
     return (s.astype(np.float64)[:, None] * (A8 @ X8)) * c.astype(np.float64)[None, :]
 
 
-def sketch_fp8_t(A, Q):
+def sketch_fp8_t(A, Q, block=None):
     """Z = A8^T Q'8 diag(c'), Q' = binary32(s_i Q_ij) (the transposed sketch)."""
-    A8, s = quantize_rows(A)
+    A8, s = quantize_rows(A, block)
     Qs = (np.asarray(Q, dtype=np.float32) * s[:, None]).astype(np.float32)
     Q8, c = quantize_cols(Qs)
     return (A8.T @ Q8) * c.astype(np.float64)[None, :]

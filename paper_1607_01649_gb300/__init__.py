@@ -29,6 +29,7 @@ RSVD_F64 = 0
 RSVD_F32 = 1
 RSVD_MIXED_BF16 = 2
 RSVD_MIXED_FP8 = 3
+RSVD_MIXED_FP8_B128 = 4
 
 RSVD_DT_F64 = 0
 RSVD_DT_F32 = 1

@@ -44,7 +44,8 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* Ah, __nv_bfloat16* Al
 template <bool VEC>
 __global__ void __launch_bounds__(256)
     fp8_rows_kernel(int rows, int cols, const float* __restrict__ A, int lda, uint8_t* __restrict__ A8, int ld8,
-                    float* __restrict__ s, __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb) {
+                    float* __restrict__ s, __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb,
+                    const float* __restrict__ amax) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < rows; i += gridDim.x * wpb) {
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(256)
       for (int j = lane; j < cols; j += 32) mx = fmaxf(mx, fabsf(a[j]));
     }
     mx = warp_max(mx);
+    if (amax) mx = amax[i];  // a maximum over a block of rows, given
     const float r = mx > 0.f ? 448.0f / mx : 1.0f;
     if (lane == 0) s[i] = 1.0f / r;
     uint8_t* q = A8 + (size_t)i * ld8;
@@ -100,7 +102,7 @@ template <int NV>
 __global__ void __launch_bounds__(256)
     fp8_rows_block_kernel(int rows, int cols, const float* __restrict__ A, int lda, uint8_t* __restrict__ A8,
                           int ld8, float* __restrict__ s, __nv_bfloat16* __restrict__ Ah,
-                          __nv_bfloat16* __restrict__ Al, int ldb) {
+                          __nv_bfloat16* __restrict__ Al, int ldb, const float* __restrict__ amax) {
   __shared__ float red[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4 nxt[NV];
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
     __syncthreads();  // red is rewritten for the next row
+    if (amax) m = amax[i];  // a maximum over a block of rows, given
     const float r = m > 0.f ? 448.0f / m : 1.0f;
     if (tid == 0) s[i] = 1.0f / r;
     uint8_t* q = A8 + (size_t)i * ld8;
@@ -159,24 +162,59 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// amax[i] = max |A| over the rows of i's block of `block` rows (and all
+// columns): one CTA per block, 16-byte loads where the rows allow them.
+__global__ void __launch_bounds__(256) fp8_block_max_kernel(int rows, int cols, const float* __restrict__ A, int lda,
+                                                            int block, bool vec, float* __restrict__ amax) {
+  __shared__ float red[8];
+  const int r0 = blockIdx.x * block, r1 = min(rows, r0 + block);
+  float mx = 0.f;
+  if (vec) {
+    const int c4 = cols / 4;
+    for (int i = r0; i < r1; ++i) {
+      const float4* a = reinterpret_cast<const float4*>(A + (size_t)i * lda);
+      for (int j = threadIdx.x; j < c4; j += blockDim.x) {
+        const float4 v = a[j];
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+    }
+  } else {
+    for (int i = r0; i < r1; ++i)
+      for (int j = threadIdx.x; j < cols; j += blockDim.x) mx = fmaxf(mx, fabsf(A[(size_t)i * lda + j]));
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float m = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) amax[i] = m;
+}
+
+void launch_fp8_block_max(int rows, int cols, const float* A, int lda, int block, float* amax, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return;
+  const bool vec = (cols % 4 == 0) && (lda % 4 == 0) && (((uintptr_t)A & 15) == 0);
+  fp8_block_max_kernel<<<ceil_div(rows, block), 256, 0, st>>>(rows, cols, A, lda, block, vec, amax);
+  note_launch();
+}
+
 void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, int ld8, float* s, __nv_bfloat16* Ah,
-                     __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st) {
+                     __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st, const float* amax) {
   if (rows == 0 || cols == 0) return;
   const bool vec = (cols % 4 == 0) && (lda % 4 == 0) && (ld8 % 4 == 0) && (((uintptr_t)A & 15) == 0) &&
                    (((uintptr_t)A8 & 3) == 0) && (!Ah || (ldb % 4 == 0 && ((uintptr_t)Ah & 7) == 0 &&
                                                          ((uintptr_t)Al & 7) == 0));
   if (vec && cols <= 4096) {
     const int blocks = rows < sms * 4 ? rows : sms * 4;
-    fp8_rows_block_kernel<4><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb);
+    fp8_rows_block_kernel<4><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb, amax);
     note_launch();
     return;
   }
   int blocks = ceil_div(rows, 8);
   if (blocks > sms * 16) blocks = sms * 16;
   if (vec)
-    fp8_rows_kernel<true><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb);
+    fp8_rows_kernel<true><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb, amax);
   else
-    fp8_rows_kernel<false><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb);
+    fp8_rows_kernel<false><<<blocks, 256, 0, st>>>(rows, cols, A, lda, A8, ld8, s, Ah, Al, ldb, amax);
   note_launch();
 }
 

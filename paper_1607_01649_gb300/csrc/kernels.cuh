@@ -77,7 +77,11 @@ cudaError_t launch_tc_gemm_e4m3(int M, int N, int K, const uint8_t* A8, int lda,
 // Rows of A (fp32) scaled to e4m3: A8 (rows x cols, ld8 bytes), s[i] = max_j |A_ij| / 448;
 // optionally the bf16 pair Ah + Al of A (ldb elements).
 void launch_fp8_rows(int rows, int cols, const float* A, int lda, uint8_t* A8, int ld8, float* s,
-                     __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st);
+                     __nv_bfloat16* Ah, __nv_bfloat16* Al, int ldb, int sms, cudaStream_t st,
+                     const float* amax = nullptr);  // amax: a given maximum per row (block scaling)
+// amax[i] = max |A| over i's block of `block` rows (the per-block scale of the
+// e4m3 copy, RSVD_MIXED_FP8_B128)
+void launch_fp8_block_max(int rows, int cols, const float* A, int lda, int block, float* amax, cudaStream_t st);
 // B (cols x rows bytes, ldt) = A^T for e4m3 bytes A (rows x cols, lda).
 void launch_u8_transpose(int rows, int cols, const uint8_t* A, int lda, uint8_t* B, int ldt, cudaStream_t st);
 // X (rows x cols fp32, ldx), optionally with row scales rsc: X' = diag(rsc) X in binary32;

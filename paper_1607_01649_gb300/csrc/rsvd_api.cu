@@ -49,6 +49,8 @@ rsvd_status check_launch(rsvd_handle_t h, const char* where) {
 
 int max_l_for(int prec) { return prec == RSVD_F64 ? 128 : 256; }
 
+inline bool is_fp8(int prec) { return prec == RSVD_MIXED_FP8 || prec == RSVD_MIXED_FP8_B128; }
+
 size_t elem_size(int prec) { return prec == RSVD_F64 ? sizeof(double) : sizeof(float); }
 
 // ------------------------------------------------------ fixed-rank layout --
@@ -125,7 +127,7 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   if (!p) return fail(h, RSVD_E_INVALID, "params is NULL");
   if (m < 0 || n < 0) return fail(h, RSVD_E_INVALID, "negative size m=%d n=%d", m, n);
   if (p->k < 0 || p->p < 0 || p->q < 0) return fail(h, RSVD_E_INVALID, "k, p, q must be >= 0");
-  if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16 && p->prec != RSVD_MIXED_FP8)
+  if (p->prec != RSVD_F64 && p->prec != RSVD_F32 && p->prec != RSVD_MIXED_BF16 && !is_fp8(p->prec))
     return fail(h, RSVD_E_UNSUPPORTED, "precision %d is not implemented", p->prec);
   const int l0 = p->k + p->p;
   const bool krylov = (p->flags & RSVD_FLAG_KRYLOV) != 0;
@@ -141,7 +143,7 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   if (p->flags & RSVD_FLAG_SINGLE_PASS) {
     if (p->q != 0) return fail(h, RSVD_E_INVALID, "single pass: q must be 0 (A is read once per sketch)");
     if (p->k > 128) return fail(h, RSVD_E_UNSUPPORTED, "single pass: k must be <= 128 (binary64 fit)");
-    if (p->prec == RSVD_MIXED_FP8)
+    if (is_fp8(p->prec))
       return fail(h, RSVD_E_UNSUPPORTED, "single pass runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
     if (p->flags & (RSVD_FLAG_KRYLOV | RSVD_FLAG_CENTER | RSVD_FLAG_RETURN_FULL_L))
       return fail(h, RSVD_E_INVALID, "single pass takes neither Krylov blocks, centring nor RETURN_FULL_L");
@@ -150,7 +152,7 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
   }
   if (p->flags & RSVD_FLAG_SRFT) {
     if (p->q != 0) return fail(h, RSVD_E_INVALID, "SRFT sketch: q must be 0 (Fig. RSVD)");
-    if (p->prec == RSVD_MIXED_FP8)
+    if (is_fp8(p->prec))
       return fail(h, RSVD_E_UNSUPPORTED, "SRFT runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
     if (p->flags & (RSVD_FLAG_KRYLOV | RSVD_FLAG_CENTER | RSVD_FLAG_SINGLE_PASS))
       return fail(h, RSVD_E_INVALID, "SRFT takes neither Krylov blocks, centring nor the single-pass fit");
@@ -158,7 +160,7 @@ rsvd_status validate_fixed(rsvd_handle_t h, int m, int n, const void* A, int lda
       return fail(h, RSVD_E_UNSUPPORTED, "SRFT: the realified basis 2 (k + p) = %d exceeds %d", 2 * l0,
                   max_l_for(p->prec));
   }
-  if (krylov && p->prec == RSVD_MIXED_FP8)
+  if (krylov && is_fp8(p->prec))
     return fail(h, RSVD_E_UNSUPPORTED, "block Krylov runs in RSVD_F64, RSVD_F32 and RSVD_MIXED_BF16");
   if (krylov && p->prec == RSVD_MIXED_BF16 && (l0 % 8) != 0)
     return fail(h, RSVD_E_INVALID, "block Krylov in RSVD_MIXED_BF16 needs k + p a multiple of 8");
@@ -438,6 +440,7 @@ struct Fp8Extra {
   float* cvec;    // l column scales
   void* colws;    // fp8_cols scratch
   float* part8;   // e4m3 product partials
+  float* amax;    // m: the block maxima of RSVD_MIXED_FP8_B128
   size_t bytes;
 };
 
@@ -457,6 +460,7 @@ Fp8Extra fp8_extra(void* ws, int m, int n, int l, int sms) {
   size_t pw = tc_gemm_e4m3_workspace(m, l, n, sms);
   if (tc_gemm_e4m3_workspace(n, l, m, sms) > pw) pw = tc_gemm_e4m3_workspace(n, l, m, sms);
   E.part8 = c.take<float>(pw / sizeof(float) + 1);
+  E.amax = c.take<float>((size_t)m);
   E.bytes = c.size();
   return E;
 }
@@ -465,7 +469,7 @@ Fp8Extra fp8_extra(void* ws, int m, int n, int l, int sms) {
 struct SketchFp8 {
   DevStatus* st;
   uint8_t *A8, *A8T, *X8t;
-  float *s, *c, *part;
+  float *s, *c, *part, *amax;
   void* colws;
   size_t bytes;
 };
@@ -482,6 +486,7 @@ SketchFp8 sketch_fp8_layout(void* ws, int trans, int m, int n, int l, int sms) {
   F.c = c.take<float>((size_t)l);
   F.colws = c.take<unsigned char>(fp8_cols_workspace(K, l));
   F.part = c.take<float>(tc_gemm_e4m3_workspace(M, l, K, sms) / sizeof(float) + 1);
+  F.amax = c.take<float>((size_t)m);
   F.bytes = c.size();
   return F;
 }
@@ -497,8 +502,12 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
   const int sms = h->sms;
   const int n8 = round8(n), l8 = round8(l), n16 = round16(n), m16 = round16(m);
   rsvd_status st;
-  // one pass over A: A8 with row scales, and the bf16 pair for the projection
-  launch_fp8_rows(m, n, A, lda, E.A8, n16, E.s, L.Ah, L.Al, n8, sms, s);
+  // one pass over A: A8 with row scales (or, RSVD_MIXED_FP8_B128, the scale
+  // of each 128-row block, found by one read of A before it), and the bf16
+  // pair for the projection
+  const bool b128 = p->prec == RSVD_MIXED_FP8_B128;
+  if (b128) launch_fp8_block_max(m, n, A, lda, 128, E.amax, s);
+  launch_fp8_rows(m, n, A, lda, E.A8, n16, E.s, L.Ah, L.Al, n8, sms, s, b128 ? E.amax : nullptr);
   launch_u8_transpose(m, n, E.A8, n16, E.A8T, m16, s);
   // G = randn(n, l); Y = A G
   launch_gaussian(n, l, p->seed, 0u, 0, RSVD_DT_F32, E.Om, l, s);
@@ -1192,7 +1201,7 @@ rsvd_status rsvd_workspace_size(rsvd_handle_t handle, int m, int n, const rsvd_p
   }
   if (params->prec == RSVD_MIXED_BF16)
     *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes;
-  else if (params->prec == RSVD_MIXED_FP8)
+  else if (is_fp8(params->prec))
     *bytes = mixed_layout(nullptr, m, n, l, kk, handle->sms).bytes + fp8_extra(nullptr, m, n, l, handle->sms).bytes;
   else
     *bytes = fixed_layout(nullptr, m, n, l, kk, params->prec, handle->sms).bytes;
@@ -1303,7 +1312,7 @@ rsvd_status rsvd_fixed_rank(rsvd_handle_t handle, int m, int n, const void* A, i
     if (st != RSVD_OK) return st;
     return finish_sync(handle, params, M.st, s);
   }
-  if (params->prec == RSVD_MIXED_FP8) {
+  if (is_fp8(params->prec)) {
     if (((uintptr_t)A & 15) != 0) return fail(handle, RSVD_E_INVALID, "A must be 16-byte aligned");
     const MixedLayout M = mixed_layout(workspace, m, n, l, kk, handle->sms);
     const Fp8Extra E = fp8_extra((char*)workspace + M.bytes, m, n, l, handle->sms);
@@ -1561,7 +1570,7 @@ rsvd_status rsvd_sketch_workspace_size(rsvd_handle_t handle, int prec, int trans
     *bytes = simt_gemm_workspace(M, l, K, handle->sms, elem_size(prec)) + 512;
   else if (prec == RSVD_MIXED_BF16)
     *bytes = tc_gemm_workspace(M, l, K, handle->sms) + 512;
-  else if (prec == RSVD_MIXED_FP8)
+  else if (is_fp8(prec))
     *bytes = sketch_fp8_layout(nullptr, trans, m, n, l, handle->sms).bytes;
   else
     return fail(handle, RSVD_E_UNSUPPORTED, "precision %d is not built yet", prec);
@@ -1583,11 +1592,13 @@ rsvd_status rsvd_sketch(rsvd_handle_t handle, int prec, int trans, int m, int n,
   if (need > 512 && (!workspace || ws_bytes < need))
     return fail(handle, RSVD_E_NOMEM, "workspace of %zu bytes < required %zu", ws_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
-  if (prec == RSVD_MIXED_FP8) {
+  if (is_fp8(prec)) {
     if (l > 256) return fail(handle, RSVD_E_UNSUPPORTED, "l = %d > 256", l);
     const SketchFp8 F = sketch_fp8_layout(workspace, trans, m, n, l, handle->sms);
     cudaMemsetAsync(F.st, 0, sizeof(DevStatus), s);
-    launch_fp8_rows(m, n, (const float*)A, lda, F.A8, round16(n), F.s, nullptr, nullptr, 0, handle->sms, s);
+    if (prec == RSVD_MIXED_FP8_B128) launch_fp8_block_max(m, n, (const float*)A, lda, 128, F.amax, s);
+    launch_fp8_rows(m, n, (const float*)A, lda, F.A8, round16(n), F.s, nullptr, nullptr, 0, handle->sms, s,
+                    prec == RSVD_MIXED_FP8_B128 ? F.amax : nullptr);
     cudaError_t e;
     if (!trans) {
       launch_fp8_cols(n, l, (const float*)X, ldx, nullptr, F.X8t, round16(n), F.c, F.colws, s);

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import fp8
+from oracle import fp8 as OF
 
 
 def test_e4m3_value_set():
@@ -87,3 +88,36 @@ def test_scaled_sketch_error_is_fp8_sized():
     Z = fp8.sketch_fp8_t(A, Q)
     exz = A.astype(np.float64).T @ Q.astype(np.float64)
     assert np.linalg.norm(Z - exz) / np.linalg.norm(exz) < 0.1
+
+
+def test_block_scaling_of_rows():
+    """Per-block scaling (one scale per 128 rows): every block's largest
+    magnitude maps to exactly 448 and nothing exceeds it; a block of one row
+    is the per-row scaling; rows that share their maximum within each block
+    give the per-row result bit for bit; otherwise the smaller rows of a block
+    are quantized on the coarser grid of the block's scale."""
+    rng = np.random.default_rng(11)
+    A = (rng.standard_normal((300, 70)) * 10.0 ** rng.uniform(-2, 2, (300, 1))).astype(np.float32)
+    A8, s = OF.quantize_rows(A, block=128)
+    for b0 in range(0, 300, 128):
+        blk = A8[b0:b0 + 128]
+        assert np.max(np.abs(blk)) == 448.0
+        assert np.all(s[b0:b0 + 128] == s[b0])
+    one8, one_s = OF.quantize_rows(A, block=1)
+    row8, row_s = OF.quantize_rows(A)
+    assert np.array_equal(one8, row8) and np.array_equal(one_s, row_s)
+    # equal row maxima inside each block: block and row scaling coincide
+    B = A.copy()
+    B[:, 0] = np.float32(1000.0)
+    Bb8, Bbs = OF.quantize_rows(B, block=128)
+    Br8, Brs = OF.quantize_rows(B)
+    assert np.array_equal(Bb8, Br8) and np.array_equal(Bbs, Brs)
+    # with unequal rows the block grid is coarser: larger reconstruction error
+    err_b = np.abs(s[:, None] * A8 - A).max(axis=1) / np.abs(A).max(axis=1)
+    err_r = np.abs(row_s[:, None] * row8 - A).max(axis=1) / np.abs(A).max(axis=1)
+    assert np.mean(err_b) > np.mean(err_r)
+    # the sketch with block scales is the exact product of the block-quantized operands
+    X = rng.standard_normal((70, 9)).astype(np.float32)
+    X8, c = OF.quantize_cols(X)
+    ref = (s.astype(np.float64)[:, None] * (A8 @ X8)) * c.astype(np.float64)[None, :]
+    np.testing.assert_array_equal(OF.sketch_fp8(A, X, block=128), ref)

@@ -8,7 +8,8 @@ tensor-core passes over A, CholeskyQR2 after each product, B^T = A^T Q in
 split bf16, the small SVD, the lift to U and V).
 
 ``--workload pca``: the 2^20 x 4096 PCA-shaped matrix (rank-64 signal plus
-noise, column-centred), k = 64, p = 64, q = 1, e4m3 sketches.
+noise, column-centred), k = 64, p = 64, q = 1, e4m3 sketches with one scale
+per 128-row block of A.
 
 ``--workload batched``: 4096 kernel-matrix blocks (1 / |x_i - y_j| between two
 point clouds 3 apart, m, n ~ U{64..1024}) solved to relative Frobenius
@@ -541,6 +542,8 @@ def run_ours(a):
         # the bf16 pair written; e4m3 also writes A8 and its byte transpose),
         # the 2q + 1 sketch passes and the split-bf16 projection (Ah + Al)
         conv = (8.0 if prec == rs.RSVD_MIXED_BF16 else 11.0) * m * n
+        if prec == rs.RSVD_MIXED_FP8_B128:
+            conv += 4.0 * m * n  # the read of A that finds the 128-row block maxima
         design_bytes = conv + (2 * q + 1) * eb * m * n + 4.0 * m * n
         roof["solve_design_floor_ms"] = design_bytes / (hbm * 1e9) * 1e3
         roof["solve_design_frac"] = roof["solve_design_floor_ms"] / ms_per_step
@@ -553,6 +556,8 @@ def run_ours(a):
             variants = poly_variants(a, rs, h, A, dev, stream, fro_rel)
         elif a.workload == "pca":
             variants = {"centring": pca_centring(a, rs, h, A, dev, stream, D)}
+            if prec == rs.RSVD_MIXED_FP8_B128:
+                variants["e4m3_per_row_scales"] = pca_per_row(a, rs, h, A, dev, stream, D)
 
     # ---- e2e: the C-ABI call with HOST buffers (pinned).  The mixed paths read
     # A exactly once, in the conversion pass, so A is passed as the host
@@ -786,6 +791,31 @@ def poly_variants(a, rs, h, A, dev, stream, fro_rel):
     except Exception as exc:
         out["adaptive_spectral_4096"] = {"error": str(exc)[:200]}
     return out
+
+
+def pca_per_row(a, rs, h, A, dev, stream, D_block):
+    """The same PCA solve with one e4m3 scale per row of A instead of per
+    128-row block (one read of A fewer): time and the singular values beside
+    the block-scaled solve's."""
+    import torch
+    m, n, k, p, q = a.m, a.n, a.k, a.p, a.q
+    prm = rs.make_params(k, p, q, seed=a.seed + 100 + a.steps - 1, prec=rs.RSVD_MIXED_FP8, flags=0)
+    ws = torch.empty(rs.rsvd_workspace_size(h, m, n, prm), dtype=torch.uint8, device=dev)
+    U = torch.empty(m, k, dtype=torch.float32, device=dev)
+    D = torch.empty(k, dtype=torch.float64, device=dev)
+    V = torch.empty(n, k, dtype=torch.float32, device=dev)
+
+    def solve():
+        code = rs.rsvd_fixed_rank(h, m, n, A, A.stride(0), prm, U, k, D, V, k, ws)
+        if code != rs.RSVD_OK:
+            raise rs.RsvdError(code, rs.last_error(h))
+
+    ms = _timed(solve, 5, stream)
+    nk = min(k, 48)
+    diff = float(((D[:nk] - D_block[:nk]).abs() / D_block[:nk]).max())
+    del ws, U, V
+    return {"value": 1000.0 / ms, "unit": "solves/s", "ms": ms,
+            "max_rel_diff_sigma_1..48_vs_block_scaled": diff}
 
 
 def pca_centring(a, rs, h, A, dev, stream, D_centred):

@@ -549,36 +549,61 @@ __global__ void __launch_bounds__(NT)
   int attempt = 0;
   for (;;) {
     // unit-diagonal scaling Gt = D^-1 G D^-1 (+ shift) in the working
-    // precision: asynchronous copies of G (row by row; G is symmetric) into
-    // the blocks, then the scaling in place
-    for (int e = tid; e < nblk * CBK * CBK; e += NT) {
-      const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
-      const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
-      C* dst = Ls + (size_t)b * CBS + r * CP + c;
-      if (i < l && j < l) {
-        if (sizeof(C) == 4)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                       "l"(Gf + (size_t)i * l + j)
-                       : "memory");
-        else
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                       "l"(G + (size_t)i * l + j)
-                       : "memory");
-      } else {
-        *dst = (i == j) ? C(1) : C(0);
-      }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    for (int e = tid; e < nblk * CBK * CBK; e += NT) {
-      const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
-      const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
-      if (i < l && j < l) {
-        C* p = Ls + (size_t)b * CBS + r * CP + c;
-        C w = *p * rdc[i] * rdc[j];
-        if (i == j) w += shift;
-        if (!isfinite(w)) w = C(0);
-        *p = w;
+    // precision, straight from G (row-major, symmetric) into the blocks:
+    // groups of four consecutive columns of one row, eight groups in flight
+    // per thread (16-byte loads where l and the base allow them)
+    {
+      const C* Gsrc = (sizeof(C) == 4) ? reinterpret_cast<const C*>(Gf) : reinterpret_cast<const C*>(G);
+      const bool v4 = (l % 4 == 0) && ((((uintptr_t)Gsrc) & (4 * sizeof(C) - 1)) == 0);
+      const int ngroups = nblk * CBK * (CBK / 4);
+      for (int g0 = tid; g0 < ngroups; g0 += 8 * NT) {
+        C v[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int g = g0 + u * NT;
+          const int b = g >> 8, r = (g >> 3) & 31, c4 = (g & 7) * 4;
+          const int i = CBK * s_bi[b < nblk ? b : 0] + r, j = CBK * s_bj[b < nblk ? b : 0] + c4;
+          if (g < ngroups && i < l && j + 3 < l && v4) {
+            if (sizeof(C) == 4) {
+              const float4 x = *reinterpret_cast<const float4*>(Gsrc + (size_t)i * l + j);
+              v[u][0] = (C)x.x;
+              v[u][1] = (C)x.y;
+              v[u][2] = (C)x.z;
+              v[u][3] = (C)x.w;
+            } else {
+              const double2 x0 = *reinterpret_cast<const double2*>(Gsrc + (size_t)i * l + j);
+              const double2 x1 = *reinterpret_cast<const double2*>(Gsrc + (size_t)i * l + j + 2);
+              v[u][0] = (C)x0.x;
+              v[u][1] = (C)x0.y;
+              v[u][2] = (C)x1.x;
+              v[u][3] = (C)x1.y;
+            }
+          } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              v[u][t] = (g < ngroups && i < l && j + t < l) ? Gsrc[(size_t)i * l + j + t] : C(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int g = g0 + u * NT;
+          if (g >= ngroups) break;
+          const int b = g >> 8, r = (g >> 3) & 31, c4 = (g & 7) * 4;
+          const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c4;
+          C* dst = Ls + (size_t)b * CBS + r * CP + c4;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            C w;
+            if (i < l && j + t < l) {
+              w = v[u][t] * rdc[i] * rdc[j + t];
+              if (i == j + t) w += shift;
+              if (!isfinite(w)) w = C(0);
+            } else {
+              w = (i == j + t) ? C(1) : C(0);
+            }
+            dst[t] = w;
+          }
+        }
       }
     }
     if (tid == 0) s_fail = 0;

@@ -361,9 +361,17 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// Cluster size: 2 nc column blocks of w = l / (2 nc) columns.  Up to l = 256
+// the portable maximum of 8 CTAs; for l >= 192 a 16-CTA cluster (a
+// non-portable size) halves the warps each SM runs per step (the kernel is
+// bound by instruction issue on its SMs) at the cost of twice the block
+// exchanges per sweep.
+static int g_jacobi_max_cluster = 16;  // lowered to 8 if a 16-CTA cluster cannot launch
+
 int jacobi_cluster_size(int l) {
   int nc = (l + 31) / 32;
-  if (nc > 8) nc = 8;
+  if (l >= 192 && g_jacobi_max_cluster >= 16) nc = 16;
+  else if (nc > 8) nc = 8;
   if (nc < 1) nc = 1;
   return nc;
 }
@@ -399,6 +407,16 @@ cudaError_t launch_jacobi(int l, const double* Rb, C* Wt, C* Jt, double* sigma, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (nc > 8) {
+    // a 16-CTA cluster must be allowed explicitly and must fit the part
+    int ncl = 0;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&ncl, kfn, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      g_jacobi_max_cluster = 8;
+      return launch_jacobi<C>(l, Rb, Wt, Jt, sigma, st, s);
+    }
+  }
   note_launch();
   return cudaLaunchKernelEx(&cfg, kfn, l, w, Rb, Wt, Jt, sigma, st, 40);
 }

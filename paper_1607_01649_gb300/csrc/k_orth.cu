@@ -347,68 +347,91 @@ struct Eps<double> {
 // Right-looking over block columns k, with one block of lookahead:
 //   (1) L_ik = A_ik L_kk^-T, i > k, forward substitution, one thread per row;
 //   (2) A_i,k+1 -= L_ik L_k+1,k^T, i > k (the next block column);
-//   (3) warp 0 factors A_k+1,k+1, warp 1 inverts L_kk (for Ub), and the other
-//       warps apply the rest of the trailing update, A_ij -= L_ik L_jk^T,
-//       k + 1 < j <= i.
-// A warp updates a 32 x 32 block with each lane holding a 4 x 8 tile.
+//   (3) warp 0 factors A_k+1,k+1 while the other warps apply the rest of the
+//       trailing update, A_ij -= L_ik L_jk^T, k + 1 < j <= i.
+// The inverses of the diagonal blocks (for Ub and the explicit inverse) come
+// after the loop, one warp per block.  A warp updates a 32 x 32 block with
+// each lane holding a 4 x 8 tile.
 constexpr int CBK = 32;             // block size
 constexpr int CP = 33;              // padded row stride within a block
 constexpr int CBS = CBK * CP;       // stored entries per block
 
 __device__ __forceinline__ int lblk(int bi, int bj) { return bi * (bi + 1) / 2 + bj; }
 
-// Warp-level Cholesky of a 32 x 32 block held as rows (lane i: row[0..31] =
-// A(i, 0..31), lower part valid).  On return row[] holds row i of L.  Returns
-// false (warp-uniformly) on a pivot below tau.
-template <typename C>
-__device__ __forceinline__ bool warp_chol32(C (&row)[32], C tau) {
+// Warp-level Cholesky of a 32 x 32 block.  Lane i holds row i of the block in
+// row[] (lower part valid) and writes row i of L to Li[0..31] (zeros above
+// the diagonal); *dii receives L(i, i).  Column q is always row[0]: each step
+// updates the trailing entries and shifts them down by one, so every register
+// index is static while the step loop stays rolled (a compact loop body keeps
+// the code resident in the instruction cache; the fully unrolled factor ran
+// slower inside the blocked factorization, where other warps run other code
+// between its calls).  Steps q0 <= q < q1 touch entries 1 .. J = 31 - q0 only
+// (later ones are past column 31), so the four quarters of the steps run with
+// J = 31, 23, 15, 7.  A loop exit inside the unrolled body instead cost more
+// than the shuffles it saved.  Returns false (warp-uniformly: the pivot is a
+// shuffled value) on a pivot below tau.
+template <typename C, int J>
+__device__ __forceinline__ bool chol_steps(C (&row)[32], int q0, int q1, C tau, C* Li, C* dii) {
   const int lane = threadIdx.x % 32;
-  bool ok = true;
+#pragma unroll 1
+  for (int q = q0; q < q1; ++q) {
+    const C akk = __shfl_sync(0xffffffffu, row[0], q);
+    if (!(akk > tau) || !isfinite(akk)) return false;
+    const C rp = rsqrt(akk), piv = akk * rp;
+    const C liq = (lane == q) ? piv : (lane > q ? row[0] * rp : C(0));
+    Li[q] = liq;
+    if (lane == q) *dii = piv;
+    // row i -= l(i, q) * l(j, q) for q < j <= i, shifted down one column
 #pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    if (ok) {  // warp-uniform; no break, so q stays a compile-time index
-      const C akk = __shfl_sync(0xffffffffu, row[q], q);
-      if (!(akk > tau) || !isfinite(akk)) {
-        ok = false;
-      } else {
-        const C rp = rsqrt(akk), piv = akk * rp;
-        const C liq = (lane == q) ? piv : (lane > q ? row[q] * rp : C(0));
-        row[q] = liq;
-        // row i -= l(i, q) * l(j, q) for q < j <= i
-#pragma unroll
-        for (int j = q + 1; j < 32; ++j) {
-          const C ljq = __shfl_sync(0xffffffffu, liq, j);
-          if (lane >= j) row[j] = fma(-liq, ljq, row[j]);
-        }
-      }
+    for (int j = 1; j <= J; ++j) {
+      const C ljq = __shfl_sync(0xffffffffu, liq, (q + j) & 31);
+      row[j - 1] = (lane >= q + j) ? fma(-liq, ljq, row[j]) : row[j];
     }
   }
-  return ok;
+  return true;
+}
+
+template <typename C>
+__device__ __forceinline__ bool warp_chol32(C (&row)[32], C tau, C* Li, C* dii) {
+  return chol_steps<C, 31>(row, 0, 8, tau, Li, dii) && chol_steps<C, 23>(row, 8, 16, tau, Li, dii) &&
+         chol_steps<C, 15>(row, 16, 24, tau, Li, dii) && chol_steps<C, 7>(row, 24, 32, tau, Li, dii);
 }
 
 // Warp-level inverse of the lower triangular L held as rows (lane i: row[]
-// = row i of L): lane i ends with x[] = row i of L^-1.  x doubles as the
-// accumulator: lanes i > t add L(i, t) X(t, :) at step t, when lane t turns
-// its accumulator into its final row.
-template <typename C>
-__device__ __forceinline__ void warp_trinv32(const C (&row)[32], C (&x)[32]) {
+// = row i of L, consumed): lane i ends with x[] = row i of L^-1.  x doubles as
+// the accumulator: lanes i > t add L(i, t) X(t, :) at step t, when lane t turns
+// its accumulator into its final row.  L(i, t) is row[0] at step t (the row
+// shifts down one column per step), so the step loop stays rolled; steps
+// t0 <= t < t0 + 8 touch X(t, c) for c <= T = t0 + 7 only (X(t, c) = 0 for
+// c > t) and shift row entries below 31 - t0 only.
+template <typename C, int T>
+__device__ __forceinline__ void trinv_steps(C (&row)[32], C (&x)[32]) {
   const int lane = threadIdx.x % 32;
+  constexpr int t0 = T - 7;
+#pragma unroll 1
+  for (int t = t0; t <= T; ++t) {
+    const C lit = row[0];
+    if (lane == t) {
+      const C rd = C(1) / lit;
+#pragma unroll
+      for (int c = 0; c <= T; ++c) x[c] = ((c == t ? C(1) : C(0)) - x[c]) * rd;
+    }
+    const C m = lane > t ? lit : C(0);
+#pragma unroll
+    for (int c = 0; c <= T; ++c) x[c] = fma(m, __shfl_sync(0xffffffffu, x[c], t), x[c]);
+#pragma unroll
+    for (int j = 0; j < 31 - t0; ++j) row[j] = row[j + 1];
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void warp_trinv32(C (&row)[32], C (&x)[32]) {
 #pragma unroll
   for (int c = 0; c < 32; ++c) x[c] = C(0);
-#pragma unroll
-  for (int t = 0; t < 32; ++t) {
-    if (lane == t) {
-      const C rd = C(1) / row[t];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) x[c] = ((c == t ? C(1) : C(0)) - x[c]) * rd;
-    }
-    const C lit = lane > t ? row[t] : C(0);
-#pragma unroll
-    for (int c = 0; c <= t; ++c) {
-      const C xtc = __shfl_sync(0xffffffffu, x[c], t);
-      if (lane > t) x[c] = fma(lit, xtc, x[c]);
-    }
-  }
+  trinv_steps<C, 7>(row, x);
+  trinv_steps<C, 15>(row, x);
+  trinv_steps<C, 23>(row, x);
+  trinv_steps<C, 31>(row, x);
 }
 
 // One warp: Cb = A B^T (sub == false, in place allowed: Cb may be Ab) or
@@ -445,25 +468,6 @@ __device__ __forceinline__ void warp_blk_nt(C* Cb, const C* Ab, const C* Bb, boo
   __syncwarp();
 }
 
-// One warp: acc (lane's 4 x 8 tile, rows 4 lr .., columns 8 lc ..) += A B for
-// 32 x 32 blocks A, B with row stride CP.
-template <typename C>
-__device__ __forceinline__ void warp_blk_nn_acc(C (&acc)[4][8], const C* Ab, const C* Bb) {
-  const int lane = threadIdx.x % 32, lr = lane >> 2, lc = lane & 3;
-#pragma unroll 4
-  for (int t = 0; t < 32; ++t) {
-    C a[4], b[8];
-#pragma unroll
-    for (int x = 0; x < 4; ++x) a[x] = Ab[(4 * lr + x) * CP + t];
-#pragma unroll
-    for (int y = 0; y < 8; ++y) b[y] = Bb[t * CP + 8 * lc + y];
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 8; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-  }
-}
-
 // One warp: Cholesky of diagonal block k in place, and 1 / L(q, q) into
 // rdg[32 k + q].  On a pivot failure sets *fail.
 template <typename C>
@@ -473,16 +477,13 @@ __device__ __forceinline__ void diag_potrf(C* Ls, C* rdg, int k, C tau, int* fai
   C row[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) row[j] = (j <= lane) ? A[j] : C(0);
-  const bool ok = warp_chol32<C>(row, tau);
+  __syncwarp();
+  C dii = C(1);
+  const bool ok = warp_chol32<C>(row, tau, A, &dii);
+  __syncwarp();
   if (!ok) {
     if (lane == 0) *fail = 1;
     return;
-  }
-  C dii = C(1);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    A[j] = (j <= lane) ? row[j] : C(0);
-    if (j == lane) dii = row[j];
   }
   rdg[CBK * k + lane] = C(1) / dii;
 }
@@ -505,7 +506,7 @@ template <typename C, int NT>
 __global__ void __launch_bounds__(NT)
     chol_kernel(int l, const double* __restrict__ G, const float* __restrict__ Gf, C* __restrict__ Ub,
                 C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate,
-                const int* skip, int inverse) {
+                const int* skip) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = (l + CBK - 1) / CBK;
@@ -638,16 +639,13 @@ __global__ void __launch_bounds__(NT)
           warp_blk_nt<C>(Ls + (size_t)lblk(i, k + 1) * CBS, Ls + (size_t)lblk(i, k) * CBS,
                          Ls + (size_t)lblk(k + 1, k) * CBS, true);
         __syncthreads();
-        // (3) factor the next diagonal block || invert this one || the rest
-        // of the trailing update
+        // (3) factor the next diagonal block || the rest of the trailing update
         if (warp == 0) {
           diag_potrf<C>(Ls, rdg, k + 1, ctau, &s_fail);
-        } else if (warp == 1) {
-          diag_trinv<C>(Ls, Xs, k);
         } else {
           const int nt = NB - k - 2;  // block columns k + 2 .. NB - 1
           const int tasks = nt * (nt + 1) / 2;
-          for (int tk = warp - 2; tk < tasks; tk += nw - 2) {
+          for (int tk = warp - 1; tk < tasks; tk += nw - 1) {
             int ii = 0;
             while ((ii + 1) * (ii + 2) / 2 <= tk) ++ii;
             const int i = k + 2 + ii, j = k + 2 + (tk - ii * (ii + 1) / 2);
@@ -661,7 +659,9 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     if (s_fail == 0) {
-      if (warp == 0) diag_trinv<C>(Ls, Xs, NB - 1);
+      // the inverses of the diagonal blocks, one warp each (they are needed
+      // only by the outputs, so they stay off the factorization's chain)
+      for (int b = warp; b < NB; b += nw) diag_trinv<C>(Ls, Xs, b);
       __syncthreads();
       break;
     }
@@ -680,91 +680,43 @@ __global__ void __launch_bounds__(NT)
       st->shifted = 1;
     if (shift > C(0)) atomicAdd(&st->shift_count, 1);
   }
-  // R(i, j) = L(j, i) d_j for i <= j
+  // R(i, j) = L(j, i) d_j for i <= j; one warp per row, lane = column within
+  // a 32-column block (the block's base is warp-uniform)
   if (R) {
     for (int i = warp; i < l; i += nw) {
       const int bi = i >> 5, ii = i & 31;
-      for (int j = lane; j < l; j += 32) {
-        const int bj = j >> 5, jj = j & 31;
-        R[(size_t)i * l + j] = (i <= j) ? (double)Ls[(size_t)lblk(bj, bi) * CBS + jj * CP + ii] * d[j] : 0.0;
+      double* Ri = R + (size_t)i * l;
+      for (int bj = 0; bj < NB; ++bj) {
+        const int j = CBK * bj + lane;
+        if (j >= l) break;
+        double v = 0.0;
+        if (bj >= bi && i <= j) v = (double)Ls[(size_t)lblk(bj, bi) * CBS + lane * CP + ii] * d[j];
+        Ri[j] = v;
       }
     }
   }
-  if (!inverse) {
-    // Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a diagonal
-    // block (i <= j), 0 below
-    for (int i = warp; i < l; i += nw) {
-      const int bi = i >> 5, ii = i & 31;
-      for (int j = lane; j < l; j += 32) {
-        const int bj = j >> 5, jj = j & 31;
-        C v = C(0);
-        if (i <= j) v = (bi == bj) ? Xs[(size_t)bj * CBS + jj * CP + ii] : Ls[(size_t)lblk(bj, bi) * CBS + jj * CP + ii];
-        Ub[(size_t)i * l + j] = v;
-      }
-    }
-    for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
-    return;
-  }
-  // Explicit inverse.  W = L^-1 in place of the off-diagonal blocks, block
-  // column j from the last to the first (the trailing part already holds its
-  // inverse): T_i = sum_{k = j + 1}^{i} W_ik L_kj (i > j), W_ij = -T_i X_jj.
-  C* Ts = rdg + CBK * NB;  // NB - 1 scratch blocks
-  {
-    const int lr = lane >> 2, lc = lane & 3;
-    for (int j = NB - 2; j >= 0; --j) {
-      // T_i = sum_k W_ik L_kj, one warp per block row i (register-tiled products)
-      for (int i = j + 1 + warp; i < NB; i += nw) {
-        C acc[4][8];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
-        for (int k = j + 1; k <= i; ++k) {
-          const C* Wb = (k == i) ? Xs + (size_t)i * CBS : Ls + (size_t)lblk(i, k) * CBS;
-          warp_blk_nn_acc<C>(acc, Wb, Ls + (size_t)lblk(k, j) * CBS);
-        }
-        C* Tb = Ts + (size_t)(i - j - 1) * CBS;
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 8; ++y) Tb[(4 * lr + x) * CP + 8 * lc + y] = acc[x][y];
-      }
-      __syncthreads();
-      // W_ij = -T_i X_jj
-      for (int i = j + 1 + warp; i < NB; i += nw) {
-        C acc[4][8];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = C(0);
-        warp_blk_nn_acc<C>(acc, Ts + (size_t)(i - j - 1) * CBS, Xs + (size_t)j * CBS);
-        C* Wb = Ls + (size_t)lblk(i, j) * CBS;
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 8; ++y) Wb[(4 * lr + x) * CP + 8 * lc + y] = -acc[x][y];
-      }
-      __syncthreads();
-    }
-  }
-  // M = R^-1 = D^-1 W^T: M(k, j) = W(j, k) / d_k for j >= k, 0 below
-  for (int k = warp; k < l; k += nw) {
-    const int bk = k >> 5, kk = k & 31;
-    for (int j = lane; j < l; j += 32) {
-      const int bj = j >> 5, jj = j & 31;
+  // Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a diagonal
+  // block (i <= j), 0 below
+  for (int i = warp; i < l; i += nw) {
+    const int bi = i >> 5, ii = i & 31;
+    C* Ui = Ub + (size_t)i * l;
+    for (int bj = 0; bj < NB; ++bj) {
+      const int j = CBK * bj + lane;
+      if (j >= l) break;
       C v = C(0);
-      if (j >= k) {
-        const C* blkp = (bj == bk) ? Xs + (size_t)bj * CBS : Ls + (size_t)lblk(bj, bk) * CBS;
-        v = blkp[jj * CP + kk] * rdc[k];
+      if (bj >= bi && i <= j) {
+        const C* blk = (bj == bi) ? Xs + (size_t)bj * CBS : Ls + (size_t)lblk(bj, bi) * CBS;
+        v = blk[lane * CP + ii];
       }
-      Ub[(size_t)k * l + j] = v;
+      Ui[j] = v;
     }
   }
+  for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
 }
 
 size_t chol_smem_bytes(int l, size_t csize) {
   const int NB = (l + CBK - 1) / CBK;
-  const size_t blocks = (size_t)NB * (NB + 1) / 2 + NB + (NB > 1 ? NB - 1 : 0);  // L, X, inverse scratch
+  const size_t blocks = (size_t)NB * (NB + 1) / 2 + NB;  // L, X
   return blocks * CBS * csize + (size_t)l * sizeof(double) + (size_t)l * csize + (size_t)CBK * NB * csize;
 }
 
@@ -925,14 +877,15 @@ void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __
 
 template <typename C>
 void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
-                 const int* gate, cudaStream_t s, const int* skip, int inverse = 0) {
-  // binary32: 512 threads (128 registers each: the diagonal-block warp keeps a
-  // row of L and a row of its inverse in registers); binary64 (l <= 128): 256
+                 const int* gate, cudaStream_t s, const int* skip) {
+  // binary32: 512 threads (at most 128 registers each; a diagonal-block warp
+  // keeps a row of L and a row of its inverse in registers); binary64
+  // (l <= 128): 256
   constexpr int NT = sizeof(C) == 4 ? 512 : 256;
   const size_t smem = chol_smem_bytes(l, sizeof(C));
   auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip, inverse);
+  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip);
   note_launch();
 }
 
@@ -1003,6 +956,155 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
 // kernel, as the three-term split-bf16 product Yh Mh + Yh Ml + Yl Mh (relative
 // error about 2^-16 instead of binary32's 2^-24; the Gram stays binary32
 // products with binary64 sums).  Shorter blocks take the SIMT solve.
+// ------------------------------------------------------ explicit inverse --
+// M = R^-1 = D^-1 L^-T for the tensor-core apply, from the Cholesky kernel's
+// blocked factor Ub (Ub(i, j) = L(j, i) across blocks, X_bb(j, i) = (L_bb^-1)(j, i)
+// inside a diagonal block) and dinv.  The block columns of W = L^-1 are
+// independent, so CTA j forms block column j by block forward substitution,
+//   W_jj = X_jj,  W_ij = -X_ii sum_{k = j}^{i - 1} L_ik W_kj  (i > j),
+// with every block it needs staged in shared memory first (L_ik for
+// j <= k < i, X_ii for i >= j), and writes block row j of M:
+// M(32 j + r, 32 i + c) = W_ij(c, r) / d_(32 j + r).  One CTA per block column
+// spreads what the single-CTA factorization would do serially; each 32 x 32
+// product is 512 threads x two outputs.
+constexpr int INV_THREADS = 512;
+
+__global__ void __launch_bounds__(INV_THREADS)
+    inv_tri_kernel(int l, const float* __restrict__ Ub, const float* __restrict__ dinv, float* __restrict__ M,
+                   const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NB = (l + CBK - 1) / CBK;
+  const int j = blockIdx.x;
+  const int nw = NB - j;                      // blocks W_jj .. W_(NB-1) j
+  float* Wc = reinterpret_cast<float*>(smem_raw);   // nw blocks
+  float* Xd = Wc + (size_t)nw * CBS;                // X_ii, i = j .. NB-1
+  float* Lb = Xd + (size_t)nw * CBS;                // L_ik, j <= k < i, packed by (i, k)
+  float* Tb = Lb + (size_t)(nw * (nw - 1) / 2) * CBS;
+  const int tid = threadIdx.x;
+  auto lidx = [&](int i, int k) { return (i - j - 1) * (i - j) / 2 + (k - j); };  // i > k >= j
+  // ---- stage: X_ii (i >= j) and L_ik (i > k >= j).  A staged block (I, K)
+  // (X_ii is (i, i)) is rows 32 K .. + 31, columns 32 I .. + 31 of Ub, stored
+  // transposed; each thread moves 4 consecutive columns of one row, eight
+  // such groups in flight.
+  const int nl = nw * (nw - 1) / 2;
+  __shared__ unsigned char s_bi[64], s_bk[64];
+  if (tid < nw + nl) {
+    if (tid < nw) {
+      s_bi[tid] = (unsigned char)(j + tid);
+      s_bk[tid] = (unsigned char)(j + tid);
+    } else {
+      const int q = tid - nw;
+      int a = 0;
+      while ((a + 1) * (a + 2) / 2 <= q) ++a;  // q = a (a + 1) / 2 + b, b <= a
+      s_bi[tid] = (unsigned char)(j + 1 + a);
+      s_bk[tid] = (unsigned char)(j + (q - a * (a + 1) / 2));
+    }
+  }
+  __syncthreads();
+  const bool v4 = (l % 4 == 0) && ((((uintptr_t)Ub) & 15) == 0);
+  const int ngroups = (nw + nl) * CBK * (CBK / 4);
+  for (int g0 = tid; g0 < ngroups; g0 += 8 * INV_THREADS) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int g = g0 + u * INV_THREADS;
+      const int b = g >> 8, t = (g >> 3) & 31, r4 = (g & 7) * 4;
+      const int bb = b < nw + nl ? b : 0;
+      const int gi = CBK * s_bk[bb] + t, gj = CBK * s_bi[bb] + r4;
+      if (g < ngroups && gi < l && gj + 3 < l && v4) {
+        v[u] = *reinterpret_cast<const float4*>(Ub + (size_t)gi * l + gj);
+      } else {
+        float x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = (g < ngroups && gi < l && gj + e < l) ? Ub[(size_t)gi * l + gj + e] : 0.f;
+        v[u] = make_float4(x[0], x[1], x[2], x[3]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int g = g0 + u * INV_THREADS;
+      if (g >= ngroups) break;
+      const int b = g >> 8, t = (g >> 3) & 31, r4 = (g & 7) * 4;
+      const int gi = CBK * s_bk[b] + t, gj0 = CBK * s_bi[b] + r4;
+      const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = r4 + e;
+        float val;
+        if (b < nw) {  // X_ii(r, t), the identity on the padding
+          val = (gi < l && gj0 + e < l) ? ((r >= t) ? x[e] : 0.f) : ((r == t) ? 1.f : 0.f);
+          Xd[(size_t)b * CBS + r * CP + t] = val;
+        } else {       // L_ik(r, t)
+          Lb[(size_t)(b - nw) * CBS + r * CP + t] = x[e];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int r = tid >> 4, c = (tid & 15) * 2;  // this thread's two outputs (r, c), (r, c + 1)
+  // W_jj = X_jj
+  Wc[r * CP + c] = Xd[r * CP + c];
+  Wc[r * CP + c + 1] = Xd[r * CP + c + 1];
+  __syncthreads();
+  for (int i = j + 1; i < NB; ++i) {
+    // T = sum_k L_ik W_kj
+    float t0 = 0.f, t1 = 0.f;
+    for (int k = j; k < i; ++k) {
+      const float* Lk = Lb + (size_t)lidx(i, k) * CBS + r * CP;
+      const float* Wk = Wc + (size_t)(k - j) * CBS + c;
+#pragma unroll 8
+      for (int u = 0; u < CBK; ++u) {
+        const float a = Lk[u];
+        t0 = fmaf(a, Wk[u * CP], t0);
+        t1 = fmaf(a, Wk[u * CP + 1], t1);
+      }
+    }
+    Tb[r * CP + c] = t0;
+    Tb[r * CP + c + 1] = t1;
+    __syncthreads();
+    // W_ij = -X_ii T
+    const float* Xi = Xd + (size_t)(i - j) * CBS + r * CP;
+    float w0 = 0.f, w1 = 0.f;
+#pragma unroll 8
+    for (int u = 0; u < CBK; ++u) {
+      const float a = Xi[u];
+      w0 = fmaf(a, Tb[u * CP + c], w0);
+      w1 = fmaf(a, Tb[u * CP + c + 1], w1);
+    }
+    Wc[(size_t)(i - j) * CBS + r * CP + c] = -w0;
+    Wc[(size_t)(i - j) * CBS + r * CP + c + 1] = -w1;
+    __syncthreads();
+  }
+  // block row j of M: M(32 j + rr, col) = W(col, 32 j + rr) / d_(32 j + rr) for
+  // col >= 32 j (W_ij(col - 32 i, rr)), 0 before
+  for (int e = tid; e < CBK * l; e += INV_THREADS) {
+    const int rr = e / l, col = e % l;
+    const int row = CBK * j + rr;
+    if (row >= l) continue;
+    float v = 0.f;
+    if (col >= CBK * j) {
+      const int i = col / CBK, cc = col % CBK;
+      v = Wc[(size_t)(i - j) * CBS + cc * CP + rr] * dinv[row];
+    }
+    M[(size_t)row * l + col] = v;
+  }
+}
+
+size_t inv_tri_smem_bytes(int l) {
+  const int NB = (l + CBK - 1) / CBK;
+  const size_t nw = NB, nl = (size_t)NB * (NB - 1) / 2;
+  return (2 * nw + nl + 1) * CBS * sizeof(float);
+}
+
+void launch_inv_tri(int l, const float* Ub, const float* dinv, float* M, const int* gate, cudaStream_t s) {
+  const int NB = (l + CBK - 1) / CBK;
+  const size_t smem = inv_tri_smem_bytes(l);
+  cudaFuncSetAttribute(inv_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  inv_tri_kernel<<<NB, INV_THREADS, smem, s>>>(l, Ub, dinv, M, gate);
+  note_launch();
+}
+
 size_t orth_tc_workspace_bytes(int rows, int l, int sms) {
   const int l8 = (l + 7) / 8 * 8;
   Carver c(nullptr);
@@ -1010,13 +1112,14 @@ size_t orth_tc_workspace_bytes(int rows, int l, int sms) {
   c.take<__nv_bfloat16>((size_t)2 * rows * l8);  // Yh, Yl
   c.take<__nv_bfloat16>((size_t)2 * l * l8);     // Mh, Ml
   c.take<unsigned char>(tc_gemm_workspace(rows, l, l, sms));
+  c.take<float>((size_t)l * l);                   // M = R^-1
   return c.size();
 }
 
-// The tensor-core apply pays for an explicit triangular inverse (on one SM)
-// and the bf16 split of M; it wins once the block is tall.  Measured on
-// GB300 with the register-tiled inverse: from 64 l rows (32768 x 256 and
-// 2^20 x 128 both gain; the SIMT solve wins below).
+// The tensor-core apply pays for an explicit triangular inverse (inv_tri_kernel,
+// one CTA per block column) and the bf16 split of M; it wins once the block is
+// tall.  Measured on GB300: from 64 l rows (32768 x 256 and 2^20 x 128 both
+// gain; the SIMT solve wins below).
 bool orth_tc_pays(int rows, int l) { return (long long)rows >= 64LL * l; }
 
 void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
@@ -1033,6 +1136,7 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
   __nv_bfloat16* Mh = c0.take<__nv_bfloat16>((size_t)l * l8);
   __nv_bfloat16* Ml = c0.take<__nv_bfloat16>((size_t)l * l8);
   float* part = c0.take<float>(tc_gemm_workspace(rows, l, l, sms) / sizeof(float) + 1);
+  float* Minv = c0.take<float>((size_t)l * l);
   Carver c(base);
   double* P = c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
   double* G = c.take<double>((size_t)l * l);
@@ -1046,12 +1150,15 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
     const int* gate = pass == 3 ? gate3 : nullptr;
     // the Gram kernel also writes the bf16 pair Yh + Yl of Y
     launch_gram<float>(rows, l, Y, ldy, P, G, Gf, sms, gate, s, nullptr, Yh, Yl, l8);
+    // the factor in its blocked form (M's slot holds it), then R^-1 by block
+    // columns on NB SMs
     launch_chol<float>(l, G, Gf, M, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s,
-                       nullptr, 1);
+                       nullptr);
+    launch_inv_tri(l, M, dinv, Minv, gate, s);
     // pass 3 runs only if pass 1 needed a shift (a device-side gate): the
     // product then returns at once and leaves Y alone (the split of M only
     // fills scratch)
-    launch_split_bf16(l, l, M, l, Mh, Ml, l8, sms, s);
+    launch_split_bf16(l, l, Minv, l, Mh, Ml, l8, sms, s);
     launch_tc_gemm(false, true, rows, l, l, Yh, l8, Yl, Mh, l8, Ml, Y, ldy, part, sms, st, s, 128, gate);
   }
   if (Ybf) launch_copy_bf16<float>(rows, l, Y, ldy, Ybf, lb, s);

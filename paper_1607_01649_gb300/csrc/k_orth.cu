@@ -3,7 +3,8 @@
 // Nakatsukasa, Yamamoto, Yanagisawa, SISC 42 (2020)).
 //
 // One pass on a rows x l block Y (row-major, updated in place):
-//   1. G = Y^T Y                    (gram_partial + gram_reduce; binary64 sums)
+//   1. G = Y^T Y                    (gram_partial + gram_reduce; sums carried
+//                                     beyond binary32 precision)
 //   2. G = D Gt D, Gt = Lt Lt^T      (chol: unit-diagonal scaling in binary64,
 //                                     Cholesky of Gt (+ s I when needed))
 //   3. Y <- Y D^-1 Lt^-T             (apply: blocked triangular solve,
@@ -12,9 +13,11 @@
 //
 // Binary64 on this part runs at 1/58 of binary32 (measured 1.20 TFLOP/s vs
 // 70 TFLOP/s), so the plain-binary32 and mixed paths form each product of the
-// Gram in binary32 over chunks of 128 rows and carry the running sums in
-// binary64; the O(l^3) Cholesky and solve arithmetic is binary32 on a
-// binary64-scaled matrix.  The binary64 path is binary64 throughout.
+// Gram in binary32 over chunks of 512 rows and carry the running sums as
+// unevaluated pairs of binary32 numbers (error-free TwoSum updates, about 48
+// significant bits), rounded once to binary64 at the end; the O(l^3) Cholesky
+// and solve arithmetic is binary32 on a binary64-scaled matrix.  The binary64
+// path is binary64 throughout.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -24,9 +27,8 @@ namespace rsvd {
 constexpr int GT = 64;       // Gram tile
 constexpr int GCH = 32;      // rows per chunk in shared memory
 constexpr int GFOLD = 4;     // chunks per binary64 fold (128 rows)
-// The binary32 Gram folds its partial sums into binary64 every 512 rows:
-// binary64 adds run at 1/64 of the binary32 rate on this part, and a fold
-// every 128 rows spent one binary64 add per 128 FMAs of a thread.
+// The binary32 Gram folds its partial sums into the running pair every 512
+// rows.
 constexpr int GFOLD32 = 16;
 
 // Partial Gram of rows [r_beg, r_end) for the upper-triangular tile
@@ -109,51 +111,72 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Binary32 partial Gram, same contract as gram_partial_kernel: 128 threads,
-// thread (ty, tx) owns rows ty * 8 .. + 7 and columns tx * 4 .. + 3 of the
-// tile (4 shared-memory vector loads per 32 FMAs); the next 32-row chunk is
-// loaded into registers while the current one is multiplied.
-constexpr int G32_THREADS = 128;
+// Binary32 partial Gram, same contract as gram_partial_kernel: 64 threads,
+// thread (ty, tx) owns the 8 x 8 entries in rows {4 ty .. + 3, 32 + 4 ty .. + 3}
+// and columns {4 tx .. + 3, 32 + 4 tx .. + 3} of the tile (four 16-byte
+// shared-memory loads per 64 FMAs; the split halves keep the loads of a
+// quarter-warp on distinct banks).  32-row chunks of the two column blocks
+// stream into shared memory by cp.async, double-buffered, so the next chunk
+// is in flight while the current one is multiplied.  Every GFOLD32 chunks the
+// binary32 sums are folded into the split's partial, an unevaluated pair of
+// binary32 numbers (hi, lo) updated by an error-free two-sum (Knuth's TwoSum),
+// so the running sums carry about 48 significant bits without binary64
+// arithmetic (which runs at 1/64 of the binary32 rate on this part).  The
+// partial is private to the CTA: the first fold writes it, later ones add.
+constexpr int G32_THREADS = 64;
 
-__device__ __forceinline__ void gram_load_chunk(const float* __restrict__ Y, int ldy, int r0, int r_end, int c0,
-                                                int l, bool vec, float4 (&reg)[4]) {
-  // 32 rows x 64 columns = 512 float4, four per thread
+// s + e = a + b exactly, s = fl(a + b) (Knuth's TwoSum; explicit round-to-
+// nearest adds, so that nothing is contracted or reassociated).
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+  return s;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = pred ? 16 : 0;  // 0: fill the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Rows r0 .. r0 + 31 (below r_end), columns c0 .. c0 + 63 (below l) of Y into
+// S: 512 groups of four floats, eight per thread.  vec: cp.async (l, ldy and
+// Y allow 16-byte copies); else plain loads and stores.
+__device__ __forceinline__ void gram_fetch_chunk(float (*S)[GT], const float* __restrict__ Y, int ldy, int r0,
+                                                 int r_end, int c0, int l, bool vec) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 8; ++u) {
     const int e = threadIdx.x + G32_THREADS * u;
     const int rr = e / 16, c4 = e % 16;
     const int gr = r0 + rr, gc = c0 + 4 * c4;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (gr < r_end) {
-      const float* src = Y + (size_t)gr * ldy + gc;
-      if (vec) {
-        if (gc < l) v = *reinterpret_cast<const float4*>(src);
-      } else {
-        if (gc < l) v.x = src[0];
-        if (gc + 1 < l) v.y = src[1];
-        if (gc + 2 < l) v.z = src[2];
-        if (gc + 3 < l) v.w = src[3];
-      }
-    }
-    reg[u] = v;
-  }
-}
-
-__device__ __forceinline__ void gram_store_chunk(float (*S)[GT], const float4 (&reg)[4]) {
+    float* dst = &S[rr][4 * c4];
+    if (vec) {
+      const bool ok = gr < r_end && gc < l;
+      cp_async16(dst, ok ? (const void*)(Y + (size_t)gr * ldy + gc) : (const void*)Y, ok);
+    } else {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (gr < r_end) {
+        const float* src = Y + (size_t)gr * ldy + gc;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int e = threadIdx.x + G32_THREADS * u;
-    *reinterpret_cast<float4*>(&S[e / 16][4 * (e % 16)]) = reg[u];
+        for (int q = 0; q < 4; ++q)
+          if (gc + q < l) v[q] = src[q];
+      }
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    }
   }
 }
 
-__global__ void __launch_bounds__(G32_THREADS)
+__global__ void __launch_bounds__(G32_THREADS, 7)
     gram_partial_f32_kernel(int rows, int l, const float* __restrict__ Y, int ldy, double* __restrict__ P,
                             int rows_per_split, const int* gate, const int* skip, __nv_bfloat16* __restrict__ Yh,
                             __nv_bfloat16* __restrict__ Yl, int lb) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
-  __shared__ __align__(16) float Yi[GCH][GT];
-  __shared__ __align__(16) float Yj[GCH][GT];
+  __shared__ __align__(16) float Yi[2][GCH][GT];
+  __shared__ __align__(16) float Yj[2][GCH][GT];
   const int nb = ceil_div(l, GT);
   int t = blockIdx.x, bi = 0;
   while (t >= nb - bi) {
@@ -162,36 +185,42 @@ __global__ void __launch_bounds__(G32_THREADS)
   }
   const int bj = bi + t;
   const bool diag = bi == bj;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x, tx = tid % 8, ty = tid / 8;
   const int r_beg = blockIdx.y * rows_per_split;
   const int r_end = min(rows, r_beg + rows_per_split);
   const bool vec = (l % 4) == 0 && (ldy % 4) == 0 && (((uintptr_t)Y) & 15) == 0;
-  float part[8][4];
-  double acc[8][4];
+  float2* out = reinterpret_cast<float2*>(P) + (size_t)blockIdx.y * l * l;
+  float part[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      part[a][b] = 0.f;
-      acc[a][b] = 0.0;
-    }
-  float4 ri[4], rj[4];
-  gram_load_chunk(Y, ldy, r_beg, r_end, bi * GT, l, vec, ri);
-  if (!diag) gram_load_chunk(Y, ldy, r_beg, r_end, bj * GT, l, vec, rj);
+    for (int b = 0; b < 8; ++b) part[a][b] = 0.f;
+  bool first_fold = true;
+  gram_fetch_chunk(Yi[0], Y, ldy, r_beg, r_end, bi * GT, l, vec);
+  if (!diag) gram_fetch_chunk(Yj[0], Y, ldy, r_beg, r_end, bj * GT, l, vec);
+  cp_async_commit();
   int chunk = 0;
   for (int r0 = r_beg; r0 < r_end; r0 += GCH, ++chunk) {
-    __syncthreads();  // previous chunk's reads are done
-    gram_store_chunk(Yi, ri);
-    if (!diag) gram_store_chunk(Yj, rj);
+    const int cur = chunk & 1;
+    if (r0 + GCH < r_end) {  // the next chunk into the other buffer
+      gram_fetch_chunk(Yi[cur ^ 1], Y, ldy, r0 + GCH, r_end, bi * GT, l, vec);
+      if (!diag) gram_fetch_chunk(Yj[cur ^ 1], Y, ldy, r0 + GCH, r_end, bj * GT, l, vec);
+    }
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of the current chunk have landed
+    __syncthreads();   // and every thread's
+    const float(*Si)[GT] = Yi[cur];
+    const float(*Sj)[GT] = diag ? Yi[cur] : Yj[cur];
     if (diag && Yh) {
       // the diagonal tiles read every element of Y exactly once: write the
       // bf16 pair Y = Yh + Yl that the tensor-core apply takes
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = threadIdx.x + G32_THREADS * u;
-        const int gr = r0 + e / 16, gc = bi * GT + 4 * (e % 16);
+      for (int u = 0; u < 8; ++u) {
+        const int e = tid + G32_THREADS * u;
+        const int rr = e / 16, c4 = e % 16;
+        const int gr = r0 + rr, gc = bi * GT + 4 * c4;
         if (gr < r_end && gc < l) {
-          const float4 a = ri[u];
+          const float4 a = *reinterpret_cast<const float4*>(&Si[rr][4 * c4]);
           const __nv_bfloat162 h01 = __floats2bfloat162_rn(a.x, a.y), h23 = __floats2bfloat162_rn(a.z, a.w);
           const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
           const __nv_bfloat162 l01 = __floats2bfloat162_rn(a.x - f01.x, a.y - f01.y);
@@ -215,66 +244,74 @@ __global__ void __launch_bounds__(G32_THREADS)
         }
       }
     }
-    __syncthreads();
-    if (r0 + GCH < r_end) {  // prefetch the next chunk
-      gram_load_chunk(Y, ldy, r0 + GCH, r_end, bi * GT, l, vec, ri);
-      if (!diag) gram_load_chunk(Y, ldy, r0 + GCH, r_end, bj * GT, l, vec, rj);
-    }
-    const float(*Sj)[GT] = diag ? Yi : Yj;
-#pragma unroll 4
+#pragma unroll 2
     for (int rr = 0; rr < GCH; ++rr) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&Yi[rr][8 * ty]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&Yi[rr][8 * ty + 4]);
-      const float4 bv = *reinterpret_cast<const float4*>(&Sj[rr][4 * tx]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&Si[rr][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Si[rr][32 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Sj[rr][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Sj[rr][32 + 4 * tx]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[4] = {bv.x, bv.y, bv.z, bv.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) part[u][v] = fmaf(a[u], b[v], part[u][v]);
+        for (int v = 0; v < 8; ++v) part[u][v] = fmaf(a[u], b[v], part[u][v]);
     }
     if ((chunk % GFOLD32) == GFOLD32 - 1 || r0 + GCH >= r_end) {
+      // fold through shared memory (the current buffers, free once every
+      // thread is done with them), one entry per thread and step, so that
+      // the fold adds no registers to the product loop
+      float* Fi = &Yi[cur][0][0];  // rows 0 .. 31 of the 64 x 64 tile
+      float* Fj = &Yj[cur][0][0];  // rows 32 .. 63
+      __syncthreads();
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < 8; ++u) {
+        const int ii = u < 4 ? 4 * ty + u : 32 + 4 * ty + u - 4;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          acc[u][v] += (double)part[u][v];
+        for (int v = 0; v < 8; ++v) {
+          const int jj = v < 4 ? 4 * tx + v : 32 + 4 * tx + v - 4;
+          (ii < 32 ? Fi + ii * GT : Fj + (ii - 32) * GT)[jj] = part[u][v];
           part[u][v] = 0.f;
         }
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int e = tid; e < GT * GT; e += G32_THREADS) {
+        const int ii = e / GT, jj = e % GT;
+        const int i = bi * GT + ii, j = bj * GT + jj;
+        if (i < l && j < l) {
+          const float pv = (ii < 32 ? Fi + ii * GT : Fj + (ii - 32) * GT)[jj];
+          float2* o = out + (size_t)i * l + j;
+          if (first_fold) {
+            *o = make_float2(pv, 0.f);
+          } else {
+            const float2 h = *o;
+            float e2;
+            const float sum = two_sum(h.x, pv, e2);
+            *o = make_float2(sum, __fadd_rn(h.y, e2));
+          }
+        }
+      }
+      first_fold = false;
     }
-  }
-  double* out = P + (size_t)blockIdx.y * l * l;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int i = bi * GT + 8 * ty + u;
-    if (i >= l) continue;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int j = bj * GT + 4 * tx + v;
-      if (j < l) out[(size_t)i * l + j] = acc[u][v];
-    }
+    __syncthreads();  // every read of this buffer is done before it is refilled
   }
 }
 
 // G[i][j] = sum over splits (fixed order) of the upper-triangular partials;
 // Gf receives G rounded to binary32 (the Cholesky kernel's input on the
-// binary32 path; converting here spreads the binary64 conversions over the GPU).
-__global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__ P, double* __restrict__ G,
-                                   float* __restrict__ Gf, const int* gate, const int* skip) {
-  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= l * l) return;
-  int i = idx / l, j = idx % l;
-  // tiles with bi > bj were not computed: read the mirrored entry instead
-  if (i / GT > j / GT) {
-    const int t = i;
-    i = j;
-    j = t;
-  }
-  // eight interleaved binary64 sums (a fixed order), so that eight loads per
-  // thread are in flight instead of one
-  const double* p = P + (size_t)i * l + j;
-  const size_t ll = (size_t)l * l;
+// binary32 path; converting here spreads the conversions over the GPU).  The
+// partials are (hi, lo) pairs of binary32 (PT = float2, summed the same way:
+// TwoSum into running pairs, one binary64 add at the end) or binary64 (summed
+// in binary64).  One CTA per 8 x 32 sub-tile (one entry per thread) of a
+// computed (upper) Gram tile: it sums the sub-tile with coalesced reads and
+// writes it, and for an off-diagonal Gram tile also its transpose (through
+// shared memory, eight consecutive entries per row), so reads and writes walk
+// rows.
+constexpr int GR_R = 8, GR_C = 32;
+
+__device__ __forceinline__ double gram_sum_entry(const double* p, size_t ll, int splits) {
+  // eight interleaved binary64 sums (a fixed order): eight loads in flight
   double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   int z = 0;
   for (; z + 7 < splits; z += 8) {
@@ -282,15 +319,95 @@ __global__ void gram_reduce_kernel(int l, int splits, const double* __restrict__
     for (int q = 0; q < 8; ++q) a[q] += p[(size_t)(z + q) * ll];
   }
   for (; z < splits; ++z) a[0] += p[(size_t)z * ll];
-  const double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-  G[idx] = s;
-  if (Gf) Gf[idx] = (float)s;
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-int gram_splits(int rows, int l, int sms) {
+__device__ __forceinline__ double gram_sum_entry(const float2* p, size_t ll, int splits) {
+  // eight interleaved running pairs (a fixed order), sixteen loads in flight
+  constexpr int Q = 8, U = 16;
+  float hs[Q], ls[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) hs[q] = ls[q] = 0.f;
+  int z = 0;
+  for (; z + U - 1 < splits; z += U) {
+    float2 v[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) v[q] = p[(size_t)(z + q) * ll];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      float e;
+      hs[q % Q] = two_sum(hs[q % Q], v[q].x, e);
+      ls[q % Q] = __fadd_rn(ls[q % Q], __fadd_rn(e, v[q].y));
+    }
+  }
+  for (; z < splits; ++z) {
+    const float2 v = p[(size_t)z * ll];
+    float e;
+    hs[0] = two_sum(hs[0], v.x, e);
+    ls[0] = __fadd_rn(ls[0], __fadd_rn(e, v.y));
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) t += (double)hs[q] + (double)ls[q];
+  return t;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(GR_R * GR_C)
+    gram_reduce_kernel(int l, int splits, const PT* __restrict__ P, double* __restrict__ G,
+                       float* __restrict__ Gf, const int* gate, const int* skip) {
+  if ((gate && *gate == 0) || (skip && *skip != 0)) return;
+  const int ti = blockIdx.y * GR_R, tj = blockIdx.x * GR_C;
+  if (ti / GT > tj / GT) return;  // the mirror of a computed tile: its CTA writes it
+  const bool mirror = ti / GT < tj / GT;
+  __shared__ double tile[GR_R][GR_C + 1];
+  const int tx = threadIdx.x % GR_C, ty = threadIdx.x / GR_C;
+  const int i = ti + ty, j = tj + tx;
+  double s = 0.0;
+  if (i < l && j < l) {
+    s = gram_sum_entry(P + (size_t)i * l + j, (size_t)l * l, splits);
+    G[(size_t)i * l + j] = s;
+    if (Gf) Gf[(size_t)i * l + j] = (float)s;
+  }
+  if (!mirror) return;
+  tile[ty][tx] = s;
+  __syncthreads();
+  // G(tj + a, ti + b) = G(ti + b, tj + a)
+  const int a = threadIdx.x / GR_R, b = threadIdx.x % GR_R;
+  const int ii = tj + a, jj = ti + b;
+  if (ii < l && jj < l) {
+    const double v = tile[b][a];
+    G[(size_t)ii * l + jj] = v;
+    if (Gf) Gf[(size_t)ii * l + jj] = (float)v;
+  }
+}
+
+// CTAs of the partial-Gram kernel for Y's element size that one SM holds at
+// once (occupancy query, cached per size; 1 if the query fails).
+int gram_resident(size_t tsize) {
+  static int cached[2] = {0, 0};
+  const int w = tsize == 4 ? 0 : 1;
+  if (cached[w] == 0) {
+    int b = 0;
+    cudaError_t e = tsize == 4
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gram_partial_f32_kernel, G32_THREADS, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gram_partial_kernel<double>, 256, 0);
+    if (e != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    cached[w] = b;
+  }
+  return cached[w];
+}
+
+// Row splits of the partial Gram: enough CTAs to fill every SM's slots in one
+// wave (a second, nearly empty wave would double the kernel's time), at least
+// four chunks of rows per split.
+int gram_splits(int rows, int l, int sms, size_t tsize) {
   const int nb = ceil_div(l, GT);
   const int tiles = nb * (nb + 1) / 2;
-  int s = ceil_div(3 * sms, tiles);
+  int s = gram_resident(tsize) * sms / tiles;
   const int smax = ceil_div(rows, 4 * GCH);
   if (s > smax) s = smax;
   if (s < 1) s = 1;
@@ -303,7 +420,7 @@ void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, flo
                  cudaStream_t s, const int* skip, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int lb) {
   const int nb = ceil_div(l, GT);
   const int tiles = nb * (nb + 1) / 2;
-  const int splits = gram_splits(rows, l, sms);
+  const int splits = gram_splits(rows, l, sms, sizeof(T));
   const int rps = ceil_div(ceil_div(rows, splits), GCH) * GCH;
   const int used = ceil_div(rows, rps);
   if (sizeof(T) == 4)
@@ -312,7 +429,12 @@ void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, flo
   else
     gram_partial_kernel<T><<<dim3(tiles, used), 256, 0, s>>>(rows, l, Y, ldy, P, rps, gate, skip);
   note_launch();
-  gram_reduce_kernel<<<ceil_div(l * l, 256), 256, 0, s>>>(l, used, P, G, Gf, gate, skip);
+  const dim3 rgrid(ceil_div(l, GR_C), ceil_div(l, GR_R));
+  if (sizeof(T) == 4)
+    gram_reduce_kernel<float2><<<rgrid, GR_R * GR_C, 0, s>>>(l, used, reinterpret_cast<const float2*>(P), G, Gf,
+                                                             gate, skip);
+  else
+    gram_reduce_kernel<double><<<rgrid, GR_R * GR_C, 0, s>>>(l, used, P, G, Gf, gate, skip);
   note_launch();
 }
 
@@ -915,7 +1037,7 @@ void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const i
 // ------------------------------------------------------- orth entry points --
 size_t orth_workspace_bytes(int rows, int l, int sms, size_t csize) {
   Carver c(nullptr);
-  c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);  // Gram partials
+  c.take<double>((size_t)gram_splits(rows, l, sms, csize) * l * l);  // Gram partials
   c.take<double>((size_t)l * l);                              // G
   c.take<float>((size_t)l * l);                               // Gf
   c.take<unsigned char>((size_t)l * l * csize);               // Ub
@@ -929,7 +1051,7 @@ template <typename T, typename C>
 void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
               DevStatus* st, int sms, cudaStream_t s, const int* skip) {
   Carver c(ws);
-  double* P = c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
+  double* P = c.take<double>((size_t)gram_splits(rows, l, sms, sizeof(T)) * l * l);
   double* G = c.take<double>((size_t)l * l);
   float* Gf = c.take<float>((size_t)l * l);
   C* Ub = c.take<C>((size_t)l * l);
@@ -965,8 +1087,7 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
 // with every block it needs staged in shared memory first (L_ik for
 // j <= k < i, X_ii for i >= j), and writes block row j of M:
 // M(32 j + r, 32 i + c) = W_ij(c, r) / d_(32 j + r).  One CTA per block column
-// spreads what the single-CTA factorization would do serially; each 32 x 32
-// product is 512 threads x two outputs.
+// spreads what the single-CTA factorization would do serially.
 constexpr int INV_THREADS = 512;
 
 __global__ void __launch_bounds__(INV_THREADS)
@@ -1042,38 +1163,60 @@ __global__ void __launch_bounds__(INV_THREADS)
     }
   }
   __syncthreads();
-  const int r = tid >> 4, c = (tid & 15) * 2;  // this thread's two outputs (r, c), (r, c + 1)
-  // W_jj = X_jj
-  Wc[r * CP + c] = Xd[r * CP + c];
-  Wc[r * CP + c + 1] = Xd[r * CP + c + 1];
+  // Right-looking: once W_kj is final, every T_i = sum_k L_ik W_kj (i > k)
+  // takes its term at once, and W_(k+1) j = -X_(k+1)(k+1) T_(k+1) follows.
+  //   T_i += L_ik W_kj: one product per 64 threads, each thread a 4 x 4 tile
+  //                     (8 shared-memory loads per 16 FMAs);
+  //   W = -X T:         all 512 threads, two outputs each.
+  for (int e = tid; e < CBS; e += INV_THREADS) Wc[e] = Xd[e];  // W_jj = X_jj
+  for (int e = tid; e < (nw - 1) * CBS; e += INV_THREADS) Tb[e] = 0.f;
   __syncthreads();
-  for (int i = j + 1; i < NB; ++i) {
-    // T = sum_k L_ik W_kj
-    float t0 = 0.f, t1 = 0.f;
-    for (int k = j; k < i; ++k) {
-      const float* Lk = Lb + (size_t)lidx(i, k) * CBS + r * CP;
-      const float* Wk = Wc + (size_t)(k - j) * CBS + c;
+  const int pp = tid >> 6, sub = tid & 63, tr = (sub >> 3) * 4, tc = (sub & 7) * 4;
+  const int r = tid >> 4, c = (tid & 15) * 2;
+  for (int k = j; k < NB - 1; ++k) {
+    const int i = k + 1 + pp;  // this thread's product, T_i += L_ik W_kj
+    if (i < NB) {
+      const float* Lk = Lb + (size_t)lidx(i, k) * CBS;
+      const float* Wk = Wc + (size_t)(k - j) * CBS;
+      float* Ti = Tb + (size_t)(i - j - 1) * CBS;
+      float acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = Ti[(tr + x) * CP + tc + y];
+#pragma unroll 8
+      for (int t = 0; t < CBK; ++t) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) av[x] = Lk[(tr + x) * CP + t];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) bv[y] = Wk[t * CP + tc + y];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) Ti[(tr + x) * CP + tc + y] = acc[x][y];
+    }
+    __syncthreads();
+    // W_(k+1) j = -X_(k+1)(k+1) T_(k+1)
+    {
+      const float* Xi = Xd + (size_t)(k + 1 - j) * CBS + r * CP;
+      const float* Tk = Tb + (size_t)(k - j) * CBS;
+      float w0 = 0.f, w1 = 0.f;
 #pragma unroll 8
       for (int u = 0; u < CBK; ++u) {
-        const float a = Lk[u];
-        t0 = fmaf(a, Wk[u * CP], t0);
-        t1 = fmaf(a, Wk[u * CP + 1], t1);
+        const float xa = Xi[u];
+        w0 = fmaf(xa, Tk[u * CP + c], w0);
+        w1 = fmaf(xa, Tk[u * CP + c + 1], w1);
       }
+      float* Wn = Wc + (size_t)(k + 1 - j) * CBS + r * CP + c;
+      Wn[0] = -w0;
+      Wn[1] = -w1;
     }
-    Tb[r * CP + c] = t0;
-    Tb[r * CP + c + 1] = t1;
-    __syncthreads();
-    // W_ij = -X_ii T
-    const float* Xi = Xd + (size_t)(i - j) * CBS + r * CP;
-    float w0 = 0.f, w1 = 0.f;
-#pragma unroll 8
-    for (int u = 0; u < CBK; ++u) {
-      const float a = Xi[u];
-      w0 = fmaf(a, Tb[u * CP + c], w0);
-      w1 = fmaf(a, Tb[u * CP + c + 1], w1);
-    }
-    Wc[(size_t)(i - j) * CBS + r * CP + c] = -w0;
-    Wc[(size_t)(i - j) * CBS + r * CP + c + 1] = -w1;
     __syncthreads();
   }
   // block row j of M: M(32 j + rr, col) = W(col, 32 j + rr) / d_(32 j + rr) for
@@ -1094,7 +1237,7 @@ __global__ void __launch_bounds__(INV_THREADS)
 size_t inv_tri_smem_bytes(int l) {
   const int NB = (l + CBK - 1) / CBK;
   const size_t nw = NB, nl = (size_t)NB * (NB - 1) / 2;
-  return (2 * nw + nl + 1) * CBS * sizeof(float);
+  return (2 * nw + nl + (nw - 1)) * CBS * sizeof(float);  // W, X, L, T
 }
 
 void launch_inv_tri(int l, const float* Ub, const float* dinv, float* M, const int* gate, cudaStream_t s) {
@@ -1138,7 +1281,7 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
   float* part = c0.take<float>(tc_gemm_workspace(rows, l, l, sms) / sizeof(float) + 1);
   float* Minv = c0.take<float>((size_t)l * l);
   Carver c(base);
-  double* P = c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
+  double* P = c.take<double>((size_t)gram_splits(rows, l, sms, 4) * l * l);
   double* G = c.take<double>((size_t)l * l);
   float* Gf = c.take<float>((size_t)l * l);
   float* M = c.take<float>((size_t)l * l);
@@ -1189,7 +1332,7 @@ template <typename T, typename C>
 void run_chol_solve(int rows, int l, const T* B, int ldb, T* Y, int ldy, void* ws, DevStatus* st, int sms,
                     cudaStream_t s) {
   Carver c(ws);
-  c.take<double>((size_t)gram_splits(rows, l, sms) * l * l);
+  c.take<double>((size_t)gram_splits(rows, l, sms, sizeof(T)) * l * l);
   double* G = c.take<double>((size_t)l * l);
   float* Gf = c.take<float>((size_t)l * l);
   C* Ub = c.take<C>((size_t)l * l);

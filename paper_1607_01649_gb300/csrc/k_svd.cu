@@ -506,33 +506,72 @@ __global__ void colmax_partial_kernel(int n, int kk, const T* __restrict__ V, in
   pidx[(size_t)blockIdx.x * kk + c] = bi;
 }
 
+// Pass 2, one CTA per column: the CTA reduces the chunk maxima in parallel
+// (ties to the lowest row), decides the column's sign, flips Wsel's column and
+// records the decision in flip[c]; colflip_kernel then flips V with row-wise
+// (coalesced) accesses.
 template <typename T, typename C>
-__global__ void colsign_kernel(int n, int kk, int chunks, const float* __restrict__ pmax, const int* __restrict__ pidx,
-                               T* __restrict__ V, int ldv, C* __restrict__ Wsel, int l) {
+__global__ void __launch_bounds__(256)
+    colsign_kernel(int n, int kk, int chunks, const float* __restrict__ pmax, const int* __restrict__ pidx,
+                   const T* __restrict__ V, int ldv, C* __restrict__ Wsel, int l, int* __restrict__ flip) {
   const int c = blockIdx.x;
+  __shared__ float s_b[8];
+  __shared__ int s_i[8];
   __shared__ int s_flip;
-  if (threadIdx.x == 0) {
-    float best = -1.f;
-    int bi = 0x7fffffff;
-    for (int z = 0; z < chunks; ++z) {
-      const float b = pmax[(size_t)z * kk + c];
-      const int i = pidx[(size_t)z * kk + c];
-      if (b > best || (b == best && i < bi)) {
-        best = b;
-        bi = i;
-      }
+  float best = -1.f;
+  int bi = 0x7fffffff;
+  for (int z = threadIdx.x; z < chunks; z += blockDim.x) {
+    const float b = pmax[(size_t)z * kk + c];
+    const int i = pidx[(size_t)z * kk + c];
+    if (b > best || (b == best && i < bi)) {
+      best = b;
+      bi = i;
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float b = __shfl_down_sync(0xffffffffu, best, o);
+    const int i = __shfl_down_sync(0xffffffffu, bi, o);
+    if (b > best || (b == best && i < bi)) {
+      best = b;
+      bi = i;
+    }
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    s_b[warp] = best;
+    s_i[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+      if (s_b[w] > best || (s_b[w] == best && s_i[w] < bi)) {
+        best = s_b[w];
+        bi = s_i[w];
+      }
     s_flip = (bi < n && V[(size_t)bi * ldv + c] < T(0)) ? 1 : 0;
+    flip[c] = s_flip;
   }
   __syncthreads();
   if (!s_flip) return;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)i * ldv + c] = -V[(size_t)i * ldv + c];
   for (int i = threadIdx.x; i < l; i += blockDim.x) Wsel[(size_t)i * kk + c] = -Wsel[(size_t)i * kk + c];
+}
+
+// Pass 2b: V(i, c) = -V(i, c) for the flipped columns, rows walked with the
+// columns fastest.
+template <typename T>
+__global__ void colflip_kernel(int n, int kk, T* __restrict__ V, int ldv, const int* __restrict__ flip) {
+  const long long total = (long long)n * kk;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / kk), c = (int)(e % kk);
+    if (flip[c]) V[(size_t)i * ldv + c] = -V[(size_t)i * ldv + c];
+  }
 }
 
 size_t sign_workspace_bytes(int n, int kk) {
   const int chunks = (n + 255) / 256;
-  return (size_t)chunks * kk * (sizeof(float) + sizeof(int)) + 512;
+  return (size_t)chunks * kk * (sizeof(float) + sizeof(int)) + (size_t)kk * sizeof(int) + 1024;
 }
 
 template <typename T, typename C>
@@ -541,12 +580,19 @@ void launch_sign_fix(int n, int kk, int l, T* V, int ldv, C* Wsel, void* ws, cud
   const int rows_per = 256;
   const int chunks = (n + rows_per - 1) / rows_per;
   float* pmax = (float*)ws;
-  int* pidx = (int*)((char*)ws + (((size_t)chunks * kk * sizeof(float) + 255) & ~(size_t)255));
+  const size_t off_i = ((size_t)chunks * kk * sizeof(float) + 255) & ~(size_t)255;
+  int* pidx = (int*)((char*)ws + off_i);
+  int* flip = (int*)((char*)ws + ((off_i + (size_t)chunks * kk * sizeof(int) + 255) & ~(size_t)255));
   const int tx = kk >= 128 ? 128 : 64;
   dim3 grid(chunks, (kk + tx - 1) / tx);
   colmax_partial_kernel<T><<<grid, tx, 0, s>>>(n, kk, V, ldv, rows_per, pmax, pidx);
   note_launch();
-  colsign_kernel<T, C><<<kk, 256, 0, s>>>(n, kk, chunks, pmax, pidx, V, ldv, Wsel, l);
+  colsign_kernel<T, C><<<kk, 256, 0, s>>>(n, kk, chunks, pmax, pidx, V, ldv, Wsel, l, flip);
+  note_launch();
+  const long long total = (long long)n * kk;
+  const long long want = (total + 4 * 256 - 1) / (4 * 256);
+  const int blocks = (int)(want < 4096 ? want : 4096);
+  colflip_kernel<T><<<blocks, 256, 0, s>>>(n, kk, V, ldv, flip);
   note_launch();
 }
 template void launch_sign_fix<float, float>(int, int, int, float*, int, float*, void*, cudaStream_t);

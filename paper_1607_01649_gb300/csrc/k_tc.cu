@@ -638,39 +638,57 @@ __global__ void split_bf16_kernel(int rows, int cols, const float* __restrict__ 
   }
 }
 
-// Vectorized variant for cols % 4 == 0, lda % 4 == 0, ldb % 4 == 0.
+// Vectorized variant for cols % 4 == 0, lda % 4 == 0, ldb % 4 == 0.  Each
+// thread walks four interleaved grid-stride streams of float4 groups, so four
+// 16-byte loads are in flight per thread; a stream's (row, column) advances by
+// whole rows per stride, so no 64-bit division runs per element.
+__device__ __forceinline__ void split4_store(float4 a, __nv_bfloat16* Ah, __nv_bfloat16* Al, size_t off) {
+  __nv_bfloat162 h01 = __floats2bfloat162_rn(a.x, a.y), h23 = __floats2bfloat162_rn(a.z, a.w);
+  uint2 hv;
+  hv.x = *reinterpret_cast<uint32_t*>(&h01);
+  hv.y = *reinterpret_cast<uint32_t*>(&h23);
+  *reinterpret_cast<uint2*>(Ah + off) = hv;
+  if (Al) {
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    __nv_bfloat162 l01 = __floats2bfloat162_rn(a.x - f01.x, a.y - f01.y);
+    __nv_bfloat162 l23 = __floats2bfloat162_rn(a.z - f23.x, a.w - f23.y);
+    uint2 lv;
+    lv.x = *reinterpret_cast<uint32_t*>(&l01);
+    lv.y = *reinterpret_cast<uint32_t*>(&l23);
+    *reinterpret_cast<uint2*>(Al + off) = lv;
+  }
+}
+
 __global__ void split_bf16_vec_kernel(int rows, int cols, const float* __restrict__ A, int lda,
                                       __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al, int ldb) {
+  constexpr int U = 4;
   const int c4 = cols / 4;
   const long long total = (long long)rows * c4;
-  // row-major walk: the row index advances by whole rows per grid stride, so
-  // no 64-bit division runs per element
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;  // one stream's step is U strides
   const long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int r = (int)(e0 / c4), c = (int)(e0 % c4);
-  const int dr = (int)(stride / c4), dc = (int)(stride % c4);
-  for (long long e = e0; e < total; e += stride) {
-    const int cc = c * 4;
-    const float4 a = *reinterpret_cast<const float4*>(A + (size_t)r * lda + cc);
-    __nv_bfloat162 h01 = __floats2bfloat162_rn(a.x, a.y), h23 = __floats2bfloat162_rn(a.z, a.w);
-    uint2 hv;
-    hv.x = *reinterpret_cast<uint32_t*>(&h01);
-    hv.y = *reinterpret_cast<uint32_t*>(&h23);
-    *reinterpret_cast<uint2*>(Ah + (size_t)r * ldb + cc) = hv;
-    if (Al) {
-      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-      __nv_bfloat162 l01 = __floats2bfloat162_rn(a.x - f01.x, a.y - f01.y);
-      __nv_bfloat162 l23 = __floats2bfloat162_rn(a.z - f23.x, a.w - f23.y);
-      uint2 lv;
-      lv.x = *reinterpret_cast<uint32_t*>(&l01);
-      lv.y = *reinterpret_cast<uint32_t*>(&l23);
-      *reinterpret_cast<uint2*>(Al + (size_t)r * ldb + cc) = lv;
-    }
-    r += dr;
-    c += dc;
-    if (c >= c4) {
-      c -= c4;
-      ++r;
+  int r[U], c[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long long e = e0 + u * stride;
+    r[u] = (int)(e / c4);
+    c[u] = (int)(e % c4);
+  }
+  const long long step = U * stride;
+  const int dr = (int)(step / c4), dc = (int)(step % c4);
+  for (long long e = e0; e < total; e += step) {
+    float4 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e + u * stride < total) a[u] = *reinterpret_cast<const float4*>(A + (size_t)r[u] * lda + 4 * c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (e + u * stride < total) split4_store(a[u], Ah, Al, (size_t)r[u] * ldb + 4 * c[u]);
+      r[u] += dr;
+      c[u] += dc;
+      if (c[u] >= c4) {
+        c[u] -= c4;
+        ++r[u];
+      }
     }
   }
 }

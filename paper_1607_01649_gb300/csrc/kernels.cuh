@@ -19,7 +19,7 @@ void launch_gemm_simt(bool trans, int M, int N, int K, const T* A, int lda, cons
                       T* partial, int sms, cudaStream_t s);
 
 // k_orth.cu
-int gram_splits(int rows, int l, int sms);
+int gram_splits(int rows, int l, int sms, size_t tsize);
 template <typename T>
 void launch_gram(int rows, int l, const T* Y, int ldy, double* P, double* G, float* Gf, int sms, const int* gate,
                  cudaStream_t s, const int* skip = nullptr, __nv_bfloat16* Yh = nullptr, __nv_bfloat16* Yl = nullptr,

@@ -885,7 +885,7 @@ CtrlLayout ctrl_layout(void* ws, int m, int n, int R, int sms, size_t rest_bytes
   L.Yp = c.take<float>((size_t)thin_splits(m, n, sms) * m * CTRL_NC);
   L.Y = c.take<float>((size_t)m * CTRL_NC);
   L.fro2p = c.take<double>((size_t)ceil_div(m, 128) * thin_splits(m, n, sms));
-  L.P = c.take<double>((size_t)gram_splits(m, CTRL_NC, sms) * CTRL_NC * CTRL_NC);
+  L.P = c.take<double>((size_t)gram_splits(m, CTRL_NC, sms, 4) * CTRL_NC * CTRL_NC);
   L.Gram = c.take<double>(CTRL_NC * CTRL_NC);
   L.T = c.take<float>((size_t)R * CTRL_NC);
   L.Tpart = c.take<float>(simt_gemm_workspace(R, CTRL_NC, n, sms, 4) / 4 + 1);

@@ -21,7 +21,9 @@ struct DevStatus {
   int rank;         // adaptive: current rank
   int done;         // adaptive: tolerance met / loop finished
   int shift_count;  // Cholesky factorizations that needed a diagonal shift
-  int pad;
+  int run2;         // orth: an intermediate basis needs its second CholeskyQR pass
+                    // (0: the first pass already gives a basis within the
+                    // acceptance bound, which is kept)
   double fro2_a;    // adaptive: ||A||_Fro^2
   double fro2_res;  // adaptive: ||A_j||_Fro^2 of the current remainder
   double scratch[6];

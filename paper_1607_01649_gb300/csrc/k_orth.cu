@@ -628,7 +628,7 @@ template <typename C, int NT>
 __global__ void __launch_bounds__(NT)
     chol_kernel(int l, const double* __restrict__ G, const float* __restrict__ Gf, C* __restrict__ Ub,
                 C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate,
-                const int* skip) {
+                const int* skip, float accept) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = (l + CBK - 1) / CBK;
@@ -731,6 +731,31 @@ __global__ void __launch_bounds__(NT)
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
+    if (accept > 0.f && attempt == 0) {
+      // acceptance test of an intermediate basis (the previous pass's Q): its
+      // Gram, scaled to unit diagonal, within accept of I entry by entry
+      // (so ||Gt - I||_2 <= (l - 1) accept) and its column norms squared
+      // within [1/2, 3/2]; then Q is kept and this pass does nothing more
+      float mx = 0.f;
+      for (int e = tid; e < nblk * CBK * CBK; e += NT) {
+        const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+        const int i = CBK * s_bi[b] + r, j = CBK * s_bj[b] + c;
+        if (i < l && j < l && i != j) mx = fmaxf(mx, fabsf((float)Ls[(size_t)b * CBS + r * CP + c]));
+      }
+      for (int i = tid; i < l; i += NT) mx = fmaxf(mx, fabsf((float)(d[i] * d[i]) - 1.f) * (2.f * accept));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&s_fail), __float_as_uint(mx));
+      __syncthreads();
+      const bool keep = __uint_as_float((unsigned)s_fail) <= accept;
+      __syncthreads();
+      if (tid == 0) {
+        st->run2 = keep ? 0 : 1;
+        s_fail = 0;
+      }
+      __syncthreads();
+      if (keep) return;
+    }
     if (warp == 0) diag_potrf<C>(Ls, rdg, 0, ctau, &s_fail);
     __syncthreads();
     if (s_fail == 0) {
@@ -999,7 +1024,7 @@ void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __
 
 template <typename C>
 void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
-                 const int* gate, cudaStream_t s, const int* skip) {
+                 const int* gate, cudaStream_t s, const int* skip, float accept = 0.f) {
   // binary32: 512 threads (at most 128 registers each; a diagonal-block warp
   // keeps a row of L and a row of its inverse in registers); binary64
   // (l <= 128): 256
@@ -1007,7 +1032,7 @@ void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double
   const size_t smem = chol_smem_bytes(l, sizeof(C));
   auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip);
+  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip, accept);
   note_launch();
 }
 
@@ -1266,7 +1291,8 @@ size_t orth_tc_workspace_bytes(int rows, int l, int sms) {
 bool orth_tc_pays(int rows, int l) { return (long long)rows >= 64LL * l; }
 
 void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
-                 DevStatus* st, int sms, cudaStream_t s) {
+                 DevStatus* st, int sms, cudaStream_t s, bool intermediate) {
+  intermediate = intermediate && !Rout;  // R needs every pass
   if (!orth_tc_pays(rows, l)) {
     run_orth<float, float>(rows, l, Y, ldy, Rout, Ybf, lb, ws, st, sms, s);
     return;
@@ -1289,20 +1315,27 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
   double* Rp = c.take<double>((size_t)3 * l * l);
   double* Rm = c.take<double>((size_t)2 * l * l);
   const int* gate3 = &st->shifted;
-  for (int pass = 1; pass <= 3; ++pass) {
+  const int* run2 = &st->run2;
+  // an intermediate basis: the second pass's Gram decides whether the first
+  // pass's Q is kept (entries of the unit-diagonal Gram within 1/(2 (l - 1))
+  // of I, so ||Gt - I||_2 <= 1/2; column norms squared within [1/2, 3/2])
+  const float accept = l > 1 ? 0.5f / (float)(l - 1) : 0.f;
+  for (int pass = 1; pass <= (intermediate ? 2 : 3); ++pass) {
     const int* gate = pass == 3 ? gate3 : nullptr;
+    const int* gate_rest = (intermediate && pass == 2) ? run2 : gate;
     // the Gram kernel also writes the bf16 pair Yh + Yl of Y
     launch_gram<float>(rows, l, Y, ldy, P, G, Gf, sms, gate, s, nullptr, Yh, Yl, l8);
     // the factor in its blocked form (M's slot holds it), then R^-1 by block
     // columns on NB SMs
     launch_chol<float>(l, G, Gf, M, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s,
-                       nullptr);
-    launch_inv_tri(l, M, dinv, Minv, gate, s);
-    // pass 3 runs only if pass 1 needed a shift (a device-side gate): the
-    // product then returns at once and leaves Y alone (the split of M only
+                       nullptr, (intermediate && pass == 2 && !Rout) ? accept : 0.f);
+    launch_inv_tri(l, M, dinv, Minv, gate_rest, s);
+    // pass 3 runs only if pass 1 needed a shift (a device-side gate), the
+    // second pass of an intermediate basis only if its Q failed the test: a
+    // gated product returns at once and leaves Y alone (the split of M only
     // fills scratch)
     launch_split_bf16(l, l, Minv, l, Mh, Ml, l8, sms, s);
-    launch_tc_gemm(false, true, rows, l, l, Yh, l8, Yl, Mh, l8, Ml, Y, ldy, part, sms, st, s, 128, gate);
+    launch_tc_gemm(false, true, rows, l, l, Yh, l8, Yl, Mh, l8, Ml, Y, ldy, part, sms, st, s, 128, gate_rest);
   }
   if (Ybf) launch_copy_bf16<float>(rows, l, Y, ldy, Ybf, lb, s);
   if (Rout) {

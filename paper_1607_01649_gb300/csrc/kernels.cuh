@@ -38,8 +38,12 @@ void run_chol_solve(int rows, int l, const T* B, int ldb, T* Y, int ldy, void* w
                     cudaStream_t s);
 // CholeskyQR2 with the apply Q = Y R^-1 on tensor cores (three-term split bf16); binary32 data
 size_t orth_tc_workspace_bytes(int rows, int l, int sms);
+// intermediate: Y is a power-iteration basis whose span alone is used next;
+// the second pass is skipped when the first already gives a basis with
+// ||Q^T Q - I||_2 <= 1/2 (checked on the second pass's Gram), and no third
+// pass runs.
 void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, int lb, void* ws,
-                 DevStatus* st, int sms, cudaStream_t s);
+                 DevStatus* st, int sms, cudaStream_t s, bool intermediate = false);
 void launch_triu_mm(int l, const double* A, const double* B, double* Cm, const int* gate, int copy_if_gated,
                     cudaStream_t s, const int* skip = nullptr);
 

@@ -387,7 +387,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
       return st;
   }
   if (cb) centre_forward<float, __nv_bfloat16>(m, n, l, L.Omb, l8, L.Y, l, *cb, sms, s);
-  run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
+  run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s, p->q > 0);
   // power steps
   for (int j = 0; j < p->q; ++j) {
     {
@@ -397,7 +397,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
         return st;
     }
     if (cb) centre_adjoint<float, __nv_bfloat16>(m, n, l, L.Yb, l8, L.Z, l, *cb, sms, s);
-    run_orth_tc(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s);
+    run_orth_tc(n, l, L.Z, l, nullptr, L.Zb, l8, L.orthws, L.st, sms, s, true);
     {
       ProfScope ps(h, 0, s);
       if ((st = tc_call(h, launch_tc_gemm(false, false, m, l, n, L.Ah, n8, nullptr, L.Zb, l8, nullptr, L.Y, l,
@@ -405,7 +405,7 @@ rsvd_status fixed_rank_mixed(rsvd_handle_t h, int m, int n, const float* A, int 
         return st;
     }
     if (cb) centre_forward<float, __nv_bfloat16>(m, n, l, L.Zb, l8, L.Y, l, *cb, sms, s);
-    run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s);
+    run_orth_tc(m, l, L.Y, l, nullptr, L.Yb, l8, L.orthws, L.st, sms, s, j + 1 < p->q);
   }
   // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
   launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);
@@ -521,7 +521,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
       return st;
   }
   if (cb) centre_forward<float, float>(m, n, l, E.Om, l, L.Y, l, *cb, sms, s);
-  run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+  run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s, p->q > 0);
   for (int j = 0; j < p->q; ++j) {
     // Z = A^T Q = A8^T (S Q)
     launch_fp8_cols(m, l, L.Y, l, E.s, E.X8t, m16, E.cvec, E.colws, s);
@@ -532,7 +532,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
         return st;
     }
     if (cb) centre_adjoint<float, float>(m, n, l, L.Y, l, L.Z, l, *cb, sms, s);
-    run_orth_tc(n, l, L.Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    run_orth_tc(n, l, L.Z, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s, true);
     launch_fp8_cols(n, l, L.Z, l, nullptr, E.X8t, n16, E.cvec, E.colws, s);
     {
       ProfScope ps(h, 0, s);
@@ -541,7 +541,7 @@ rsvd_status fixed_rank_fp8(rsvd_handle_t h, int m, int n, const float* A, int ld
         return st;
     }
     if (cb) centre_forward<float, float>(m, n, l, L.Z, l, L.Y, l, *cb, sms, s);
-    run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s);
+    run_orth_tc(m, l, L.Y, l, nullptr, nullptr, 0, L.orthws, L.st, sms, s, j + 1 < p->q);
   }
   // B^T = A^T Q as Ah^T Qh + Ah^T Ql + Al^T Qh
   launch_split_bf16(m, l, L.Y, l, L.Yb, L.Yl, l8, sms, s);

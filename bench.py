@@ -488,6 +488,13 @@ def run_ours(a):
 
     res_rel, fro_a = fro_rel(U, D, V)
     spec_rel, spec_conv, spec_a = spectral_rel(U, D, V)
+
+    def orth_err(X):
+        # max |X^T X - I| in float64
+        X64 = X.double()
+        return float((X64.T @ X64 - torch.eye(X64.shape[1], dtype=torch.float64, device=dev)).abs().max())
+
+    orth = {"max_abs(U^T U - I)": orth_err(U), "max_abs(V^T V - I)": orth_err(V)}
     if a.workload == "pca":
         # the signal's singular values (the noise moves them by about its norm)
         sig_true = torch.linspace(100.0, 1.0, 64, dtype=torch.float64, device=dev)[:k]
@@ -496,7 +503,7 @@ def run_ours(a):
         err = {"max_rel_err_sigma_1..48_vs_signal": d_rel, "fro_residual_rel": res_rel,
                "noise_floor_rel": 1e-3 * (m * n) ** 0.5 / fro_a,
                "spectral_residual_rel": spec_rel, "spectral_estimate_last_rel_change": spec_conv,
-               "sigma_k+1_rel(noise, sqrt(m)+sqrt(n) times 1e-3)": 1e-3 * (m ** 0.5 + n ** 0.5) / spec_a}
+               "sigma_k+1_rel(noise, sqrt(m)+sqrt(n) times 1e-3)": 1e-3 * (m ** 0.5 + n ** 0.5) / spec_a, **orth}
     else:
         sig_true = torch.arange(1, k + 1, dtype=torch.float64, device=dev).pow(-1.5)
         d_rel = float(((D - sig_true).abs() / sig_true).max())
@@ -504,7 +511,7 @@ def run_ours(a):
         err = {"max_rel_err_sigma_1..k_vs_construction": d_rel, "fro_residual_rel": res_rel,
                "fro_residual_optimal_rel(Eckart-Young)": fro_opt / fro_a,
                "spectral_residual_rel": spec_rel, "spectral_estimate_last_rel_change": spec_conv,
-               "sigma_k+1_rel(Eckart-Young)": (k + 1) ** -1.5}
+               "sigma_k+1_rel(Eckart-Young)": (k + 1) ** -1.5, **orth}
 
     # ---- roofline of the dominant kernel: the tcgen05 sketch product
     roof = None

@@ -11,12 +11,15 @@
 // The Jacobi runs in one thread-block cluster of NC CTAs.  The 2 NC column
 // blocks (w columns each) follow a round-robin tournament; in every round a
 // CTA sweeps all column pairs of the two blocks it holds (one warp per pair),
-// then each CTA pulls the two blocks it needs next from the CTAs that hold
-// them, through distributed shared memory.
+// then each CTA pushes its two blocks to the CTAs that need them next: one
+// bulk copy per block from its shared memory into the receiver's, signalled
+// on the receiver's mbarrier (one barrier per buffer parity), and one cluster
+// barrier per round.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "sm100.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(512)
   const size_t blk = (size_t)2 * w * cs;  // X then J, w columns each
   __shared__ int s_rot;
   __shared__ int s_total;
+  __shared__ __align__(8) uint64_t in_bar[2];  // incoming blocks, by buffer parity
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int nwarps = blockDim.x / 32;
   const double tol = 16.0 * sqrt((double)l) * JacobiTol<C>::u;
@@ -167,8 +171,18 @@ __global__ void __launch_bounds__(512)
   };
   load_block(buf + 0 * blk, rr_pos(me, 0, P));
   load_block(buf + 1 * blk, rr_pos(P - 1 - me, 0, P));
-  if (tid == 0) s_total = 0;
-  __syncthreads();
+  if (tid == 0) {
+    s_total = 0;
+    sm100::mbar_init(&in_bar[0], 1);
+    sm100::mbar_init(&in_bar[1], 1);
+    sm100::fence_mbar_init();
+  }
+  uint32_t in_phase = 0u;  // bit b: phase parity of in_bar[b]
+  bool timed_out = false;
+  const uint32_t blk_bytes = (uint32_t)(blk * sizeof(C));
+  // every CTA's barriers exist before any block is pushed
+  if (P > 2) cluster.sync();
+  else __syncthreads();
 
   int sweep = 0;
   bool converged = false;
@@ -268,38 +282,41 @@ __global__ void __launch_bounds__(512)
         }
         __syncthreads();
       }
-      // ---- exchange: pull the blocks needed in the next round
+      // ---- exchange: push both blocks to the CTAs that hold them in the
+      // next round (buffer parity par ^ 1 there).  Receivers' buffers of that
+      // parity are free: their previous contents went out in the last round,
+      // whose reads completed before the last cluster barrier.
       if (P > 2) {
-        cluster.sync();
-        const int rn = r + 1;  // next round index within the tournament (mod P-1)
         const int npar = par ^ 1;
-        C* ntop = buf + (size_t)(2 * npar) * blk;
-        C* nbot = buf + (size_t)(2 * npar + 1) * blk;
-        for (int half = 0; half < 2; ++half) {
-          const int pos_next = half == 0 ? me : P - 1 - me;
-          const int player = rr_pos(pos_next, rn % (P - 1), P);
-          const int pos_now = rr_where(player, r, P);
-          const int holder = pos_now < NC ? pos_now : P - 1 - pos_now;
-          const int slot = pos_now < NC ? 0 : 1;
-          C* src = cluster.map_shared_rank(buf + (size_t)(2 * par + slot) * blk, holder);
-          C* dst = half == 0 ? ntop : nbot;
-          // 16-byte remote loads, four in flight per thread
-          const size_t nv = blk * sizeof(C) / 16;
-          const float4* s4 = reinterpret_cast<const float4*>(src);
-          float4* d4 = reinterpret_cast<float4*>(dst);
-          size_t e = tid;
-          for (; e + 3 * blockDim.x < nv; e += 4 * blockDim.x) {
-            const float4 v0 = s4[e], v1 = s4[e + blockDim.x], v2 = s4[e + 2 * blockDim.x],
-                         v3 = s4[e + 3 * blockDim.x];
-            d4[e] = v0;
-            d4[e + blockDim.x] = v1;
-            d4[e + 2 * blockDim.x] = v2;
-            d4[e + 3 * blockDim.x] = v3;
+        if (tid == 0) {
+          sm100::fence_proxy_async_smem();  // the steps' stores, visible to the copy engine
+          const int rn = (r + 1) % (P - 1);
+          for (int half = 0; half < 2; ++half) {
+            const int player = rr_pos(half == 0 ? me : P - 1 - me, r, P);
+            const int pos_next = rr_where(player, rn, P);
+            const int holder = pos_next < NC ? pos_next : P - 1 - pos_next;
+            const int slot = pos_next < NC ? 0 : 1;
+            const uint32_t src = sm100::smem_u32(buf + (size_t)(2 * par + half) * blk);
+            const uint32_t dst_l = sm100::smem_u32(buf + (size_t)(2 * npar + slot) * blk);
+            const uint32_t bar_l = sm100::smem_u32(&in_bar[npar]);
+            uint32_t dst, bar;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst) : "r"(dst_l), "r"(holder));
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(bar) : "r"(bar_l), "r"(holder));
+            asm volatile(
+                "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"(dst), "r"(src), "r"(blk_bytes), "r"(bar) : "memory");
           }
-          for (; e < nv; e += blockDim.x) d4[e] = s4[e];
-          for (size_t x = nv * 16 / sizeof(C) + tid; x < blk; x += blockDim.x) dst[x] = src[x];
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          // two blocks arrive here for the next round
+          sm100::mbar_arrive_expect_tx(&in_bar[npar], 2u * blk_bytes);
+          // this round's blocks may be overwritten once read
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
         cluster.sync();
+        // bounded wait (2 s); after a timeout the kernel runs on without
+        // waiting again and reports RSVD_E_TIMEOUT
+        if (!timed_out && !sm100::mbar_wait(&in_bar[npar], (in_phase >> npar) & 1u)) timed_out = true;
+        in_phase ^= 1u << npar;
       } else {
         // single CTA: same two blocks; move them to the other buffer pair
         const int npar = par ^ 1;
@@ -321,6 +338,7 @@ __global__ void __launch_bounds__(512)
     converged = (total == 0);
   }
   if (me == 0 && tid == 0) st->jacobi_sweeps = sweep;
+  if (timed_out && lane == 0) set_status(st, RSVD_E_TIMEOUT);
 
   // ---- outputs: after the last round the blocks sit in the buffer pair of
   // parity (sweeps * (P-1)) & 1, at round 0 positions of the tournament

@@ -477,6 +477,11 @@ struct Eps<double> {
 constexpr int CBK = 32;             // block size
 constexpr int CP = 33;              // padded row stride within a block
 constexpr int CBS = CBK * CP;       // stored entries per block
+// The latest diagonal block's factor transposed (row q = column q of L), row
+// stride LTP, with 32 entries of slack after the last row: the panel
+// substitution reads row q from column q + 1 on at fixed offsets.
+constexpr int LTP = 33;
+constexpr int LT_ENTRIES = CBK * LTP + 32;
 
 __device__ __forceinline__ int lblk(int bi, int bj) { return bi * (bi + 1) / 2 + bj; }
 
@@ -493,7 +498,7 @@ __device__ __forceinline__ int lblk(int bi, int bj) { return bi * (bi + 1) / 2 +
 // than the shuffles it saved.  Returns false (warp-uniformly: the pivot is a
 // shuffled value) on a pivot below tau.
 template <typename C, int J>
-__device__ __forceinline__ bool chol_steps(C (&row)[32], int q0, int q1, C tau, C* Li, C* dii) {
+__device__ __forceinline__ bool chol_steps(C (&row)[32], int q0, int q1, C tau, C* Li, C* dii, C* LT) {
   const int lane = threadIdx.x % 32;
 #pragma unroll 1
   for (int q = q0; q < q1; ++q) {
@@ -502,6 +507,7 @@ __device__ __forceinline__ bool chol_steps(C (&row)[32], int q0, int q1, C tau, 
     const C rp = rsqrt(akk), piv = akk * rp;
     const C liq = (lane == q) ? piv : (lane > q ? row[0] * rp : C(0));
     Li[q] = liq;
+    LT[q * LTP + lane] = liq;  // column q of L as row q of its transpose
     if (lane == q) *dii = piv;
     // row i -= l(i, q) * l(j, q) for q < j <= i, shifted down one column
 #pragma unroll
@@ -514,9 +520,9 @@ __device__ __forceinline__ bool chol_steps(C (&row)[32], int q0, int q1, C tau, 
 }
 
 template <typename C>
-__device__ __forceinline__ bool warp_chol32(C (&row)[32], C tau, C* Li, C* dii) {
-  return chol_steps<C, 31>(row, 0, 8, tau, Li, dii) && chol_steps<C, 23>(row, 8, 16, tau, Li, dii) &&
-         chol_steps<C, 15>(row, 16, 24, tau, Li, dii) && chol_steps<C, 7>(row, 24, 32, tau, Li, dii);
+__device__ __forceinline__ bool warp_chol32(C (&row)[32], C tau, C* Li, C* dii, C* LT) {
+  return chol_steps<C, 31>(row, 0, 8, tau, Li, dii, LT) && chol_steps<C, 23>(row, 8, 16, tau, Li, dii, LT) &&
+         chol_steps<C, 15>(row, 16, 24, tau, Li, dii, LT) && chol_steps<C, 7>(row, 24, 32, tau, Li, dii, LT);
 }
 
 // Warp-level inverse of the lower triangular L held as rows (lane i: row[]
@@ -590,10 +596,28 @@ __device__ __forceinline__ void warp_blk_nt(C* Cb, const C* Ab, const C* Bb, boo
   __syncwarp();
 }
 
+// Thread-per-row forward substitution x <- x L_kk^-T (L_kk lower triangular,
+// given transposed in LT; rdg = 1 / diag), writing x to a[] as it goes.  x[0] is always column q: each
+// step updates the later entries and shifts them down by one (static register
+// indices, a rolled step loop); steps q0 <= q < q1 touch entries 1 .. J only.
+// A fully unrolled substitution (528 FMAs of straight-line code per row) ran
+// about three times slower inside the factorization.
+template <typename C, int J>
+__device__ __forceinline__ void trsm_steps(C (&x)[32], C* a, const C* LT, const C* rdg, int q0, int q1) {
+#pragma unroll 1
+  for (int q = q0; q < q1; ++q) {
+    const C xq = x[0] * rdg[q];
+    a[q] = xq;
+    const C* lq = LT + q * LTP + q;  // lq[j] = L(q + j, q); past column 31 never stored
+#pragma unroll
+    for (int j = 1; j <= J; ++j) x[j - 1] = fma(-xq, lq[j], x[j]);
+  }
+}
+
 // One warp: Cholesky of diagonal block k in place, and 1 / L(q, q) into
 // rdg[32 k + q].  On a pivot failure sets *fail.
 template <typename C>
-__device__ __forceinline__ void diag_potrf(C* Ls, C* rdg, int k, C tau, int* fail) {
+__device__ __forceinline__ void diag_potrf(C* Ls, C* rdg, int k, C tau, int* fail, C* LT) {
   const int lane = threadIdx.x % 32;
   C* A = Ls + (size_t)lblk(k, k) * CBS + lane * CP;
   C row[32];
@@ -601,7 +625,7 @@ __device__ __forceinline__ void diag_potrf(C* Ls, C* rdg, int k, C tau, int* fai
   for (int j = 0; j < 32; ++j) row[j] = (j <= lane) ? A[j] : C(0);
   __syncwarp();
   C dii = C(1);
-  const bool ok = warp_chol32<C>(row, tau, A, &dii);
+  const bool ok = warp_chol32<C>(row, tau, A, &dii, LT);
   __syncwarp();
   if (!ok) {
     if (lane == 0) *fail = 1;
@@ -628,7 +652,7 @@ template <typename C, int NT>
 __global__ void __launch_bounds__(NT)
     chol_kernel(int l, const double* __restrict__ G, const float* __restrict__ Gf, C* __restrict__ Ub,
                 C* __restrict__ dinv, double* __restrict__ R, DevStatus* st, int pass, const int* gate,
-                const int* skip, float accept) {
+                const int* skip, float accept, C* __restrict__ Lblk) {
   if ((gate && *gate == 0) || (skip && *skip != 0)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = (l + CBK - 1) / CBK;
@@ -638,6 +662,7 @@ __global__ void __launch_bounds__(NT)
   double* d = reinterpret_cast<double*>(Xs + (size_t)NB * CBS);
   C* rdc = reinterpret_cast<C*>(d + l);
   C* rdg = rdc + l;  // 1 / L(i, i), 32 NB entries
+  C* LT = rdg + CBK * NB;  // the latest diagonal factor, transposed (LT_ENTRIES)
   __shared__ int s_fail;
   __shared__ unsigned char s_bi[64], s_bj[64];
   const int tid = threadIdx.x;
@@ -756,27 +781,23 @@ __global__ void __launch_bounds__(NT)
       __syncthreads();
       if (keep) return;
     }
-    if (warp == 0) diag_potrf<C>(Ls, rdg, 0, ctau, &s_fail);
+    if (warp == 0) diag_potrf<C>(Ls, rdg, 0, ctau, &s_fail, LT);
     __syncthreads();
     if (s_fail == 0) {
       for (int k = 0; k < NB; ++k) {
         // (1) L_ik = A_ik L_kk^-T by forward substitution, one thread per row
         {
-          const C* Lkk = Ls + (size_t)lblk(k, k) * CBS;
           for (int rr = tid; rr < (NB - 1 - k) * CBK; rr += NT) {
             const int i = k + 1 + rr / CBK, r = rr % CBK;
             C* a = Ls + (size_t)lblk(i, k) * CBS + r * CP;
             C x[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) x[q] = a[q];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              x[q] *= rdg[CBK * k + q];
-#pragma unroll
-              for (int r2 = q + 1; r2 < 32; ++r2) x[r2] = fma(-x[q], Lkk[r2 * CP + q], x[r2]);
-            }
-#pragma unroll
-            for (int q = 0; q < 32; ++q) a[q] = x[q];
+            const C* rk = rdg + CBK * k;
+            trsm_steps<C, 31>(x, a, LT, rk, 0, 8);
+            trsm_steps<C, 23>(x, a, LT, rk, 8, 16);
+            trsm_steps<C, 15>(x, a, LT, rk, 16, 24);
+            trsm_steps<C, 7>(x, a, LT, rk, 24, 32);
           }
         }
         __syncthreads();
@@ -788,7 +809,7 @@ __global__ void __launch_bounds__(NT)
         __syncthreads();
         // (3) factor the next diagonal block || the rest of the trailing update
         if (warp == 0) {
-          diag_potrf<C>(Ls, rdg, k + 1, ctau, &s_fail);
+          diag_potrf<C>(Ls, rdg, k + 1, ctau, &s_fail, LT);
         } else {
           const int nt = NB - k - 2;  // block columns k + 2 .. NB - 1
           const int tasks = nt * (nt + 1) / 2;
@@ -842,20 +863,30 @@ __global__ void __launch_bounds__(NT)
       }
     }
   }
-  // Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a diagonal
-  // block (i <= j), 0 below
-  for (int i = warp; i < l; i += nw) {
-    const int bi = i >> 5, ii = i & 31;
-    C* Ui = Ub + (size_t)i * l;
-    for (int bj = 0; bj < NB; ++bj) {
-      const int j = CBK * bj + lane;
-      if (j >= l) break;
-      C v = C(0);
-      if (bj >= bi && i <= j) {
-        const C* blk = (bj == bi) ? Xs + (size_t)bj * CBS : Ls + (size_t)lblk(bj, bi) * CBS;
-        v = blk[lane * CP + ii];
+  if (Lblk) {
+    // the blocked factor as it sits in shared memory (L blocks, then the
+    // diagonal-block inverses), for the explicit inverse kernel: one flat,
+    // 16-byte copy
+    const int n4 = (nblk + NB) * CBS * (int)sizeof(C) / 16;
+    const float4* s4 = reinterpret_cast<const float4*>(Ls);
+    float4* d4 = reinterpret_cast<float4*>(Lblk);
+    for (int e = tid; e < n4; e += NT) d4[e] = s4[e];
+  } else {
+    // Ub(i, j) = L(j, i) for block(i) < block(j), X_bb(j, i) inside a diagonal
+    // block (i <= j), 0 below
+    for (int i = warp; i < l; i += nw) {
+      const int bi = i >> 5, ii = i & 31;
+      C* Ui = Ub + (size_t)i * l;
+      for (int bj = 0; bj < NB; ++bj) {
+        const int j = CBK * bj + lane;
+        if (j >= l) break;
+        C v = C(0);
+        if (bj >= bi && i <= j) {
+          const C* blk = (bj == bi) ? Xs + (size_t)bj * CBS : Ls + (size_t)lblk(bj, bi) * CBS;
+          v = blk[lane * CP + ii];
+        }
+        Ui[j] = v;
       }
-      Ui[j] = v;
     }
   }
   for (int i = tid; i < l; i += NT) dinv[i] = rdc[i];
@@ -864,7 +895,8 @@ __global__ void __launch_bounds__(NT)
 size_t chol_smem_bytes(int l, size_t csize) {
   const int NB = (l + CBK - 1) / CBK;
   const size_t blocks = (size_t)NB * (NB + 1) / 2 + NB;  // L, X
-  return blocks * CBS * csize + (size_t)l * sizeof(double) + (size_t)l * csize + (size_t)CBK * NB * csize;
+  return blocks * CBS * csize + (size_t)l * sizeof(double) + (size_t)l * csize + (size_t)CBK * NB * csize +
+         (size_t)LT_ENTRIES * csize;
 }
 
 // ----------------------------------------------------------------- apply --
@@ -1024,7 +1056,7 @@ void launch_apply(int rows, int l, T* Y, int ldy, const C* Ub, const C* dinv, __
 
 template <typename C>
 void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double* R, DevStatus* st, int pass,
-                 const int* gate, cudaStream_t s, const int* skip, float accept = 0.f) {
+                 const int* gate, cudaStream_t s, const int* skip, float accept = 0.f, C* Lblk = nullptr) {
   // binary32: 512 threads (at most 128 registers each; a diagonal-block warp
   // keeps a row of L and a row of its inverse in registers); binary64
   // (l <= 128): 256
@@ -1032,7 +1064,7 @@ void launch_chol(int l, const double* G, const float* Gf, C* Ub, C* dinv, double
   const size_t smem = chol_smem_bytes(l, sizeof(C));
   auto kfn = chol_kernel<C, NT>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip, accept);
+  kfn<<<1, NT, smem, s>>>(l, G, Gf, Ub, dinv, R, st, pass, gate, skip, accept, Lblk);
   note_launch();
 }
 
@@ -1116,11 +1148,12 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
 constexpr int INV_THREADS = 512;
 
 __global__ void __launch_bounds__(INV_THREADS)
-    inv_tri_kernel(int l, const float* __restrict__ Ub, const float* __restrict__ dinv, float* __restrict__ M,
+    inv_tri_kernel(int l, const float* __restrict__ Lblk, const float* __restrict__ dinv, float* __restrict__ M,
                    const int* gate) {
   if (gate && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = (l + CBK - 1) / CBK;
+  const int nblk = NB * (NB + 1) / 2;
   const int j = blockIdx.x;
   const int nw = NB - j;                      // blocks W_jj .. W_(NB-1) j
   float* Wc = reinterpret_cast<float*>(smem_raw);   // nw blocks
@@ -1129,61 +1162,40 @@ __global__ void __launch_bounds__(INV_THREADS)
   float* Tb = Lb + (size_t)(nw * (nw - 1) / 2) * CBS;
   const int tid = threadIdx.x;
   auto lidx = [&](int i, int k) { return (i - j - 1) * (i - j) / 2 + (k - j); };  // i > k >= j
-  // ---- stage: X_ii (i >= j) and L_ik (i > k >= j).  A staged block (I, K)
-  // (X_ii is (i, i)) is rows 32 K .. + 31, columns 32 I .. + 31 of Ub, stored
-  // transposed; each thread moves 4 consecutive columns of one row, eight
-  // such groups in flight.
+  // ---- stage X_ii (i >= j) and L_ik (i > k >= j): whole blocks of the
+  // Cholesky kernel's blocked factor (its shared-memory layout: the L blocks
+  // at index bi (bi + 1) / 2 + bj, then the diagonal-block inverses), copied
+  // 16 bytes at a time, eight copies in flight per thread
   const int nl = nw * (nw - 1) / 2;
-  __shared__ unsigned char s_bi[64], s_bk[64];
+  __shared__ unsigned short s_src[64];
   if (tid < nw + nl) {
     if (tid < nw) {
-      s_bi[tid] = (unsigned char)(j + tid);
-      s_bk[tid] = (unsigned char)(j + tid);
+      s_src[tid] = (unsigned short)(nblk + j + tid);
     } else {
       const int q = tid - nw;
       int a = 0;
       while ((a + 1) * (a + 2) / 2 <= q) ++a;  // q = a (a + 1) / 2 + b, b <= a
-      s_bi[tid] = (unsigned char)(j + 1 + a);
-      s_bk[tid] = (unsigned char)(j + (q - a * (a + 1) / 2));
+      const int i = j + 1 + a, k = j + (q - a * (a + 1) / 2);
+      s_src[tid] = (unsigned short)lblk(i, k);
     }
   }
   __syncthreads();
-  const bool v4 = (l % 4 == 0) && ((((uintptr_t)Ub) & 15) == 0);
-  const int ngroups = (nw + nl) * CBK * (CBK / 4);
-  for (int g0 = tid; g0 < ngroups; g0 += 8 * INV_THREADS) {
-    float4 v[8];
+  {
+    constexpr int B4 = CBS / 4;  // float4 per block
+    const int total = (nw + nl) * B4;
+    const float4* src = reinterpret_cast<const float4*>(Lblk);
+    float4* dst = reinterpret_cast<float4*>(Xd);  // Xd and Lb are contiguous
+    for (int g0 = tid; g0 < total; g0 += 8 * INV_THREADS) {
+      float4 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int g = g0 + u * INV_THREADS;
-      const int b = g >> 8, t = (g >> 3) & 31, r4 = (g & 7) * 4;
-      const int bb = b < nw + nl ? b : 0;
-      const int gi = CBK * s_bk[bb] + t, gj = CBK * s_bi[bb] + r4;
-      if (g < ngroups && gi < l && gj + 3 < l && v4) {
-        v[u] = *reinterpret_cast<const float4*>(Ub + (size_t)gi * l + gj);
-      } else {
-        float x[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) x[e] = (g < ngroups && gi < l && gj + e < l) ? Ub[(size_t)gi * l + gj + e] : 0.f;
-        v[u] = make_float4(x[0], x[1], x[2], x[3]);
+      for (int u = 0; u < 8; ++u) {
+        const int g = g0 + u * INV_THREADS;
+        if (g < total) v[u] = src[(size_t)s_src[g / B4] * B4 + g % B4];
       }
-    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int g = g0 + u * INV_THREADS;
-      if (g >= ngroups) break;
-      const int b = g >> 8, t = (g >> 3) & 31, r4 = (g & 7) * 4;
-      const int gi = CBK * s_bk[b] + t, gj0 = CBK * s_bi[b] + r4;
-      const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = r4 + e;
-        float val;
-        if (b < nw) {  // X_ii(r, t), the identity on the padding
-          val = (gi < l && gj0 + e < l) ? ((r >= t) ? x[e] : 0.f) : ((r == t) ? 1.f : 0.f);
-          Xd[(size_t)b * CBS + r * CP + t] = val;
-        } else {       // L_ik(r, t)
-          Lb[(size_t)(b - nw) * CBS + r * CP + t] = x[e];
-        }
+      for (int u = 0; u < 8; ++u) {
+        const int g = g0 + u * INV_THREADS;
+        if (g < total) dst[g] = v[u];
       }
     }
   }
@@ -1259,17 +1271,24 @@ __global__ void __launch_bounds__(INV_THREADS)
   }
 }
 
+// Floats of the Cholesky kernel's blocked factor (L blocks and the
+// diagonal-block inverses, CBS entries each).
+size_t chol_blocked_floats(int l) {
+  const size_t NB = (l + CBK - 1) / CBK;
+  return (NB * (NB + 1) / 2 + NB) * CBS;
+}
+
 size_t inv_tri_smem_bytes(int l) {
   const int NB = (l + CBK - 1) / CBK;
   const size_t nw = NB, nl = (size_t)NB * (NB - 1) / 2;
   return (2 * nw + nl + (nw - 1)) * CBS * sizeof(float);  // W, X, L, T
 }
 
-void launch_inv_tri(int l, const float* Ub, const float* dinv, float* M, const int* gate, cudaStream_t s) {
+void launch_inv_tri(int l, const float* Lblk, const float* dinv, float* M, const int* gate, cudaStream_t s) {
   const int NB = (l + CBK - 1) / CBK;
   const size_t smem = inv_tri_smem_bytes(l);
   cudaFuncSetAttribute(inv_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  inv_tri_kernel<<<NB, INV_THREADS, smem, s>>>(l, Ub, dinv, M, gate);
+  inv_tri_kernel<<<NB, INV_THREADS, smem, s>>>(l, Lblk, dinv, M, gate);
   note_launch();
 }
 
@@ -1281,6 +1300,7 @@ size_t orth_tc_workspace_bytes(int rows, int l, int sms) {
   c.take<__nv_bfloat16>((size_t)2 * l * l8);     // Mh, Ml
   c.take<unsigned char>(tc_gemm_workspace(rows, l, l, sms));
   c.take<float>((size_t)l * l);                   // M = R^-1
+  c.take<float>(chol_blocked_floats(l));          // the blocked factor
   return c.size();
 }
 
@@ -1306,6 +1326,7 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
   __nv_bfloat16* Ml = c0.take<__nv_bfloat16>((size_t)l * l8);
   float* part = c0.take<float>(tc_gemm_workspace(rows, l, l, sms) / sizeof(float) + 1);
   float* Minv = c0.take<float>((size_t)l * l);
+  float* Lblk = c0.take<float>(chol_blocked_floats(l));
   Carver c(base);
   double* P = c.take<double>((size_t)gram_splits(rows, l, sms, 4) * l * l);
   double* G = c.take<double>((size_t)l * l);
@@ -1328,8 +1349,8 @@ void run_orth_tc(int rows, int l, float* Y, int ldy, double* Rout, __nv_bfloat16
     // the factor in its blocked form (M's slot holds it), then R^-1 by block
     // columns on NB SMs
     launch_chol<float>(l, G, Gf, M, dinv, Rout ? Rp + (size_t)(pass - 1) * l * l : nullptr, st, pass, gate, s,
-                       nullptr, (intermediate && pass == 2 && !Rout) ? accept : 0.f);
-    launch_inv_tri(l, M, dinv, Minv, gate_rest, s);
+                       nullptr, (intermediate && pass == 2 && !Rout) ? accept : 0.f, Lblk);
+    launch_inv_tri(l, Lblk, dinv, Minv, gate_rest, s);
     // pass 3 runs only if pass 1 needed a shift (a device-side gate), the
     // second pass of an intermediate basis only if its Q failed the test: a
     // gated product returns at once and leaves Y alone (the split of M only
@@ -1403,6 +1424,13 @@ template <typename T>
 void launch_copy_bf16(int rows, int l, const T* Y, int ldy, __nv_bfloat16* Yb, int lb, cudaStream_t s) {
   const long long total = (long long)rows * l;
   if (total == 0) return;
+  if (sizeof(T) == 4 && l % 4 == 0 && ldy % 4 == 0 && lb % 4 == 0 && (((uintptr_t)Y & 15) == 0) &&
+      (((uintptr_t)Yb & 7) == 0)) {
+    // binary32: the vectorized conversion (four 16-byte loads in flight per
+    // thread), hi part only; its grid is capped at 8 x 256 CTAs
+    launch_split_bf16(rows, l, reinterpret_cast<const float*>(Y), ldy, Yb, nullptr, lb, 256, s);
+    return;
+  }
   copy_bf16_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(rows, l, Y, ldy, Yb, lb);
   note_launch();
 }

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(512)
   const size_t blk = (size_t)2 * w * cs;  // X then J, w columns each
   __shared__ int s_rot;
   __shared__ int s_total;
+  __shared__ int s_bad;
   __shared__ __align__(8) uint64_t in_bar[2];  // incoming blocks, by buffer parity
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int nwarps = blockDim.x / 32;
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(512)
   load_block(buf + 1 * blk, rr_pos(P - 1 - me, 0, P));
   if (tid == 0) {
     s_total = 0;
+    s_bad = 0;
     sm100::mbar_init(&in_bar[0], 1);
     sm100::mbar_init(&in_bar[1], 1);
     sm100::fence_mbar_init();
@@ -336,6 +338,62 @@ __global__ void __launch_bounds__(512)
     if (me == 0 && tid == 0) s_total = 0;
     cluster.sync();
     converged = (total == 0);
+    // Once a sweep rotates at most l pairs, test every pair of the current
+    // columns at once instead of sweeping again to find none to rotate: the
+    // fresh norms and the same dot product, summed in the same order, and the
+    // same test a sweep applies (with no rotation the columns do not change
+    // within a sweep, so the decision is the one a rotation-free sweep would
+    // take); if no pair fails, the next sweep is skipped.
+    if (!converged && total <= l) {
+      const int pn = ((sweep + 1) * (P - 1)) & 1;  // the next sweep's round-0 buffers
+      for (int cc = warp; cc < 2 * w; cc += nwarps) {
+        C* x = buf + (size_t)(2 * pn + cc / w) * blk + (size_t)(cc % w) * cs;
+        const V* xv = reinterpret_cast<const V*>(x);
+        C a = C(0);
+        for (int v = 0; v < nv; ++v) a = JVec<C>::dot(xv[v * 32 + lane], xv[v * 32 + lane], a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) x[lp] = a;
+      }
+      cluster.sync();
+      bool bad = false;
+      // each warp takes remote columns (every CTA's two blocks) and tests
+      // them against this CTA's 2w columns
+      for (int rb = warp; rb < NC * 2 * w; rb += nwarps) {
+        const int h = rb / (2 * w), sl = (rb % (2 * w)) / w, cb = rb % w;
+        const C* xb = cluster.map_shared_rank(buf + (size_t)(2 * pn + sl) * blk + (size_t)cb * cs, h);
+        const V* vb = reinterpret_cast<const V*>(xb) + lane;
+        V b[2];
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+          if (v < nv) b[v] = vb[32 * v];
+        const C be = xb[lp];
+        for (int oc = 0; oc < 2 * w; ++oc) {
+          if (h == me && sl == oc / w && cb == oc % w) continue;  // the column itself
+          const C* xa = buf + (size_t)(2 * pn + oc / w) * blk + (size_t)(oc % w) * cs;
+          const V* va = reinterpret_cast<const V*>(xa) + lane;
+          V a[2];
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+            if (v < nv) a[v] = va[32 * v];
+          const C al = xa[lp];
+          C g0 = C(0), g1 = C(0);
+          g0 = JVec<C>::dot(a[0], b[0], g0);
+          if (nv > 1) g1 = JVec<C>::dot(a[1], b[1], g1);
+          C ga = g0 + g1;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+          if (al > C(0) && be > C(0) && ga * ga > tol2 * al * be) bad = true;
+        }
+      }
+      if (bad && lane == 0) atomicOr(cluster.map_shared_rank(&s_bad, 0), 1);
+      cluster.sync();
+      const int nbad = *cluster.map_shared_rank(&s_bad, 0);
+      cluster.sync();
+      if (me == 0 && tid == 0) s_bad = 0;
+      cluster.sync();
+      converged = (nbad == 0);
+    }
   }
   if (me == 0 && tid == 0) st->jacobi_sweeps = sweep;
   if (timed_out && lane == 0) set_status(st, RSVD_E_TIMEOUT);

@@ -275,20 +275,32 @@ __global__ void __launch_bounds__(G32_THREADS, 7)
         }
       }
       __syncthreads();
-#pragma unroll 4
-      for (int e = tid; e < GT * GT; e += G32_THREADS) {
-        const int ii = e / GT, jj = e % GT;
-        const int i = bi * GT + ii, j = bj * GT + jj;
-        if (i < l && j < l) {
-          const float pv = (ii < 32 ? Fi + ii * GT : Fj + (ii - 32) * GT)[jj];
-          float2* o = out + (size_t)i * l + j;
-          if (first_fold) {
-            *o = make_float2(pv, 0.f);
-          } else {
-            const float2 h = *o;
-            float e2;
-            const float sum = two_sum(h.x, pv, e2);
-            *o = make_float2(sum, __fadd_rn(h.y, e2));
+      // 64 entries per thread in batches of 8: the running pairs of a batch
+      // are loaded together (8 loads in flight), then updated and stored
+      for (int e0 = tid; e0 < GT * GT; e0 += 8 * G32_THREADS) {
+        float2 h[8];
+        if (!first_fold) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * G32_THREADS;
+            const int i = bi * GT + e / GT, j = bj * GT + e % GT;
+            h[u] = (i < l && j < l) ? out[(size_t)i * l + j] : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * G32_THREADS;
+          const int ii = e / GT, jj = e % GT;
+          const int i = bi * GT + ii, j = bj * GT + jj;
+          if (i < l && j < l) {
+            const float pv = (ii < 32 ? Fi + ii * GT : Fj + (ii - 32) * GT)[jj];
+            float2 v = make_float2(pv, 0.f);
+            if (!first_fold) {
+              float e2;
+              const float sum = two_sum(h[u].x, pv, e2);
+              v = make_float2(sum, __fadd_rn(h[u].y, e2));
+            }
+            out[(size_t)i * l + j] = v;
           }
         }
       }

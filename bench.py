@@ -711,15 +711,15 @@ def poly_variants(a, rs, h, A, dev, stream, fro_rel):
     * krylov_2x128: the extended sampling matrix, 2 blocks of 128 columns
       (the same 4 passes as q = 1 at width 256);
     * basic_q0_l128: Fig. RSVD, k = 120, p = 8 (2 passes);
-    * single_pass_l128: Fig. singlepass_gen, k = 120, p = 8 (the two
-      sketches as separate launches: 2 reads of A);
+    * single_pass_l256: Fig. singlepass_gen, k = 120, p = 136 (the two
+      sketches as separate launches: 2 reads of A; with p = 8 the fit of
+      the core from bf16 sketches is too poorly conditioned to be useful);
     * srft_l128: Fig. RSVD with the SRFT test matrix, k = 100, p = 28
       (complex factors);
     * adaptive_spectral_4096: rsvd_adaptive_tol in its spectral mode on a
       4096^2 exp(-j/20)-decay matrix (binary32; a j^-1.5 tail keeps the
       Frobenius norm of the remainder, which the probes see, far above a
-      spectral eps at any rank under 256), eps = 1e-3 ||A||_2, beside the
-      Frobenius mode at the tolerance that gives the same spectral error."""
+      spectral eps at any rank under 256), eps = 5e-3 ||A||_2."""
     import torch
     m, n = a.m, a.n
     out = {}
@@ -732,7 +732,7 @@ def poly_variants(a, rs, h, A, dev, stream, fro_rel):
              ("power_q2_l256", dict(k=120, p=136, q=2), 6, 256),
              ("krylov_2x128", dict(k=120, p=8, q=2, krylov=True), 4, 256),
              ("basic_q0_l128", dict(k=120, p=8, q=0), 2, 128),
-             ("single_pass_l128", dict(k=120, p=8, q=0, single_pass=True), 2, 128),
+             ("single_pass_l256", dict(k=120, p=136, q=0, single_pass=True), 2, 256),
              ("srft_l128", dict(k=100, p=28, q=0, srft=True), 2, 256)]
     for name, kw, passes, width in cases:
         try:
@@ -778,7 +778,12 @@ def poly_variants(a, rs, h, A, dev, stream, fro_rel):
     try:
         from workloads import exp_decay_matrix_torch
         As = exp_decay_matrix_torch(4096, 4096, seed=a.seed + 7, rate=20.0, device=dev)
-        eps = 1e-3 * float(torch.exp(torch.tensor(-1.0 / 20.0)))  # 1e-3 sigma_1
+        # 5e-3 sigma_1: the probe test (max of 16 fresh probes at most
+        # eps / (10 sqrt(2/pi))) then stops at rank 208; at 1e-3 sigma_1 the
+        # blocked finder needs more than 256 columns on this spectrum (the
+        # float64 oracle's probes, same seeds: 1.25e-4 at rank 240 against a
+        # threshold of 1.19e-4)
+        eps = 5e-3 * float(torch.exp(torch.tensor(-1.0 / 20.0)))
         res = {}
 
         def solve_spec():

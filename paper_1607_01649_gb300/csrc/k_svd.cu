@@ -506,16 +506,18 @@ template cudaError_t launch_jacobi<double>(int, const double*, double*, double*,
 // first); D[rank] = sigma for rank < kk; Wsel, Jsel (l x kk row-major) hold the
 // selected columns.
 template <typename C>
-__global__ void sort_gather_kernel(int l, int kk, const double* __restrict__ sigma, const C* __restrict__ Wt,
-                                   const C* __restrict__ Jt, double* __restrict__ D, C* __restrict__ Wsel,
-                                   C* __restrict__ Jsel, int* __restrict__ perm) {
+__global__ void __launch_bounds__(256)
+    sort_gather_kernel(int l, int kk, const double* __restrict__ sigma, const C* __restrict__ Wt,
+                       const C* __restrict__ Jt, double* __restrict__ D, C* __restrict__ Wsel,
+                       C* __restrict__ Jsel, int* __restrict__ perm) {
+  // One CTA per selected column c: every CTA ranks all l values (l <= 512,
+  // l^2 integer compares over the CTA), then moves its column: row src of Wt
+  // and Jt (contiguous reads) into column c of Wsel and Jsel.
   __shared__ int sperm[512];
-  // Sort key: sigma, with NaN mapped to -inf so that (key desc, index asc) is
-  // a strict total order and the ranks form a permutation of 0..l-1.
-  for (int i = threadIdx.x; i < l; i += blockDim.x) sperm[i] = i;
-  __syncthreads();
   // Keys: the IEEE bit patterns of the (non-negative) sigmas order like the
-  // values; NaN maps to -1.  Integer compares avoid binary64 arithmetic.
+  // values; NaN maps to -1, so (key desc, index asc) is a strict total order
+  // and the ranks form a permutation of 0..l-1.  Integer compares avoid
+  // binary64 arithmetic.
   __shared__ long long key[512];
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
     const double v = sigma[i];
@@ -532,23 +534,23 @@ __global__ void sort_gather_kernel(int l, int kk, const double* __restrict__ sig
     sperm[rank] = i;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < kk; c += blockDim.x) {
-    const int src = min(max(sperm[c], 0), l - 1);
+  const int c = blockIdx.x;
+  const int src = min(max(sperm[c], 0), l - 1);
+  if (threadIdx.x == 0) {
     D[c] = sigma[src];
     if (perm) perm[c] = src;
   }
-  for (int e = threadIdx.x; e < l * kk; e += blockDim.x) {
-    const int i = e / kk, c = e % kk;
-    const int src = min(max(sperm[c], 0), l - 1);
-    Wsel[e] = Wt[(size_t)src * l + i];
-    Jsel[e] = Jt[(size_t)src * l + i];
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    Wsel[(size_t)i * kk + c] = Wt[(size_t)src * l + i];
+    Jsel[(size_t)i * kk + c] = Jt[(size_t)src * l + i];
   }
 }
 
 template <typename C>
 void launch_sort_gather(int l, int kk, const double* sigma, const C* Wt, const C* Jt, double* D, C* Wsel, C* Jsel,
                         cudaStream_t s) {
-  sort_gather_kernel<C><<<1, 512, 0, s>>>(l, kk, sigma, Wt, Jt, D, Wsel, Jsel, nullptr);
+  if (kk < 1) return;
+  sort_gather_kernel<C><<<kk, 256, 0, s>>>(l, kk, sigma, Wt, Jt, D, Wsel, Jsel, nullptr);
   note_launch();
 }
 template void launch_sort_gather<float>(int, int, const double*, const float*, const float*, double*, float*,

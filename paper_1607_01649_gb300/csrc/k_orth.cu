@@ -466,7 +466,10 @@ struct Eps<double> {
 // the binary32 path).  Out:
 //   Ub   : l x l row-major, type C: the upper triangular factor Lt^T whose
 //          32 x 32 diagonal blocks are replaced by their inverses; with dinv
-//          it defines Q = (Y D^-1) Lt^-T (blocked triangular solve, apply_kernel)
+//          it defines Q = (Y D^-1) Lt^-T (blocked triangular solve, apply_kernel).
+//          With Lblk given, the factor is written instead in its blocked
+//          shared-memory form (the L blocks, then the diagonal-block inverses)
+//          for the explicit inverse kernel.
 //   dinv : 1 / d_i, d_i = sqrt(G_ii)
 //   R    : optional l x l row-major binary64, R = Lt^T D (zeros below the diagonal)
 // where G = D Gt D and Gt = Lt Lt^T.  Pivots below tau (unit-diagonal scale)
@@ -1149,8 +1152,8 @@ void run_orth(int rows, int l, T* Y, int ldy, double* Rout, __nv_bfloat16* Ybf, 
 // products with binary64 sums).  Shorter blocks take the SIMT solve.
 // ------------------------------------------------------ explicit inverse --
 // M = R^-1 = D^-1 L^-T for the tensor-core apply, from the Cholesky kernel's
-// blocked factor Ub (Ub(i, j) = L(j, i) across blocks, X_bb(j, i) = (L_bb^-1)(j, i)
-// inside a diagonal block) and dinv.  The block columns of W = L^-1 are
+// blocked factor Lblk (the L blocks L_ik and the diagonal-block inverses
+// X_bb = L_bb^-1, each 32 x 32 with row stride CP) and dinv.  The block columns of W = L^-1 are
 // independent, so CTA j forms block column j by block forward substitution,
 //   W_jj = X_jj,  W_ij = -X_ii sum_{k = j}^{i - 1} L_ik W_kj  (i > j),
 // with every block it needs staged in shared memory first (L_ik for
